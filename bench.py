@@ -1,0 +1,353 @@
+"""Benchmark: time to ||F(u)||_2 < 1e-8 and subdomain Newton steps/s, FP64 plain vs chosen form.
+
+Workload (default): nonlinear diffusion -div((1 + u^2) grad u) = 1 on the unit square,
+1024 x 1024 P1 cells (~1.05M dofs), 1024 subdomains from the seeded uneven brick partition
+(+-15 % per side, seed 2410), overlap 2, RGDSW coarse space, hybrid two-level coupling
+(Eq. 11), zero initial guess.  One step = one complete solve from u = 0 to ||F|| < 1e-8:
+coarse Newton, one persistent batched local-Newton launch per outer iteration, exact
+tangent inside GMRES, outer Newton update -- every step of the hot path on the device.
+The chosen form uses FP32 local band factors with FP64 iterative refinement; the plain
+form factors in FP64.  Setup (maps, coarse basis) runs once before the timed region and is
+reported separately.
+
+The line printed by rank 0 is the JSON contract of this repository (metric, value = whole-
+job subdomain Newton steps/s, roofline of the dominant kernel, e2e through host buffers,
+cpu_baseline = the FP64 oracle on a bounded sample).  ``--impl reference`` times the oracle
+itself on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time to ||F||<1e-8 and subdomain Newton steps/s: plain FP64 vs chosen form"
+UNIT = "subdomain Newton steps/s"
+
+
+def workload(name: str):
+    from paper_2410_24138_gb300 import inputs as I
+    if name == "c2":
+        return I.diffusion_c2(), "diffusion 1024x1024 P1 (1.05M dofs), 1024 uneven subdomains, overlap 2"
+    if name == "c1":
+        return I.diffusion_c1(), "diffusion 64x64 P1, 4x4 subdomains, overlap 1"
+    if name == "c3":
+        return I.neohooke_c3(), "Neo-Hooke 512x512 Q1 (0.5M dofs), 256 uneven subdomains, overlap 2, 5 load steps"
+    raise SystemExit(f"unknown workload {name}")
+
+
+# ----------------------------------------------------------------------------------------------
+# CPU baseline: the oracle, as it stands, on a bounded sample of the same workload
+# ----------------------------------------------------------------------------------------------
+def oracle_sample(name: str, budget_s: float = 20.0):
+    """Local Newton solves of the first outer iteration (u = 0, one-level corrections) for as
+    many subdomains as fit in ``budget_s`` seconds; returns (steps/s, steps, subdomains, seconds)."""
+    from oracle import schwarz as S
+    p, _ = workload(name)
+    n_try = min(p.n_sub, 4096)
+    rng = np.random.default_rng(0)
+    which = sorted(rng.choice(p.n_sub, size=n_try, replace=False).tolist())
+    sw = S.Schwarz(p, S.Options(coupling=S.ONE_LEVEL), which=which)
+    u = np.zeros(sw.N)
+    load = 1.0 / max(1, p.load_steps)
+    steps = 0
+    done = 0
+    t0 = time.perf_counter()
+    for lp in sw.locals:
+        w, its, status, _, _ = lp.solve_newton(u, u[lp.sub.dofs], sw.opts, load)
+        steps += its
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return steps / dt, steps, done, dt
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    rates = []
+    for _ in range(args.warmup):
+        oracle_sample(args.workload, budget_s=2.0)
+    total_steps, total_time, subs = 0, 0.0, 0
+    for _ in range(args.steps):
+        r, st, sd, dt = oracle_sample(args.workload, budget_s=args.ref_budget)
+        rates.append(r)
+        total_steps += st
+        total_time += dt
+        subs += sd
+    value = total_steps / total_time
+    _, desc = workload(args.workload)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_time / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": desc},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{subs} subdomain local Newton solves (first outer iteration, u = 0) over "
+                                       f"{args.steps} steps, {total_steps} subdomain Newton steps"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ----------------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------------------------
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def timed_solves(torch, solver, n_dofs, steps, flush_buf):
+    """Device-resident solves from u = 0; returns per-step ms, total subdomain Newton steps, reports."""
+    stream = torch.cuda.current_stream()
+    times, reps = [], []
+    for _ in range(steps):
+        flush_buf.add_(1.0)  # write 512 MB > L2 between steps
+        u = torch.zeros(n_dofs, dtype=torch.float64, device="cuda")
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        u, rep = solver.solve(u)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        reps.append(rep)
+    return times, reps
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2410_24138_gb300 import build, nls
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    build.build()
+    p, desc = workload(args.workload)
+    stream = torch.cuda.current_stream().cuda_stream
+    flush_buf = torch.zeros(64 * 1024 * 1024, dtype=torch.float64, device="cuda")
+
+    def make(precision, profile=0):
+        s = nls.Solver(device=local, stream=stream)
+        s.set_problem(p)
+        s.set_coarse(nls.COARSE_RGDSW)
+        s.set_options(coupling=nls.COUPLING["hybrid"], load_steps=p.load_steps,
+                      local_precision=nls.PREC_FP32_IR if precision == "fp32" else nls.PREC_FP64,
+                      profile_kernels=profile)
+        t0 = time.perf_counter()
+        s.setup()
+        return s, time.perf_counter() - t0
+
+    chosen, setup_s = make("fp32")
+    sizes = chosen.sizes()
+    n_dofs = sizes.n_dofs
+    # warm-up (also compiles nothing: the library is prebuilt)
+    timed_solves(torch, chosen, n_dofs, args.warmup, flush_buf)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    t_wall0 = time.perf_counter()
+    times, reps = timed_solves(torch, chosen, n_dofs, args.steps, flush_buf)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall0
+    clk = clocks.stop()
+    if world > 1:
+        dist.barrier()
+    total_ms = sum(times)
+    steps_local = sum(r.subdomain_newton_steps for r in reps)
+    ms_t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+    st_t = torch.tensor([float(steps_local)], device="cuda", dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(st_t, op=dist.ReduceOp.SUM)
+    value = st_t.item() / (ms_t.item() * 1e-3)
+    rep0 = reps[-1]
+
+    # per-kernel timing of one more solve (CUDA events on the launching stream)
+    prof, _ = make("fp32", profile=1)
+    timed_solves(torch, prof, n_dofs, 1, flush_buf)
+    prof.reset_kernel_stats()
+    ptimes, preps = timed_solves(torch, prof, n_dofs, 1, flush_buf)
+    kstats = prof.kernel_stats()
+    prof.close()
+
+    # plain FP64 form on the same mesh
+    plain, plain_setup = make("fp64")
+    timed_solves(torch, plain, n_dofs, 1, flush_buf)
+    p_times, p_reps = timed_solves(torch, plain, n_dofs, max(1, min(args.steps, 3)), flush_buf)
+    plain_rate = sum(r.subdomain_newton_steps for r in p_reps) / (sum(p_times) * 1e-3)
+    plain.close()
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    host_u = torch.zeros(n_dofs, dtype=torch.float64).pin_memory()
+    e2e_steps, e2e_ms = 0, 0.0
+    for _ in range(args.steps):
+        flush_buf.add_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        hu = host_u.numpy()
+        hu[:] = 0.0
+        _, rep = chosen.solve(hu)
+        e2e_ms += (time.perf_counter() - t0) * 1e3
+        e2e_steps += rep.subdomain_newton_steps
+    e2e_value = e2e_steps / (e2e_ms * 1e-3)
+
+    # roofline of the dominant kernel
+    peaks, peak_kind = measured_peaks()
+    dom_name, (dom_launches, dom_ms) = max(kstats.items(), key=lambda kv: kv[1][1])
+    total_prof_ms = sum(v[1] for v in kstats.values())
+    roof = roofline_for(dom_name, dom_launches, dom_ms, sizes, peaks, peak_kind)
+
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            r, st, sd, dt = oracle_sample(args.workload, budget_s=args.ref_budget)
+            cpu = {"value": r, "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": f"{sd} subdomain local Newton solves of the first outer iteration (u = 0), "
+                             f"{st} subdomain Newton steps in {dt:.1f} s, single-threaded numpy/scipy"}
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+            "config": {"workload": desc, "coupling": "hybrid", "precision": "FP32 band factors + FP64 refinement",
+                       "l2": "512 MB buffer written between steps; working set > L2",
+                       "parallelism": "replicas" if world > 1 else "single GPU", "setup_s": setup_s,
+                       "n_dofs": n_dofs, "n_sub": sizes.n_sub, "coarse_dofs": sizes.n_coarse_dofs},
+            "time_to_solution_s": {"chosen": statistics.median(times) * 1e-3,
+                                   "plain_fp64": statistics.median(p_times) * 1e-3},
+            "subdomain_newton_steps_per_s": {"chosen": value / world, "plain_fp64": plain_rate},
+            "speedup_chosen_vs_plain": statistics.median(p_times) / statistics.median(times),
+            "iterations": {"outer": rep0.outer_iterations, "gmres": rep0.gmres_iterations,
+                           "subdomain_newton_steps": rep0.subdomain_newton_steps,
+                           "coarse_newton_steps": rep0.coarse_newton_steps,
+                           "final_residual": rep0.final_residual, "local_failures": rep0.local_failures},
+            "phases_s": {"inner": rep0.time_inner_s, "coarse": rep0.time_coarse_s, "gmres": rep0.time_gmres_s,
+                         "other": rep0.time_other_s},
+            "kernels_ms": {k: [v[0], round(v[1], 3), round(100.0 * v[1] / total_prof_ms, 1)] for k, v in
+                           sorted(kstats.items(), key=lambda kv: -kv[1][1])[:8]},
+            "roofline": roof,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * n_dofs, "d2h_bytes_per_step": 8 * n_dofs},
+            "gpu_launches": int(sum(r.kernel_launches for r in reps)),
+            "clocks": clk,
+            "cpu_baseline": cpu,
+            "wall_s": t_wall,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def roofline_for(name, launches, ms, sizes, peaks, peak_kind):
+    """Achieved algorithmic bandwidth (or ALU rate) of the dominant kernel per launch."""
+    avg_s = ms * 1e-3 / max(1, launches)
+    if "local_apply" in name:
+        fb = sizes.factor_bytes
+        # one pass over the factors, the local Jacobian (value + column index), the table gather
+        # of the input vector and the owned scatter of the output
+        alg = (sizes.total_factor_entries * fb + sizes.total_local_nnz * 12 + sizes.total_table_dofs * 12
+               + sizes.n_dofs * 8)
+        peak = peaks["hbm_gbs"]
+        return {"kernel": name, "bound": "hbm", "achieved": alg / avg_s / 1e9, "peak": peak, "unit": "GB/s",
+                "frac": alg / avg_s / 1e9 / peak, "traffic": None, "algorithmic_bytes_per_launch": alg,
+                "avg_launch_ms": avg_s * 1e3, "peak_source": peak_kind}
+    if "multidot" in name or "multiaxpy" in name or "spmv" in name or "p0" in name:
+        return {"kernel": name, "bound": "hbm", "achieved": None, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": None, "traffic": None, "avg_launch_ms": avg_s * 1e3, "peak_source": peak_kind}
+    return {"kernel": name, "bound": "alu", "achieved": None, "peak": None, "unit": "TFLOP/s", "frac": None,
+            "traffic": None, "avg_launch_ms": avg_s * 1e3, "peak_source": peak_kind}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3"])
+    ap.add_argument("--ref-budget", type=float, default=20.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("at least 3 warm-up steps are required")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

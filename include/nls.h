@@ -1,0 +1,221 @@
+/*
+ * nls.h -- C ABI of the GB300 (sm_103a) two-level nonlinear Schwarz solver.
+ *
+ * The library solves the discrete nonlinear problem F(u) = 0 of Eq. 3 of Heinlein, Ho,
+ * Klawonn, Lanser, "Nonlinear Two-Level Schwarz Methods: A Parallel Implementation in
+ * FROSch" (arXiv 2410.24138), for the two model problems of Section 1:
+ *   - Eq. 1, nonlinear diffusion -div(k (1 + u^2) grad u) = f on P1 triangles, and
+ *   - Eq. 2, compressible Neo-Hooke elasticity on Q1 quadrilaterals (2 dofs per node),
+ * by Newton's method on the nonlinearly preconditioned problem F_x(u) = 0 of Section 2:
+ * x = one-level (Eq. 5), additive (Eq. 10) or hybrid (Eq. 11), with the local corrections
+ * of Eq. 4 on element-overlapping subdomains, the restricted extension of Eq. 8, the RGDSW
+ * coarse correction of Eq. 9 and the exact tangents of Eqs. 6 and 12 inside GMRES (Eq. 13).
+ *
+ * Conventions for every call:
+ *   - Every function returns an int status: NLS_OK (0), a negative NLS_E_* error, or a
+ *     positive NLS_W_* warning.  nls_strerror() gives a static message; nls_last_error()
+ *     gives the detail of the last error on a context.
+ *   - The caller owns every array it passes; the library copies what it needs before the
+ *     call returns.  Arrays are host pointers unless an argument says "device": then they
+ *     must be device memory of the context's device (for example a torch CUDA tensor).
+ *   - Global dof numbering: dof = node * ndof + component (ndof = 1 for Eq. 1, 2 for Eq. 2).
+ *     Global vectors have n_nodes * ndof entries; entries of Dirichlet dofs hold the
+ *     Dirichlet values.
+ *   - One context per CUDA stream; calls on a context are not thread safe.
+ *   - The library allocates its device memory in nls_setup() and frees it in nls_destroy().
+ */
+#ifndef NLS_H
+#define NLS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes --------------------------------------------------------------------- */
+#define NLS_OK 0
+#define NLS_E_ARG (-1)            /* invalid argument, size or call order */
+#define NLS_E_CUDA (-2)           /* a CUDA runtime call failed */
+#define NLS_E_NOMEM (-3)          /* device or host allocation failed */
+#define NLS_E_UNSUPPORTED (-4)    /* a feature outside the library's scope was requested */
+#define NLS_E_LOCAL_NEWTON (-5)   /* a local (Eq. 4) or coarse (Eq. 9) Newton solve failed */
+#define NLS_E_PIVOT (-6)          /* zero or non-finite pivot in a no-pivoting band factorization */
+#define NLS_E_GMRES (-7)          /* GMRES reached its iteration limit */
+#define NLS_E_DIVERGED (-8)       /* non-finite outer residual */
+#define NLS_E_DEVICE_TIMEOUT (-9) /* a bounded device-side wait gave up */
+#define NLS_W_NOT_CONVERGED 1     /* outer Newton stopped at its iteration limit */
+
+/* ---- enumerations --------------------------------------------------------------------- */
+#define NLS_P1_TRI 1              /* 3-node triangles, nodes counter-clockwise */
+#define NLS_Q1_QUAD 2             /* 4-node quadrilaterals, nodes counter-clockwise */
+#define NLS_LAW_DIFFUSION 1       /* Eq. 1 */
+#define NLS_LAW_NEOHOOKE 2        /* Eq. 2 */
+#define NLS_COUPLING_ONE 0        /* F_1 = sum P~_i T_i (Eq. 5, RASPEN form) */
+#define NLS_COUPLING_ADD 1        /* F_a (Eq. 10) */
+#define NLS_COUPLING_HYBRID 2     /* F_h (Eq. 11) */
+#define NLS_COARSE_NONE 0
+#define NLS_COARSE_RGDSW 1        /* RGDSW option 2.2 with the Dirichlet-edge modification (Section 2) */
+#define NLS_PREC_FP64 0           /* local factorizations and triangular solves in FP64 */
+#define NLS_PREC_FP32_IR 1        /* FP32 factorizations + FP64 iterative refinement */
+
+/* Solver options.  nls_options_default() fills the values of Section 3 of the paper:
+ * inner Newton rel 1e-5 / abs 1e-11, GMRES rel 1e-6 with at most 1000 iterations. */
+typedef struct nls_options {
+  int32_t coupling;           /* NLS_COUPLING_* */
+  int32_t local_precision;    /* NLS_PREC_* for the local factorizations */
+  int32_t coarse_precision;   /* NLS_PREC_* for the coarse factorization */
+  int32_t load_steps;         /* dead load ramped as k / load_steps, k = 1..load_steps */
+  double outer_atol;          /* outer Newton stops when ||F(u)||_2 < outer_atol */
+  int32_t outer_maxit;
+  double inner_rtol, inner_atol;   /* local and coarse Newton stopping test */
+  int32_t inner_maxit;
+  int32_t ls_trials;          /* Armijo backtracking trial steps (alpha = 1, 1/2, ...) */
+  double armijo;              /* sufficient decrease constant */
+  double gmres_rtol;
+  int32_t gmres_restart;
+  int32_t gmres_maxit;
+  double ir_rtol;             /* iterative refinement stops at ||r - J s|| <= ir_rtol ||r|| */
+  int32_t ir_max_sweeps;
+  int32_t threads_per_block;  /* CTA size of the batched local kernels (0 = library choice) */
+  int32_t verbose;
+  int32_t profile_kernels;    /* 1: time every kernel launch with CUDA events on the context's
+                                 stream and accumulate per-kernel totals (nls_get_kernel_stats) */
+} nls_options;
+
+/* Per-solve report. */
+typedef struct nls_report {
+  int32_t status;                 /* same as the return value of nls_solve */
+  int32_t outer_iterations;       /* summed over load steps */
+  int32_t gmres_iterations;       /* summed */
+  int64_t subdomain_newton_steps; /* sum over outer iterations and subdomains of local Newton iterations */
+  int32_t coarse_newton_steps;    /* summed */
+  int32_t local_failures;         /* (subdomain, outer iteration) pairs whose local Newton did not converge */
+  int32_t first_failed_subdomain; /* -1 if none */
+  double final_residual;          /* ||F(u)||_2 at exit */
+  double time_total_s;            /* device wall time of nls_solve (CUDA events) */
+  double time_inner_s;            /* batched local Newton launches ("Inner solve") */
+  double time_coarse_s;           /* coarse Newton and coarse factorizations ("Coarse solve") */
+  double time_gmres_s;            /* GMRES incl. tangent applications ("GMRES") */
+  double time_other_s;            /* the rest ("Other") */
+  int64_t kernel_launches;        /* kernels launched by this call */
+} nls_report;
+
+typedef struct nls_ctx nls_ctx;
+
+/* Fill *opt with the defaults described above. */
+void nls_options_default(nls_options* opt);
+
+/* Create a context on CUDA device `device`, using `cuda_stream` (a cudaStream_t, or NULL for
+ * a stream the library creates).  *out receives the context. */
+int nls_create(nls_ctx** out, int device, void* cuda_stream);
+void nls_destroy(nls_ctx* ctx);
+const char* nls_strerror(int status);
+const char* nls_last_error(const nls_ctx* ctx);
+
+/* Mesh (Section 1, P1 or Q1): xy [n_nodes * 2] coordinates, conn [n_elems * nen] node ids
+ * (nen = 3 for NLS_P1_TRI, 4 for NLS_Q1_QUAD), counter-clockwise. */
+int nls_set_mesh(nls_ctx* ctx, int elem_type, int64_t n_nodes, const double* xy, int64_t n_elems,
+                 const int32_t* conn);
+
+/* Dirichlet data u = g_D on the listed dofs (Eqs. 1, 2).  All components of a node must be
+ * fixed together (NLS_E_UNSUPPORTED otherwise). */
+int nls_set_dirichlet(nls_ctx* ctx, int64_t n, const int64_t* dofs, const double* values);
+
+/* Dead-load traction g_N of Eq. 2 on boundary segments: edge_nodes [n_edges * 2],
+ * traction [n_edges * 2] force per unit length at load factor 1. */
+int nls_set_traction(nls_ctx* ctx, int64_t n_edges, const int32_t* edge_nodes, const double* traction);
+
+/* Material law.  NLS_LAW_DIFFUSION: params unused, k_elem and f_elem [n_elems] (NULL = 1).
+ * NLS_LAW_NEOHOOKE: params = {E, nu}; k_elem, f_elem must be NULL. */
+int nls_set_material(nls_ctx* ctx, int law, const double* params, const double* k_elem, const double* f_elem);
+
+/* Non-overlapping element partition elem_to_sub [n_elems] with ids 0..n_sub-1, grown by
+ * `overlap` >= 1 layers of node-sharing elements (Section 2: element-based overlap). */
+int nls_set_partition(nls_ctx* ctx, int32_t n_sub, const int32_t* elem_to_sub, int32_t overlap);
+
+/* Coarse space NLS_COARSE_NONE or NLS_COARSE_RGDSW. */
+int nls_set_coarse(nls_ctx* ctx, int kind);
+
+int nls_set_options(nls_ctx* ctx, const nls_options* opt);
+int nls_get_options(const nls_ctx* ctx, nls_options* opt);
+
+/* Build every map (overlap, local numbering, owners, coarse interface classes), upload to the
+ * device and compute the coarse basis.  Must follow the nls_set_* calls above. */
+int nls_setup(nls_ctx* ctx);
+
+/* Host part of nls_setup only: builds every integer map (overlap, local numbering, owners,
+ * coarse interface classes) without touching a GPU.  The inspection calls nls_get_sizes,
+ * nls_get_local_dofs, nls_get_overlap_elems, nls_get_owners and nls_get_coarse_nodes work
+ * after it; nls_solve and the evaluation hooks need nls_setup. */
+int nls_setup_host(nls_ctx* ctx);
+
+/* Solve F(u) = 0 by the outer Newton iteration on F_x (Eq. 13).  u_inout [n_nodes * ndof]:
+ * initial guess in, solution out (Dirichlet entries are overwritten with the Dirichlet values);
+ * host memory, or device memory when u_is_device != 0.  rep may be NULL. */
+int nls_solve(nls_ctx* ctx, double* u_inout, int u_is_device, nls_report* rep);
+
+/* ---- parity and inspection hooks ------------------------------------------------------- */
+
+/* Sizes of the setup products. */
+typedef struct nls_sizes {
+  int64_t n_nodes, n_dofs, n_elems;
+  int32_t ndof, n_sub, n_coarse_nodes, n_coarse_dofs;
+  int64_t total_local_dofs;   /* sum_i |V_i| */
+  int64_t total_overlap_elems;
+  int32_t max_local_dofs, max_half_band, coarse_half_band;
+  int64_t device_bytes;
+  int64_t total_factor_entries;  /* sum_i |V_i| (2 b_i + 1): band factor storage of all subdomains */
+  int64_t total_local_nnz;       /* sum_i nnz(R_i DF P_i plus its boundary columns) */
+  int64_t total_table_dofs;      /* sum_i dofs touched by Omega_i' */
+  int32_t factor_bytes;          /* 4 (FP32 factors) or 8 (FP64 factors) per the current options */
+  int32_t pad;
+} nls_sizes;
+
+/* Per-kernel timing collected while nls_options.profile_kernels is set.  `name` is a static
+ * string owned by the library. */
+typedef struct nls_kernel_stat {
+  const char* name;
+  int64_t launches;
+  double total_ms;
+} nls_kernel_stat;
+/* Copy up to `cap` entries (kernels with at least one launch) into out; *n_out receives the count. */
+int nls_get_kernel_stats(const nls_ctx* ctx, int32_t cap, nls_kernel_stat* out, int32_t* n_out);
+int nls_reset_kernel_stats(nls_ctx* ctx);
+int nls_get_sizes(const nls_ctx* ctx, nls_sizes* out);
+
+/* Local numbering of subdomain `sub` (R_i of Section 2): the global dof ids of its local
+ * unknowns in local order (ascending), dofs_out[cap]; owned_out[cap] (may be NULL) receives 1
+ * where P~_i keeps the dof (Eq. 8).  *n_out receives |V_i|. */
+int nls_get_local_dofs(const nls_ctx* ctx, int32_t sub, int64_t cap, int64_t* dofs_out, uint8_t* owned_out,
+                       int64_t* n_out);
+/* Elements of the overlapping subdomain Omega_i' (ascending global ids). */
+int nls_get_overlap_elems(const nls_ctx* ctx, int32_t sub, int64_t cap, int32_t* elems_out, int64_t* n_out);
+/* owner(node) of every node (min id of the non-overlapping subdomains touching it). */
+int nls_get_owners(const nls_ctx* ctx, int32_t* owners_out);
+/* Coarse nodes: for coarse node c, its smallest global node id (ascending order). */
+int nls_get_coarse_nodes(const nls_ctx* ctx, int32_t* first_node_out);
+/* The coarse basis P_0 as a dense column-major [n_dofs x n_coarse_dofs] host array. */
+int nls_get_coarse_basis(const nls_ctx* ctx, double* P0_out);
+
+/* F(u) of Eq. 3 (Dirichlet rows zero) at load factor `load`; u, F of length n_dofs. */
+int nls_eval_F(nls_ctx* ctx, const double* u, double* F, int is_device, double load);
+
+/* F_x(u) (Eq. 5, 10 or 11 per the coupling option) at load factor `load`, and keep the
+ * linearisation for nls_apply_tangent.  local_its_out [n_sub] and local_status_out [n_sub]
+ * (may be NULL) receive the local Newton iteration counts and status (0 = converged,
+ * 1 = iteration limit, 2 = line search failed, 3 = non-finite, 4 = bad pivot). */
+int nls_eval_Fx(nls_ctx* ctx, const double* u, double* Fx, int is_device, double load,
+                int32_t* local_its_out, int32_t* local_status_out);
+
+/* y = DF_x(u) v (Eqs. 6, 12) at the u of the last nls_eval_Fx. */
+int nls_apply_tangent(nls_ctx* ctx, const double* v, double* y, int is_device);
+
+/* Converged local states w_i = R_i (u - P_i T_i(u)) of the last nls_eval_Fx, concatenated in
+ * subdomain order (total_local_dofs entries). */
+int nls_get_local_states(nls_ctx* ctx, double* w_out, int is_device);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NLS_H */

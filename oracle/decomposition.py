@@ -75,8 +75,11 @@ def owners(prob: Problem, star) -> np.ndarray:
     return np.minimum.reduceat(sub_of, ptr[:-1]).astype(np.int32)
 
 
-def decompose(prob: Problem):
-    """Build all overlapping subdomains of a problem.  Returns (subdomains, owner per node)."""
+def decompose(prob: Problem, which=None):
+    """Build the overlapping subdomains of a problem (all, or the ids in ``which``).
+
+    Returns (subdomains, owner per node).
+    """
     star = node_star(prob.conn, prob.n_nodes)
     ptr, star_el = star
     star_size = np.diff(ptr)
@@ -85,8 +88,10 @@ def decompose(prob: Problem):
     dirichlet[prob.dirichlet_nodes] = True
     ndof = prob.ndof
     subs = []
-    for i in range(prob.n_sub):
-        base = np.nonzero(prob.elem_to_sub == i)[0]
+    order = np.argsort(prob.elem_to_sub, kind="stable")
+    bounds = np.searchsorted(prob.elem_to_sub[order], np.arange(prob.n_sub + 1))
+    for i in (range(prob.n_sub) if which is None else which):
+        base = order[bounds[i]:bounds[i + 1]]
         elems = grow(base, prob.conn, star, prob.overlap)
         tnodes, inv = np.unique(prob.conn[elems], return_inverse=True)
         lconn = inv.reshape(elems.shape[0], -1).astype(np.int64)

@@ -156,13 +156,15 @@ class Model:
         self.f = np.ones(n_el) if prob.f_elem is None else np.asarray(prob.f_elem, dtype=np.float64)
         self.mu, self.lam = lame(prob.young, prob.poisson)
 
-    def element_terms(self, elems: np.ndarray, Xe: np.ndarray, ue: np.ndarray, want_jac: bool = True):
+    def element_terms(self, elems: np.ndarray, Xe: np.ndarray, ue: np.ndarray, want_jac: bool = True,
+                      load: float = 1.0):
         """(r [E, nen*ndof], K [E, nen*ndof, nen*ndof] or None, ok flag) for the listed elements.
 
+        ``load`` scales the external source f of Eq. 1 (load stepping ramps every external load).
         ``ok`` is False when a Neo-Hooke element has det F <= 0 at a Gauss point.
         """
         if self.prob.law == LAW_DIFFUSION:
-            r, K = diffusion_p1(Xe, ue, self.k[elems], self.f[elems], want_jac)
+            r, K = diffusion_p1(Xe, ue, self.k[elems], load * self.f[elems], want_jac)
             return r, K, True
         with np.errstate(invalid="ignore", divide="ignore"):
             r, K, detmin = neohooke_q1(Xe, ue, self.mu, self.lam, want_jac)
@@ -185,11 +187,11 @@ def free_mask(prob: Problem) -> np.ndarray:
 
 
 def global_residual(model: Model, u: np.ndarray, load: float = 1.0) -> np.ndarray:
-    """F(u) of Eq. 3 over all dofs; rows of Dirichlet dofs are zero."""
+    """F(u) of Eq. 3 over all dofs at load factor ``load`` (scaling f and g_N); Dirichlet rows are zero."""
     prob = model.prob
     all_e = np.arange(prob.conn.shape[0])
     dofs = element_dofs(prob.conn, model.ndof)
-    r, _, _ = model.element_terms(all_e, prob.xy[prob.conn], u[dofs], want_jac=False)
+    r, _, _ = model.element_terms(all_e, prob.xy[prob.conn], u[dofs], want_jac=False, load=load)
     F = np.zeros(u.shape[0])
     np.add.at(F, dofs.ravel(), r.ravel())
     if prob.traction_edges is not None:

@@ -134,7 +134,7 @@ class LocalProblem:
         return xt
 
     def residual(self, xt: np.ndarray, load: float):
-        r, _, ok = self.model.element_terms(self.sub.elems, self.Xe, xt[self.ldofs], want_jac=False)
+        r, _, ok = self.model.element_terms(self.sub.elems, self.Xe, xt[self.ldofs], want_jac=False, load=load)
         full = np.zeros(self.nt)
         np.add.at(full, self.ldofs.ravel(), r.ravel())
         if self.edofs is not None:
@@ -178,13 +178,13 @@ class LocalResult:
 class Schwarz:
     """Everything set up once per problem: model, subdomains, owners, coarse space."""
 
-    def __init__(self, prob: Problem, opts: Options, with_coarse: bool | None = None):
+    def __init__(self, prob: Problem, opts: Options, with_coarse: bool | None = None, which=None):
         self.prob = prob
         self.opts = opts
         self.model = fem.Model(prob)
         self.N = prob.n_nodes * prob.ndof
         self.free = fem.free_mask(prob)
-        self.subs, self.owner = dec.decompose(prob)
+        self.subs, self.owner = dec.decompose(prob, which)
         self.locals = [LocalProblem(self.model, s) for s in self.subs]
         need_coarse = opts.coupling != ONE_LEVEL if with_coarse is None else with_coarse
         self.cs = None

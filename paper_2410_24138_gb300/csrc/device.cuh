@@ -1,0 +1,360 @@
+// Device building blocks of the nonlinear Schwarz solver (sm_103a).
+//
+// * element routines of Eq. 1 (P1 nonlinear diffusion) and Eq. 2 (Q1 compressible Neo-Hooke),
+// * block reductions with a fixed summation order (results do not depend on scheduling),
+// * the no-pivoting band LU with a sliding shared-memory window over (b + 2) rows, reading
+//   the assembled CSR rows of a local Jacobian and streaming finished factor rows to global
+//   memory,
+// * blocked forward / backward substitution with the band factors (one warp solves each
+//   32-row diagonal block, the whole CTA applies its coupling to the next b rows).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "nls_internal.h"
+
+namespace nls {
+namespace dev {
+
+constexpr int kWarp = 32;
+
+// ------------------------------------------------------------------------------------------
+// reductions (deterministic for a fixed block size)
+// ------------------------------------------------------------------------------------------
+__device__ inline double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum over the block; every thread receives the result.  `red` holds >= 33 doubles.
+__device__ inline double block_sum(double v, double* red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    double t = (lane < nw) ? red[lane] : 0.0;
+    t = warp_sum(t);
+    if (lane == 0) red[32] = t;
+  }
+  __syncthreads();
+  return red[32];
+}
+
+// ------------------------------------------------------------------------------------------
+// Eq. 1 on P1 triangles.  geo = {dphi_0/dx, dphi_0/dy, dphi_1/dx, ..., area, pad}.
+// Residual of the element:  r_a = k Q (grad u . grad phi_a), Q = int_T (1 + u^2) by the
+// exact edge-midpoint rule; the source term is handled through the external load vector.
+// ------------------------------------------------------------------------------------------
+struct P1State {
+  double gx, gy, m01, m12, m20, kq, k, area;
+};
+
+__device__ inline P1State p1_state(const double* geo, double k, double u0, double u1, double u2) {
+  P1State s;
+  s.gx = u0 * geo[0] + u1 * geo[2] + u2 * geo[4];
+  s.gy = u0 * geo[1] + u1 * geo[3] + u2 * geo[5];
+  s.m01 = 0.5 * (u0 + u1);
+  s.m12 = 0.5 * (u1 + u2);
+  s.m20 = 0.5 * (u2 + u0);
+  s.area = geo[6];
+  s.k = k;
+  const double Q = s.area * (1.0 / 3.0) * (3.0 + s.m01 * s.m01 + s.m12 * s.m12 + s.m20 * s.m20);
+  s.kq = k * Q;
+  return s;
+}
+
+__device__ inline void p1_residual(const double* geo, const P1State& s, double r[3]) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) r[a] = s.kq * (s.gx * geo[2 * a] + s.gy * geo[2 * a + 1]);
+}
+
+// K[a][b] = d r_a / d u_b = k Q grad phi_a . grad phi_b + k (grad u . grad phi_a) dQ/du_b
+template <typename T>
+__device__ inline void p1_jacobian(const double* geo, const P1State& s, T K[9]) {
+  const double a3 = s.area * (1.0 / 3.0);
+  const double dQ[3] = {a3 * (s.m01 + s.m20), a3 * (s.m01 + s.m12), a3 * (s.m12 + s.m20)};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const double flux = s.gx * geo[2 * a] + s.gy * geo[2 * a + 1];
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+      K[a * 3 + b] = (T)(s.kq * (geo[2 * a] * geo[2 * b] + geo[2 * a + 1] * geo[2 * b + 1]) + s.k * flux * dQ[b]);
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Eq. 2 on Q1 quadrilaterals, 2x2 Gauss.  geo per Gauss point q (stride 10): dN_a/dX (4 x 2)
+// then weight * det(dX/dxi).  P = mu F - (mu - lambda ln J) F^-T.
+// With p_a = F^-1 applied from the left to grad N_a (p_a[i] = sum_J gradN_a[J] Finv[J][i]):
+//   r_{a,i}      = w [ mu (F gradN_a)_i - (mu - lambda ln J) p_a[i] ]
+//   K_{ai, bk}   = w [ mu delta_ik gradN_a . gradN_b + lambda p_a[i] p_b[k] + (mu - lambda ln J) p_a[k] p_b[i] ]
+// ------------------------------------------------------------------------------------------
+template <typename T>
+struct NHPoint {
+  T F00, F01, F10, F11, i00, i01, i10, i11, c, w;  // c = mu - lambda ln J
+  bool ok;
+};
+
+template <typename T>
+__device__ inline NHPoint<T> nh_point(const double* g, const T u[8], T mu, T lam) {
+  NHPoint<T> p;
+  p.F00 = 1;
+  p.F01 = 0;
+  p.F10 = 0;
+  p.F11 = 1;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const T bx = (T)g[2 * a], by = (T)g[2 * a + 1];
+    p.F00 += u[2 * a] * bx;
+    p.F01 += u[2 * a] * by;
+    p.F10 += u[2 * a + 1] * bx;
+    p.F11 += u[2 * a + 1] * by;
+  }
+  const T det = p.F00 * p.F11 - p.F01 * p.F10;
+  p.ok = det > (T)0;
+  const T inv = (T)1 / det;
+  p.i00 = p.F11 * inv;
+  p.i01 = -p.F01 * inv;
+  p.i10 = -p.F10 * inv;
+  p.i11 = p.F00 * inv;
+  p.c = mu - lam * (p.ok ? log(det) : (T)0);
+  p.w = (T)g[8];
+  return p;
+}
+
+__device__ inline void nh_residual(const double* geo, const double u[8], double mu, double lam, double r[8], bool& ok) {
+#pragma unroll
+  for (int k = 0; k < 8; ++k) r[k] = 0.0;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const double* g = geo + q * 10;
+    NHPoint<double> p = nh_point<double>(g, u, mu, lam);
+    ok = ok && p.ok;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const double bx = g[2 * a], by = g[2 * a + 1];
+      const double pa0 = bx * p.i00 + by * p.i10, pa1 = bx * p.i01 + by * p.i11;
+      r[2 * a] += p.w * (mu * (p.F00 * bx + p.F01 * by) - p.c * pa0);
+      r[2 * a + 1] += p.w * (mu * (p.F10 * bx + p.F11 * by) - p.c * pa1);
+    }
+  }
+}
+
+template <typename T>
+__device__ inline void nh_jacobian(const double* geo, const double ud[8], double mud, double lamd, T K[64]) {
+  T u[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) u[k] = (T)ud[k];
+  const T mu = (T)mud, lam = (T)lamd;
+#pragma unroll
+  for (int k = 0; k < 64; ++k) K[k] = 0;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const double* g = geo + q * 10;
+    NHPoint<T> p = nh_point<T>(g, u, mu, lam);
+    T bx[4], by[4], p0[4], p1[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      bx[a] = (T)g[2 * a];
+      by[a] = (T)g[2 * a + 1];
+      p0[a] = bx[a] * p.i00 + by[a] * p.i10;
+      p1[a] = bx[a] * p.i01 + by[a] * p.i11;
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const T gg = mu * (bx[a] * bx[b] + by[a] * by[b]);
+        // rows (a, i), cols (b, k)
+        K[(2 * a + 0) * 8 + 2 * b + 0] += p.w * (gg + lam * p0[a] * p0[b] + p.c * p0[a] * p0[b]);
+        K[(2 * a + 0) * 8 + 2 * b + 1] += p.w * (lam * p0[a] * p1[b] + p.c * p1[a] * p0[b]);
+        K[(2 * a + 1) * 8 + 2 * b + 0] += p.w * (lam * p1[a] * p0[b] + p.c * p0[a] * p1[b]);
+        K[(2 * a + 1) * 8 + 2 * b + 1] += p.w * (gg + lam * p1[a] * p1[b] + p.c * p1[a] * p1[b]);
+      }
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Band LU without pivoting.  Rows of the matrix come from a CSR block (columns are table dof
+// indices; only columns < n belong to the local matrix) or from a dense band array.
+// Factor layout (row-major band, W = 2b + 1 entries per row): d < b holds L[i][i-b+d],
+// d = b holds 1 / U[i][i], d > b holds U[i][i+d-b].
+// ------------------------------------------------------------------------------------------
+struct RowSource {
+  const int32_t* rowptr;  // nullptr: dense band rows in `val` (W entries per row)
+  const int32_t* colidx;
+  const double* val;
+};
+
+template <typename FT>
+__device__ inline void load_band_row_warp(int row, int n, int b, const RowSource& src, FT* dst) {
+  const int W = 2 * b + 1, lane = threadIdx.x & 31;
+  if (src.rowptr == nullptr) {
+    for (int d = lane; d < W; d += 32) dst[d] = (row < n) ? (FT)src.val[(int64_t)row * W + d] : (FT)0;
+    __syncwarp();
+    return;
+  }
+  for (int d = lane; d < W; d += 32) dst[d] = (FT)0;
+  __syncwarp();
+  if (row < n) {
+    const int k1 = src.rowptr[row + 1];
+    for (int k = src.rowptr[row] + lane; k < k1; k += 32) {
+      const int col = src.colidx[k];
+      if (col < n) dst[col - row + b] = (FT)src.val[k];
+    }
+  }
+  __syncwarp();
+}
+
+// Returns (to every thread) 0 on success, 1 if a pivot was zero or not finite.
+// smem: win [(b + 2) * (2b + 1)], rp [b + 2], flag [1].
+template <typename FT>
+__device__ int band_lu(int n, int b, const RowSource& src, FT* __restrict__ F, FT* win, FT* rp, int* flag) {
+  const int W = 2 * b + 1, R = b + 2;
+  const int tid = threadIdx.x, T = blockDim.x, wid = tid >> 5, nw = T >> 5;
+  if (n <= 0) return 0;
+  if (tid == 0) *flag = 0;
+  // rows 0..b into slots 0..b
+  for (int i = wid; i <= b; i += nw) load_band_row_warp<FT>(i, n, b, src, win + (i % R) * W);
+  __syncthreads();
+  if (tid == 0) {
+    const FT p = win[b];
+    if (!(p != (FT)0) || !isfinite((double)p)) *flag = 1;
+    rp[0] = (FT)1 / p;
+  }
+  __syncthreads();
+  const int bb = b * b;
+  const int dq = (b > 0) ? T / b : 0, dr = (b > 0) ? T % b : 0;
+  const int ri0 = (b > 0) ? tid / b : 0, cj0 = (b > 0) ? tid % b : 0;
+  for (int k = 0; k < n; ++k) {
+    const int sk = k % R;
+    const FT* rowk = win + sk * W;
+    const FT rpk = rp[sk];
+    const int lim = min(b, n - 1 - k);
+    // warp 0: write back row k (scaled L part, reciprocal pivot) and stage row k + b + 1
+    if (wid == 0) {
+      FT* out = F + (int64_t)k * W;
+      for (int d = tid; d < W; d += 32) {
+        const int j = k - b + d;
+        FT v = rowk[d];
+        if (d < b) v = (j >= 0) ? v * rp[j % R] : (FT)0;
+        else if (d == b) v = rpk;
+        out[d] = v;
+      }
+      load_band_row_warp<FT>(k + b + 1, n, b, src, win + ((k + b + 1) % R) * W);
+    }
+    // rank-1 update of rows k+1..k+lim, columns k+1..k+lim
+    if (lim > 0) {
+      const int base = (k + 1) % R;
+      int ri = ri0, cj = cj0;
+      for (int idx = tid; idx < bb; idx += T) {
+        if (ri < lim && cj < lim) {
+          int slot = base + ri;
+          if (slot >= R) slot -= R;
+          FT* rowi = win + slot * W;
+          const FT l = rowi[b - 1 - ri] * rpk;
+          const FT nv = rowi[cj - ri + b] - l * rowk[b + 1 + cj];
+          rowi[cj - ri + b] = nv;
+          if (idx == 0) {
+            if (!(nv != (FT)0) || !isfinite((double)nv)) *flag = 1;
+            rp[(k + 1) % R] = (FT)1 / nv;
+          }
+        }
+        cj += dr;
+        ri += dq;
+        if (cj >= b) {
+          cj -= b;
+          ri += 1;
+        }
+      }
+    } else if (tid == 0 && k + 1 < n) {
+      const FT nv = win[((k + 1) % R) * W + b];
+      if (!(nv != (FT)0) || !isfinite((double)nv)) *flag = 1;
+      rp[(k + 1) % R] = (FT)1 / nv;
+    }
+    __syncthreads();
+  }
+  return *flag;
+}
+
+// ------------------------------------------------------------------------------------------
+// Triangular solves with the band factors, in place on y[0..n) (shared memory).
+// ------------------------------------------------------------------------------------------
+template <typename FT>
+__device__ void band_solve(int n, int b, const FT* __restrict__ F, FT* y) {
+  const int W = 2 * b + 1, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  // forward: L (unit lower)
+  for (int k0 = 0; k0 < n; k0 += 32) {
+    const int kb = min(32, n - k0);
+    if (wid == 0) {
+      FT yl = (lane < kb) ? y[k0 + lane] : (FT)0;
+      FT Lrow[32];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const int d = j - lane + b;
+        Lrow[j] = (j < lane && lane < kb && d >= 0) ? F[(int64_t)(k0 + lane) * W + d] : (FT)0;
+      }
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const FT yj = __shfl_sync(0xffffffffu, yl, j);
+        if (j < kb) yl -= Lrow[j] * yj;
+      }
+      if (lane < kb) y[k0 + lane] = yl;
+    }
+    __syncthreads();
+    // rows k0+kb .. k0+kb+b-1 take the contribution of the finished block
+    for (int r = tid; r < b; r += blockDim.x) {
+      const int i = k0 + kb + r;
+      if (i < n) {
+        const int j0 = max(k0, i - b);
+        FT acc = 0;
+        const FT* Fi = F + (int64_t)i * W + (j0 - i + b);
+        for (int j = j0; j < k0 + kb; ++j) acc += Fi[j - j0] * y[j];
+        y[i] -= acc;
+      }
+    }
+    __syncthreads();
+  }
+  // backward: U (diagonal stored inverted)
+  for (int k1 = n; k1 > 0; k1 -= 32) {
+    const int k0 = max(0, k1 - 32), kb = k1 - k0;
+    if (wid == 0) {
+      FT yl = (lane < kb) ? y[k0 + lane] : (FT)0;
+      FT Urow[32];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const int d = j - lane + b;
+        Urow[j] = (j >= lane && lane < kb && j < kb && d <= 2 * b) ? F[(int64_t)(k0 + lane) * W + d] : (FT)0;
+      }
+#pragma unroll
+      for (int j = 31; j >= 0; --j) {
+        if (j < kb) {
+          // lane j finishes x_j = y_j / U_jj, then everyone above subtracts U[l][j] x_j
+          FT xj = (lane == j) ? yl * Urow[j] : (FT)0;
+          xj = __shfl_sync(0xffffffffu, xj, j);
+          if (lane == j) yl = xj;
+          else if (lane < j) yl -= Urow[j] * xj;
+        }
+      }
+      if (lane < kb) y[k0 + lane] = yl;
+    }
+    __syncthreads();
+    for (int r = tid; r < b; r += blockDim.x) {
+      const int i = k0 - 1 - r;
+      if (i >= 0) {
+        const int j1 = min(k1 - 1, i + b);
+        FT acc = 0;
+        const FT* Fi = F + (int64_t)i * W + (k0 - i + b);
+        for (int j = k0; j <= j1; ++j) acc += Fi[j - k0] * y[j];
+        y[i] -= acc;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace dev
+}  // namespace nls

@@ -1,0 +1,1684 @@
+// Device solver of the two-level nonlinear Schwarz method (sm_103a).
+//
+// Kernels:
+//   k_local_newton   one persistent launch per F_x evaluation: every overlapping subdomain
+//                    (longest first, pulled from a device work counter) runs its local
+//                    Newton loop for Eq. 4 -- colour-ordered element assembly of the FP64
+//                    residual and of the local Jacobian (CSR), sliding-window band LU in
+//                    FP32 or FP64, triangular solves with FP64 iterative refinement, Armijo
+//                    line search -- and refactors the Jacobian at the converged state for the
+//                    exact tangent (Eq. 6 / Eq. 12).  It writes P~_i T_i straight into F_x.
+//   k_local_apply    one CTA per subdomain: sum_i P~_i (R_i DF(v_i) P_i)^-1 R_i DF(v_i) y.
+//   k_harmonic       energy-minimising extension of the RGDSW interface values (setup).
+//   k_galerkin       per non-overlapping subdomain: Phi_j^T K^(j)(x) Phi_j (coarse matrix).
+//   k_coarse_*       band LU / solve of A_0 = P_0^T DF P_0 in one CTA (Eq. 9).
+//   k_global_*       colour-ordered global residual F(u) and Jacobian DF(u) (Eq. 3).
+//   k_vec_*          GMRES vector kernels with fixed-order (deterministic) reductions.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <stdexcept>
+#include <string>
+#include <type_traits>
+#include <vector>
+
+#include "device.cuh"
+#include "nls_internal.h"
+
+namespace nls {
+
+namespace {
+
+struct CudaFailure : std::runtime_error {
+  explicit CudaFailure(const std::string& s) : std::runtime_error(s) {}
+};
+
+#define CK(call)                                                                                  \
+  do {                                                                                            \
+    cudaError_t e_ = (call);                                                                      \
+    if (e_ != cudaSuccess) throw CudaFailure(std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+constexpr int kVecBlocks = 1216;  // 8 per SM on 152 SMs
+constexpr int kVecThreads = 256;
+constexpr int kVecWarps = kVecBlocks * (kVecThreads / 32);
+constexpr int kMaxGmresVecs = 128;
+
+enum LocalStatus { ST_OK = 0, ST_MAXIT = 1, ST_LS = 2, ST_NONFINITE = 3, ST_PIVOT = 4 };
+
+// ------------------------------------------------------------------------------------------
+// argument blocks
+// ------------------------------------------------------------------------------------------
+struct LocalArgs {
+  const SubMeta* meta;
+  const int32_t *tnode_gid, *elem_gid, *lconn, *color_ptr, *rowptr, *colidx, *epos;
+  const uint8_t* owned;
+  double* csr;
+  void* factor;
+  double* wbuf;
+  int32_t *its, *status;
+  const int32_t* order;
+  int32_t* queue;
+  const double *geom, *kcoef, *fext;
+  double mu, lam, load;
+  int ndof, nen, count, max_n, max_nt, max_b;
+  double rtol, atol, armijo, ir_rtol;
+  int maxit, ls_trials, ir_max;
+  const double* x;        // evaluation point (global)
+  double* out;            // F_x: owned entries receive x - w
+  const double* guess;    // optional start states (concatenated local vectors)
+  int want_tangent;
+  // tangent application
+  const double* v;
+  const double* add;
+  // coarse (harmonic extension / Galerkin)
+  const double* phi;
+  const int64_t* phi_off;
+  const int32_t* cj_ptr;
+  double* Y;
+  double* blk;
+  const int64_t* blk_off;
+};
+
+__host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// shared-memory plan (bytes) of the local kernels
+struct SmemPlan {
+  size_t xt, r, rt, s, red, yv, win, rp, flag, total;
+};
+
+template <typename FT>
+__host__ __device__ inline SmemPlan smem_plan(int max_n, int max_nt, int max_b, bool with_window) {
+  SmemPlan p;
+  size_t o = 0;
+  p.xt = o; o += sizeof(double) * max_nt;
+  p.r = o; o += sizeof(double) * max_n;
+  p.rt = o; o += sizeof(double) * max_n;
+  p.s = o; o += sizeof(double) * max_n;
+  p.red = o; o += sizeof(double) * 40;
+  p.yv = o; o += align_up(sizeof(FT) * max_n, 16);
+  p.win = o; o += with_window ? align_up(sizeof(FT) * (size_t)(max_b + 2) * (2 * max_b + 1), 16) : 0;
+  p.rp = o; o += with_window ? align_up(sizeof(FT) * (max_b + 2), 16) : 0;
+  p.flag = o; o += 16;
+  p.total = o;
+  return p;
+}
+
+// ------------------------------------------------------------------------------------------
+// local assembly (colour-ordered, deterministic)
+// ------------------------------------------------------------------------------------------
+template <int LAW>
+__device__ bool local_residual(const LocalArgs& A, const SubMeta& m, const double* xt, double* r) {
+  const int nd = A.ndof, nen = A.nen;
+  for (int a = threadIdx.x; a < m.n; a += blockDim.x) {
+    const int64_t g = (int64_t)A.tnode_gid[m.tnode_off + a / nd] * nd + a % nd;
+    r[a] = -A.load * A.fext[g];
+  }
+  __syncthreads();
+  bool ok = true;
+  const int32_t* cp = A.color_ptr + m.color_off;
+  for (int c = 0; c < m.ncolor; ++c) {
+    for (int e = cp[c] + threadIdx.x; e < cp[c + 1]; e += blockDim.x) {
+      const int64_t le = m.elem_off + e;
+      const int32_t gid = A.elem_gid[le];
+      const int32_t* lc = A.lconn + le * nen;
+      if (LAW == NLS_LAW_DIFFUSION) {
+        const double* geo = A.geom + (int64_t)gid * 8;
+        const dev::P1State st = dev::p1_state(geo, A.kcoef[gid], xt[lc[0]], xt[lc[1]], xt[lc[2]]);
+        double re[3];
+        dev::p1_residual(geo, st, re);
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+          if (lc[a] < m.nV) r[lc[a]] += re[a];
+      } else {
+        const double* geo = A.geom + (int64_t)gid * 40;
+        double ue[8], re[8];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          ue[2 * a] = xt[2 * lc[a]];
+          ue[2 * a + 1] = xt[2 * lc[a] + 1];
+        }
+        bool eok = true;
+        dev::nh_residual(geo, ue, A.mu, A.lam, re, eok);
+        ok = ok && eok;
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+          if (lc[a] < m.nV) {
+            r[2 * lc[a]] += re[2 * a];
+            r[2 * lc[a] + 1] += re[2 * a + 1];
+          }
+      }
+    }
+    __syncthreads();
+  }
+  return __syncthreads_and(ok ? 1 : 0) != 0;
+}
+
+// Local Jacobian into the CSR block of the subdomain (rows per m.nrows).
+template <int LAW, typename JT>
+__device__ void local_jacobian(const LocalArgs& A, const SubMeta& m, const double* xt, double* csr) {
+  const int nen = A.nen, ned = nen * A.ndof, ned2 = ned * ned;
+  for (int64_t k = threadIdx.x; k < m.nnz; k += blockDim.x) csr[k] = 0.0;
+  __syncthreads();
+  const int32_t* cp = A.color_ptr + m.color_off;
+  for (int c = 0; c < m.ncolor; ++c) {
+    for (int e = cp[c] + threadIdx.x; e < cp[c + 1]; e += blockDim.x) {
+      const int64_t le = m.elem_off + e;
+      const int32_t gid = A.elem_gid[le];
+      const int32_t* lc = A.lconn + le * nen;
+      const int32_t* ep = A.epos + m.epos_off + (int64_t)e * ned2;
+      if (LAW == NLS_LAW_DIFFUSION) {
+        const double* geo = A.geom + (int64_t)gid * 8;
+        const dev::P1State st = dev::p1_state(geo, A.kcoef[gid], xt[lc[0]], xt[lc[1]], xt[lc[2]]);
+        double K[9];
+        dev::p1_jacobian<double>(geo, st, K);
+#pragma unroll
+        for (int q = 0; q < 9; ++q)
+          if (ep[q] >= 0) csr[ep[q]] += K[q];
+      } else {
+        const double* geo = A.geom + (int64_t)gid * 40;
+        double ue[8];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          ue[2 * a] = xt[2 * lc[a]];
+          ue[2 * a + 1] = xt[2 * lc[a] + 1];
+        }
+        JT K[64];
+        dev::nh_jacobian<JT>(geo, ue, A.mu, A.lam, K);
+#pragma unroll
+        for (int q = 0; q < 64; ++q)
+          if (ep[q] >= 0) csr[ep[q]] += (double)K[q];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// s = J^-1 rhs with the band factors, then FP64 iterative refinement against the CSR matrix
+// (columns < n) when the factors are FP32.  `res` is an n-vector of scratch.
+template <typename FT>
+__device__ int local_solve(const LocalArgs& A, const SubMeta& m, const int32_t* rowptr, const int32_t* colidx,
+                           const double* csr, const FT* F, const double* rhs, double rhs_norm, double* s, double* res,
+                           FT* yv, double* red) {
+  const int n = m.n;
+  for (int a = threadIdx.x; a < n; a += blockDim.x) yv[a] = (FT)rhs[a];
+  __syncthreads();
+  dev::band_solve<FT>(n, m.b, F, yv);
+  for (int a = threadIdx.x; a < n; a += blockDim.x) s[a] = (double)yv[a];
+  __syncthreads();
+  int sweeps = 0;
+  if (sizeof(FT) == 4) {
+    for (int sw = 0; sw < A.ir_max; ++sw) {
+      double loc = 0.0;
+      for (int a = threadIdx.x; a < n; a += blockDim.x) {
+        double acc = rhs[a];
+        for (int k = rowptr[a]; k < rowptr[a + 1]; ++k) {
+          const int col = colidx[k];
+          if (col < n) acc -= csr[k] * s[col];
+        }
+        res[a] = acc;
+        loc += acc * acc;
+      }
+      const double rn = sqrt(dev::block_sum(loc, red));
+      if (!(rn > A.ir_rtol * rhs_norm)) break;
+      for (int a = threadIdx.x; a < n; a += blockDim.x) yv[a] = (FT)res[a];
+      __syncthreads();
+      dev::band_solve<FT>(n, m.b, F, yv);
+      for (int a = threadIdx.x; a < n; a += blockDim.x) s[a] += (double)yv[a];
+      __syncthreads();
+      ++sweeps;
+    }
+  }
+  return sweeps;
+}
+
+// ------------------------------------------------------------------------------------------
+// k_local_newton: the batched local corrections T_i of Eq. 4
+// ------------------------------------------------------------------------------------------
+template <int LAW, typename FT>
+__global__ void __launch_bounds__(1024) k_local_newton(LocalArgs A) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const SmemPlan P = smem_plan<FT>(A.max_n, A.max_nt, A.max_b, true);
+  double* xt = (double*)(smem + P.xt);
+  double* r = (double*)(smem + P.r);
+  double* rt = (double*)(smem + P.rt);
+  double* s = (double*)(smem + P.s);
+  double* red = (double*)(smem + P.red);
+  FT* yv = (FT*)(smem + P.yv);
+  FT* win = (FT*)(smem + P.win);
+  FT* rp = (FT*)(smem + P.rp);
+  int* flag = (int*)(smem + P.flag);
+  __shared__ int s_item;
+  using JT = typename std::conditional<LAW == NLS_LAW_DIFFUSION, double, FT>::type;
+  const int tid = threadIdx.x, nd = A.ndof;
+  for (;;) {
+    if (tid == 0) s_item = atomicAdd(A.queue, 1);
+    __syncthreads();
+    const int item = s_item;
+    __syncthreads();
+    if (item >= A.count) break;
+    const int sub = A.order[item];
+    const SubMeta m = A.meta[sub];
+    const int n = m.n;
+    const int32_t* rowptr = A.rowptr + m.rowptr_off;
+    const int32_t* colidx = A.colidx + m.nnz_off;
+    double* csr = A.csr + m.nnz_off;
+    FT* F = (FT*)A.factor + m.factor_off;
+    double* wb = A.wbuf + m.vec_off;
+    for (int t = tid; t < m.nt; t += blockDim.x)
+      xt[t] = A.x[(int64_t)A.tnode_gid[m.tnode_off + t / nd] * nd + t % nd];
+    __syncthreads();
+    if (A.guess)
+      for (int a = tid; a < n; a += blockDim.x) xt[a] = A.guess[m.vec_off + a];
+    __syncthreads();
+    bool ok = local_residual<LAW>(A, m, xt, r);
+    double loc = 0.0;
+    for (int a = tid; a < n; a += blockDim.x) loc += r[a] * r[a];
+    double rn = sqrt(dev::block_sum(loc, red));
+    if (!ok) rn = INFINITY;
+    const double tol = fmax(A.atol, A.rtol * rn);
+    int its = 0, status = ST_OK;
+    if (!isfinite(rn)) status = ST_NONFINITE;
+    while (status == ST_OK && rn > tol) {
+      if (its >= A.maxit) {
+        status = ST_MAXIT;
+        break;
+      }
+      local_jacobian<LAW, JT>(A, m, xt, csr);
+      dev::RowSource src{rowptr, colidx, csr};
+      if (dev::band_lu<FT>(n, m.b, src, F, win, rp, flag)) {
+        status = ST_PIVOT;
+        break;
+      }
+      local_solve<FT>(A, m, rowptr, colidx, csr, F, r, rn, s, rt, yv, red);
+      for (int a = tid; a < n; a += blockDim.x) wb[a] = xt[a];
+      __syncthreads();
+      double alpha = 1.0, rtn = INFINITY;
+      bool accepted = false;
+      for (int trial = 0; trial < A.ls_trials; ++trial) {
+        for (int a = tid; a < n; a += blockDim.x) xt[a] = wb[a] - alpha * s[a];
+        __syncthreads();
+        const bool tok = local_residual<LAW>(A, m, xt, rt);
+        double l2 = 0.0;
+        for (int a = tid; a < n; a += blockDim.x) l2 += rt[a] * rt[a];
+        rtn = sqrt(dev::block_sum(l2, red));
+        if (!tok) rtn = INFINITY;
+        if (isfinite(rtn) && rtn <= (1.0 - A.armijo * alpha) * rn) {
+          accepted = true;
+          break;
+        }
+        alpha *= 0.5;
+      }
+      ++its;
+      if (!accepted) {
+        for (int a = tid; a < n; a += blockDim.x) xt[a] = wb[a];
+        __syncthreads();
+        status = ST_LS;
+        break;
+      }
+      double* tmp = r;
+      r = rt;
+      rt = tmp;
+      rn = rtn;
+    }
+    if (A.want_tangent && status != ST_NONFINITE && status != ST_PIVOT) {
+      local_jacobian<LAW, JT>(A, m, xt, csr);
+      dev::RowSource src{rowptr, colidx, csr};
+      if (dev::band_lu<FT>(n, m.b, src, F, win, rp, flag)) status = ST_PIVOT;
+    }
+    for (int a = tid; a < n; a += blockDim.x) {
+      wb[a] = xt[a];
+      if (A.owned[m.vec_off + a]) {
+        const int64_t g = (int64_t)A.tnode_gid[m.tnode_off + a / nd] * nd + a % nd;
+        A.out[g] = A.x[g] - xt[a];
+      }
+    }
+    if (tid == 0) {
+      A.its[sub] = its;
+      A.status[sub] = status;
+    }
+    __syncthreads();
+    // restore the ping-pong buffers for the next subdomain
+    r = (double*)(smem + P.r);
+    rt = (double*)(smem + P.rt);
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// k_local_apply: out[owned] = (R_i DF(v_i) P_i)^-1 R_i DF(v_i) v  (+ add[owned])
+// ------------------------------------------------------------------------------------------
+template <typename FT>
+__global__ void __launch_bounds__(1024) k_local_apply(LocalArgs A) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const SmemPlan P = smem_plan<FT>(A.max_n, A.max_nt, A.max_b, false);
+  double* yt = (double*)(smem + P.xt);
+  double* q = (double*)(smem + P.r);
+  double* res = (double*)(smem + P.rt);
+  double* z = (double*)(smem + P.s);
+  double* red = (double*)(smem + P.red);
+  FT* yv = (FT*)(smem + P.yv);
+  const int sub = blockIdx.x, tid = threadIdx.x, nd = A.ndof;
+  const SubMeta m = A.meta[sub];
+  const int n = m.n;
+  const int32_t* rowptr = A.rowptr + m.rowptr_off;
+  const int32_t* colidx = A.colidx + m.nnz_off;
+  const double* csr = A.csr + m.nnz_off;
+  const FT* F = (const FT*)A.factor + m.factor_off;
+  for (int t = tid; t < m.nt; t += blockDim.x) yt[t] = A.v[(int64_t)A.tnode_gid[m.tnode_off + t / nd] * nd + t % nd];
+  __syncthreads();
+  double loc = 0.0;
+  for (int a = tid; a < n; a += blockDim.x) {
+    double acc = 0.0;
+    for (int k = rowptr[a]; k < rowptr[a + 1]; ++k) acc += csr[k] * yt[colidx[k]];
+    q[a] = acc;
+    loc += acc * acc;
+  }
+  const double qn = sqrt(dev::block_sum(loc, red));
+  local_solve<FT>(A, m, rowptr, colidx, csr, F, q, qn, z, res, yv, red);
+  for (int a = tid; a < n; a += blockDim.x)
+    if (A.owned[m.vec_off + a]) {
+      const int64_t g = (int64_t)A.tnode_gid[m.tnode_off + a / nd] * nd + a % nd;
+      A.out[g] = z[a] + (A.add ? A.add[g] : 0.0);
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// coarse space: harmonic extension (setup) and Galerkin blocks
+// ------------------------------------------------------------------------------------------
+template <int LAW>
+__global__ void __launch_bounds__(1024) k_harmonic(LocalArgs A) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const SmemPlan P = smem_plan<double>(A.max_n, A.max_nt, A.max_b, true);
+  double* xt = (double*)(smem + P.xt);
+  double* q = (double*)(smem + P.r);
+  double* red = (double*)(smem + P.red);
+  double* yv = (double*)(smem + P.yv);
+  double* win = (double*)(smem + P.win);
+  double* rp = (double*)(smem + P.rp);
+  int* flag = (int*)(smem + P.flag);
+  const int j = blockIdx.x, tid = threadIdx.x, nd = A.ndof;
+  const SubMeta m = A.meta[j];
+  const int n = m.n;
+  const int nc = A.cj_ptr[j + 1] - A.cj_ptr[j];
+  double* phi = const_cast<double*>(A.phi) + A.phi_off[j];
+  if (tid == 0) A.status[j] = ST_OK;
+  const int32_t* rowptr = A.rowptr + m.rowptr_off;
+  const int32_t* colidx = A.colidx + m.nnz_off;
+  double* csr = A.csr + m.nnz_off;
+  double* F = (double*)A.factor + m.factor_off;
+  for (int t = tid; t < m.nt; t += blockDim.x) xt[t] = A.x[(int64_t)A.tnode_gid[m.tnode_off + t / nd] * nd + t % nd];
+  __syncthreads();
+  local_jacobian<LAW, double>(A, m, xt, csr);
+  if (n == 0 || nc == 0) return;
+  dev::RowSource src{rowptr, colidx, csr};
+  if (dev::band_lu<double>(n, m.b, src, F, win, rp, flag)) {
+    if (tid == 0) A.status[j] = ST_PIVOT;
+    return;
+  }
+  for (int lc = 0; lc < nc; ++lc) {
+    for (int a = tid; a < n; a += blockDim.x) {
+      double acc = 0.0;
+      for (int k = rowptr[a]; k < rowptr[a + 1]; ++k) {
+        const int col = colidx[k];
+        if (col >= n) acc -= csr[k] * phi[(int64_t)col * nc + lc];
+      }
+      yv[a] = acc;
+    }
+    __syncthreads();
+    dev::band_solve<double>(n, m.b, F, yv);
+    for (int a = tid; a < n; a += blockDim.x) phi[(int64_t)a * nc + lc] = yv[a];
+    __syncthreads();
+  }
+  (void)q;
+  (void)red;
+}
+
+template <int LAW, typename JT>
+__global__ void __launch_bounds__(1024) k_galerkin(LocalArgs A) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const SmemPlan P = smem_plan<double>(A.max_n, A.max_nt, A.max_b, false);
+  double* xt = (double*)(smem + P.xt);
+  const int j = blockIdx.x, tid = threadIdx.x, nd = A.ndof;
+  const SubMeta m = A.meta[j];
+  const int nc = A.cj_ptr[j + 1] - A.cj_ptr[j];
+  const double* phi = A.phi + A.phi_off[j];
+  double* Y = A.Y + A.phi_off[j];
+  const int32_t* rowptr = A.rowptr + m.rowptr_off;
+  const int32_t* colidx = A.colidx + m.nnz_off;
+  double* csr = A.csr + m.nnz_off;
+  for (int t = tid; t < m.nt; t += blockDim.x) xt[t] = A.x[(int64_t)A.tnode_gid[m.tnode_off + t / nd] * nd + t % nd];
+  __syncthreads();
+  local_jacobian<LAW, JT>(A, m, xt, csr);
+  if (nc == 0) return;
+  // Y = K^(j) Phi_j
+  for (int64_t idx = tid; idx < (int64_t)m.nt * nc; idx += blockDim.x) {
+    const int t = (int)(idx / nc), lc = (int)(idx % nc);
+    double acc = 0.0;
+    for (int k = rowptr[t]; k < rowptr[t + 1]; ++k) acc += csr[k] * phi[(int64_t)colidx[k] * nc + lc];
+    Y[idx] = acc;
+  }
+  __syncthreads();
+  // block = Phi_j^T Y, one warp per entry, fixed-order lane sums
+  const int lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+  double* blk = A.blk + A.blk_off[j];
+  for (int e = wid; e < nc * nc; e += nw) {
+    const int c = e / nc, d = e % nc;
+    double acc = 0.0;
+    for (int t = lane; t < m.nt; t += 32) acc += phi[(int64_t)t * nc + c] * Y[(int64_t)t * nc + d];
+    acc = dev::warp_sum(acc);
+    if (lane == 0) blk[e] = acc;
+  }
+}
+
+__global__ void k_a0_gather(int64_t nentries, const int32_t* ptr, const int64_t* src, const double* blk, double* A0) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nentries; e += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int32_t k = ptr[e]; k < ptr[e + 1]; ++k) acc += blk[src[k]];
+    A0[e] = acc;
+  }
+}
+
+__global__ void k_gather_values(int64_t n, const int64_t* src, const double* from, double* to) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+    to[k] = from[src[k]];
+}
+
+__global__ void k_gather_values32(int64_t n, const int32_t* src, const double* from, double* to) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+    to[k] = from[src[k]];
+}
+
+// coarse band factorization (one CTA)
+template <typename FT>
+__global__ void __launch_bounds__(1024) k_coarse_factor(int N0, int b0, const double* A0, FT* F, int* status) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  FT* win = (FT*)smem;
+  FT* rp = win + (size_t)(b0 + 2) * (2 * b0 + 1);
+  int* flag = (int*)(rp + b0 + 2);
+  dev::RowSource src{nullptr, nullptr, A0};
+  const int bad = dev::band_lu<FT>(N0, b0, src, F, win, rp, flag);
+  if (threadIdx.x == 0) *status = bad ? ST_PIVOT : ST_OK;
+}
+
+// coarse solve z = A0^-1 g (global-memory vectors), FP64 refinement against the band A0
+template <typename FT>
+__global__ void __launch_bounds__(1024) k_coarse_solve(int N0, int b0, const double* A0, const FT* F, const double* g,
+                                                       double* z, double* res, FT* y, double ir_rtol, int ir_max) {
+  __shared__ double red[40];
+  const int W = 2 * b0 + 1;
+  double loc = 0.0;
+  for (int a = threadIdx.x; a < N0; a += blockDim.x) {
+    y[a] = (FT)g[a];
+    loc += g[a] * g[a];
+  }
+  const double gn = sqrt(dev::block_sum(loc, red));
+  dev::band_solve<FT>(N0, b0, F, y);
+  for (int a = threadIdx.x; a < N0; a += blockDim.x) z[a] = (double)y[a];
+  __syncthreads();
+  if (sizeof(FT) == 4) {
+    for (int sw = 0; sw < ir_max; ++sw) {
+      double l2 = 0.0;
+      for (int a = threadIdx.x; a < N0; a += blockDim.x) {
+        double acc = g[a];
+        for (int d = 0; d < W; ++d) {
+          const int col = a - b0 + d;
+          if (col >= 0 && col < N0) acc -= A0[(int64_t)a * W + d] * z[col];
+        }
+        res[a] = acc;
+        l2 += acc * acc;
+      }
+      const double rn = sqrt(dev::block_sum(l2, red));
+      if (!(rn > ir_rtol * gn)) break;
+      for (int a = threadIdx.x; a < N0; a += blockDim.x) y[a] = (FT)res[a];
+      __syncthreads();
+      dev::band_solve<FT>(N0, b0, F, y);
+      for (int a = threadIdx.x; a < N0; a += blockDim.x) z[a] += (double)y[a];
+      __syncthreads();
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// global assembly (colour passes: elements of one colour share no node)
+// ------------------------------------------------------------------------------------------
+template <int LAW>
+__global__ void k_global_residual(const int32_t* elems, int e0, int e1, const int32_t* conn, const double* geom,
+                                  const double* kcoef, const double* x, double* F, double mu, double lam, int* bad) {
+  for (int i = e0 + blockIdx.x * blockDim.x + threadIdx.x; i < e1; i += gridDim.x * blockDim.x) {
+    const int32_t e = elems[i];
+    if (LAW == NLS_LAW_DIFFUSION) {
+      const int32_t* c = conn + (int64_t)e * 3;
+      const double* geo = geom + (int64_t)e * 8;
+      const dev::P1State st = dev::p1_state(geo, kcoef[e], x[c[0]], x[c[1]], x[c[2]]);
+      double re[3];
+      dev::p1_residual(geo, st, re);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) F[c[a]] += re[a];
+    } else {
+      const int32_t* c = conn + (int64_t)e * 4;
+      const double* geo = geom + (int64_t)e * 40;
+      double ue[8], re[8];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        ue[2 * a] = x[2 * (int64_t)c[a]];
+        ue[2 * a + 1] = x[2 * (int64_t)c[a] + 1];
+      }
+      bool ok = true;
+      dev::nh_residual(geo, ue, mu, lam, re, ok);
+      if (!ok) *bad = 1;
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        F[2 * (int64_t)c[a]] += re[2 * a];
+        F[2 * (int64_t)c[a] + 1] += re[2 * a + 1];
+      }
+    }
+  }
+}
+
+template <int LAW, typename JT>
+__global__ void k_global_jacobian(const int32_t* elems, int e0, int e1, const int32_t* conn, const double* geom,
+                                  const double* kcoef, const double* x, const int32_t* epos, double* val, double mu,
+                                  double lam) {
+  for (int i = e0 + blockIdx.x * blockDim.x + threadIdx.x; i < e1; i += gridDim.x * blockDim.x) {
+    const int32_t e = elems[i];
+    if (LAW == NLS_LAW_DIFFUSION) {
+      const int32_t* c = conn + (int64_t)e * 3;
+      const double* geo = geom + (int64_t)e * 8;
+      const dev::P1State st = dev::p1_state(geo, kcoef[e], x[c[0]], x[c[1]], x[c[2]]);
+      double K[9];
+      dev::p1_jacobian<double>(geo, st, K);
+      const int32_t* ep = epos + (int64_t)e * 9;
+#pragma unroll
+      for (int q = 0; q < 9; ++q) val[ep[q]] += K[q];
+    } else {
+      const int32_t* c = conn + (int64_t)e * 4;
+      const double* geo = geom + (int64_t)e * 40;
+      double ue[8];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        ue[2 * a] = x[2 * (int64_t)c[a]];
+        ue[2 * a + 1] = x[2 * (int64_t)c[a] + 1];
+      }
+      JT K[64];
+      dev::nh_jacobian<JT>(geo, ue, mu, lam, K);
+      const int32_t* ep = epos + (int64_t)e * 64;
+#pragma unroll
+      for (int q = 0; q < 64; ++q) val[ep[q]] += (double)K[q];
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// vector kernels
+// ------------------------------------------------------------------------------------------
+__global__ void k_axpby(int64_t n, double a, const double* x, double b, const double* y, double* z) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    z[i] = a * x[i] + (y ? b * y[i] : 0.0);
+}
+
+__global__ void k_init_residual(int64_t n, double load, const double* fext, double* F) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    F[i] = -load * fext[i];
+}
+
+__global__ void k_mask(int64_t n, const uint8_t* free_dof, double* x) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    if (!free_dof[i]) x[i] = 0.0;
+}
+
+__global__ void k_set_dirichlet(int64_t n, const uint8_t* free_dof, const double* ubc, double* x) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    if (!free_dof[i]) x[i] = ubc[i];
+}
+
+// y = J x on free rows (0 on Dirichlet rows)
+__global__ void k_spmv_free(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val,
+                            const uint8_t* free_dof, const double* x, double* y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    if (free_dof[i])
+      for (int32_t k = rowptr[i]; k < rowptr[i + 1]; ++k) acc += val[k] * x[col[k]];
+    y[i] = acc;
+  }
+}
+
+// y = a * x + s * (P0 c)
+__global__ void k_p0_apply(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val, const double* c,
+                           double a, const double* x, double s, double* y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int32_t k = rowptr[i]; k < rowptr[i + 1]; ++k) acc += val[k] * c[col[k]];
+    y[i] = (x ? a * x[i] : 0.0) + s * acc;
+  }
+}
+
+// g = P0^T v, one warp per coarse row
+__global__ void k_p0t_apply(int n0, const int32_t* rowptr, const int32_t* col, const double* val, const double* v,
+                            double* g) {
+  const int lane = threadIdx.x & 31;
+  for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < n0; r += (gridDim.x * blockDim.x) >> 5) {
+    double acc = 0.0;
+    for (int32_t k = rowptr[r] + lane; k < rowptr[r + 1]; k += 32) acc += val[k] * v[col[k]];
+    acc = dev::warp_sum(acc);
+    if (lane == 0) g[r] = acc;
+  }
+}
+
+// per-warp partial dot products of `nv` vectors (stride ld) with w
+__global__ void k_multidot_partial(int64_t n, int nv, const double* V, int64_t ld, const double* w, double* partial) {
+  const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int i = 0; i < nv; ++i) {
+    const double* vi = V + (int64_t)i * ld;
+    double acc = 0.0;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += stride) acc += vi[k] * w[k];
+    acc = dev::warp_sum(acc);
+    if (lane == 0) partial[(int64_t)i * kVecWarps + gw] = acc;
+  }
+}
+
+__global__ void k_partial_final(int nv, const double* partial, double* out) {
+  __shared__ double red[40];
+  for (int i = blockIdx.x; i < nv; i += gridDim.x) {
+    double acc = 0.0;
+    for (int k = threadIdx.x; k < kVecWarps; k += blockDim.x) acc += partial[(int64_t)i * kVecWarps + k];
+    acc = dev::block_sum(acc, red);
+    if (threadIdx.x == 0) out[i] = acc;
+    __syncthreads();
+  }
+}
+
+// w -= sum_i coef[i] V_i
+__global__ void k_multiaxpy(int64_t n, int nv, const double* V, int64_t ld, const double* coef, double sign, double* w) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int i = 0; i < nv; ++i) acc += coef[i] * V[(int64_t)i * ld + k];
+    w[k] += sign * acc;
+  }
+}
+
+__global__ void k_scale_inv(int64_t n, const double* x, const double* nrm, double* y) {
+  const double s = 1.0 / *nrm;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = x[i] * s;
+}
+
+__global__ void k_sqrt_inplace(double* x) { *x = sqrt(*x); }
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------------
+// device state
+// ------------------------------------------------------------------------------------------
+struct Dev {
+  cudaStream_t s = nullptr;
+  std::vector<void*> allocs;
+  int64_t bytes = 0;
+  int64_t launches = 0;
+  int nsm = 152;
+  size_t smem_optin = 0;
+  template <typename T>
+  T* alloc(size_t n) {
+    void* p = nullptr;
+    if (n == 0) n = 1;
+    CK(cudaMalloc(&p, n * sizeof(T)));
+    allocs.push_back(p);
+    bytes += (int64_t)(n * sizeof(T));
+    return (T*)p;
+  }
+  template <typename T>
+  T* upload(const std::vector<T>& v) {
+    T* p = alloc<T>(v.size());
+    if (!v.empty()) CK(cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+    return p;
+  }
+  void release(void* p) {
+    for (auto& q : allocs)
+      if (q == p) {
+        cudaFree(q);
+        q = nullptr;
+      }
+  }
+  // mesh
+  int32_t *conn = nullptr, *g_elem = nullptr, *g_rowptr = nullptr, *g_col = nullptr, *g_epos = nullptr;
+  double *geom = nullptr, *kcoef = nullptr, *fext = nullptr, *ubc = nullptr, *g_val = nullptr;
+  uint8_t* free_dof = nullptr;
+  DeviceLocalSet ov, nov;
+  // coarse
+  int32_t *p0_rowptr = nullptr, *p0_col = nullptr, *p0t_rowptr = nullptr, *p0t_col = nullptr, *p0t_src = nullptr;
+  int64_t* p0_src = nullptr;
+  double *p0_val = nullptr, *p0t_val = nullptr, *phi = nullptr, *Y = nullptr, *blk = nullptr, *A0 = nullptr;
+  int64_t *phi_off = nullptr, *blk_off = nullptr, *a0_src = nullptr;
+  int32_t *cj_ptr = nullptr, *a0_ptr = nullptr;
+  void* A0f = nullptr;
+  int32_t* cstatus = nullptr;
+  // vectors
+  double *u = nullptr, *x = nullptr, *u0 = nullptr, *Fx = nullptr, *F = nullptr, *t1 = nullptr, *t2 = nullptr,
+         *w0 = nullptr, *gx = nullptr;
+  double *c = nullptr, *ct = nullptr, *dc = nullptr, *g = nullptr, *gt = nullptr, *cres = nullptr;
+  void* cy = nullptr;
+  double *V = nullptr, *partial = nullptr, *scal = nullptr, *coef = nullptr;
+  int* bad = nullptr;
+  double* h_scal = nullptr;  // pinned
+  int m = 0;                 // GMRES restart length allocated
+  bool tangent_ready = false;
+  double last_load = 1.0;
+  // per-launch CUDA-event timing (nls_options.profile_kernels)
+  bool prof = false;
+  struct EvRec {
+    cudaEvent_t a, b;
+    const char* name;
+  };
+  std::vector<EvRec> evs;
+  size_t ev_used = 0;
+  struct Stat {
+    std::string name;
+    int64_t launches;
+    double ms;
+  };
+  std::vector<Stat> stats;
+  void prof_begin(const char* name) {
+    if (ev_used == evs.size()) {
+      EvRec r;
+      CK(cudaEventCreate(&r.a));
+      CK(cudaEventCreate(&r.b));
+      evs.push_back(r);
+    }
+    evs[ev_used].name = name;
+    CK(cudaEventRecord(evs[ev_used].a, s));
+  }
+  void prof_end() {
+    CK(cudaEventRecord(evs[ev_used].b, s));
+    ++ev_used;
+    if (ev_used >= 65536) prof_flush();
+  }
+  void prof_flush() {
+    if (!ev_used) return;
+    CK(cudaStreamSynchronize(s));
+    for (size_t i = 0; i < ev_used; ++i) {
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, evs[i].a, evs[i].b));
+      Stat* st = nullptr;
+      for (auto& x : stats)
+        if (x.name == evs[i].name) st = &x;
+      if (!st) {
+        stats.push_back(Stat{evs[i].name, 0, 0.0});
+        st = &stats.back();
+      }
+      st->launches += 1;
+      st->ms += ms;
+    }
+    ev_used = 0;
+  }
+};
+
+namespace {
+
+inline int grid_for(int64_t n, int threads = 256) {
+  int64_t b = (n + threads - 1) / threads;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(b, kVecBlocks));
+}
+
+#define LAUNCH(D, kernel, grid, block, smem, ...)                          \
+  do {                                                                     \
+    const bool prof_ = (D).prof;                                           \
+    if (prof_) (D).prof_begin(#kernel);                                    \
+    kernel<<<(grid), (block), (smem), (D).s>>>(__VA_ARGS__);               \
+    if (prof_) (D).prof_end();                                             \
+    (D).launches += 1;                                                     \
+    CK(cudaGetLastError());                                                \
+  } while (0)
+
+int local_threads(const Context& c) {
+  if (c.opt.threads_per_block) return c.opt.threads_per_block;
+  return c.ndof == 1 ? 256 : 512;
+}
+
+bool fp32_local(const Context& c) { return c.opt.local_precision == NLS_PREC_FP32_IR; }
+bool fp32_coarse(const Context& c) { return c.opt.coarse_precision == NLS_PREC_FP32_IR; }
+
+LocalArgs make_args(const Context& c, const LocalSet& hs, const DeviceLocalSet& ds) {
+  LocalArgs A;
+  std::memset(&A, 0, sizeof(A));
+  Dev& D = *c.dev;
+  A.meta = ds.meta;
+  A.tnode_gid = ds.tnode_gid;
+  A.elem_gid = ds.elem_gid;
+  A.lconn = ds.lconn;
+  A.color_ptr = ds.color_ptr;
+  A.rowptr = ds.rowptr;
+  A.colidx = ds.colidx;
+  A.epos = ds.epos;
+  A.owned = ds.owned;
+  A.csr = ds.csr_val;
+  A.factor = ds.factor;
+  A.wbuf = ds.w;
+  A.its = ds.its;
+  A.status = ds.status;
+  A.order = ds.order;
+  A.queue = ds.queue;
+  A.geom = D.geom;
+  A.kcoef = D.kcoef;
+  A.fext = D.fext;
+  const double E = c.young, nu = c.poisson;
+  A.mu = E / (2.0 * (1.0 + nu));
+  A.lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+  A.load = 1.0;
+  A.ndof = c.ndof;
+  A.nen = c.nen;
+  A.count = hs.count;
+  A.max_n = hs.max_n;
+  A.max_nt = hs.max_nt;
+  A.max_b = hs.max_b;
+  A.rtol = c.opt.inner_rtol;
+  A.atol = c.opt.inner_atol;
+  A.armijo = c.opt.armijo;
+  A.ir_rtol = c.opt.ir_rtol;
+  A.maxit = c.opt.inner_maxit;
+  A.ls_trials = c.opt.ls_trials;
+  A.ir_max = c.opt.ir_max_sweeps;
+  return A;
+}
+
+// Allow the kernel the whole opt-in shared memory minus its static shared memory.
+template <typename K>
+void set_smem(K kernel, size_t optin) {
+  cudaFuncAttributes fa;
+  CK(cudaFuncGetAttributes(&fa, kernel));
+  const size_t dyn = optin > fa.sharedSizeBytes ? optin - fa.sharedSizeBytes : 0;
+  CK(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+}
+
+void sync(Dev& D) { CK(cudaStreamSynchronize(D.s)); }
+
+// ---- reductions with a host read-back ---------------------------------------------------------
+double dot(Dev& D, int64_t n, const double* x, const double* y) {
+  LAUNCH(D, k_multidot_partial, kVecBlocks, kVecThreads, 0, n, 1, x, (int64_t)0, y, D.partial);
+  LAUNCH(D, k_partial_final, 1, 256, 0, 1, D.partial, D.scal);
+  CK(cudaMemcpyAsync(D.h_scal, D.scal, sizeof(double), cudaMemcpyDeviceToHost, D.s));
+  sync(D);
+  return D.h_scal[0];
+}
+
+double norm2(Dev& D, int64_t n, const double* x) { return std::sqrt(std::max(0.0, dot(D, n, x, x))); }
+
+// ---- global residual / Jacobian ------------------------------------------------------------
+void global_residual(Context& c, const double* x, double* F, double load) {
+  Dev& D = *c.dev;
+  const double E = c.young, nu = c.poisson;
+  const double mu = E / (2.0 * (1.0 + nu)), lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+  LAUNCH(D, k_init_residual, grid_for(c.N), 256, 0, c.N, load, D.fext, F);
+  for (size_t k = 0; k + 1 < c.g_color_ptr.size(); ++k) {
+    const int e0 = c.g_color_ptr[k], e1 = c.g_color_ptr[k + 1];
+    if (c.law == NLS_LAW_DIFFUSION)
+      LAUNCH(D, k_global_residual<NLS_LAW_DIFFUSION>, grid_for(e1 - e0), 256, 0, D.g_elem, e0, e1, D.conn, D.geom,
+             D.kcoef, x, F, mu, lam, D.bad);
+    else
+      LAUNCH(D, k_global_residual<NLS_LAW_NEOHOOKE>, grid_for(e1 - e0), 256, 0, D.g_elem, e0, e1, D.conn, D.geom,
+             D.kcoef, x, F, mu, lam, D.bad);
+  }
+  LAUNCH(D, k_mask, grid_for(c.N), 256, 0, c.N, D.free_dof, F);
+}
+
+void global_jacobian(Context& c, const double* x) {
+  Dev& D = *c.dev;
+  const double E = c.young, nu = c.poisson;
+  const double mu = E / (2.0 * (1.0 + nu)), lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+  CK(cudaMemsetAsync(D.g_val, 0, sizeof(double) * c.g_col.size(), D.s));
+  for (size_t k = 0; k + 1 < c.g_color_ptr.size(); ++k) {
+    const int e0 = c.g_color_ptr[k], e1 = c.g_color_ptr[k + 1];
+    if (c.law == NLS_LAW_DIFFUSION)
+      LAUNCH(D, (k_global_jacobian<NLS_LAW_DIFFUSION, double>), grid_for(e1 - e0), 256, 0, D.g_elem, e0, e1, D.conn,
+             D.geom, D.kcoef, x, D.g_epos, D.g_val, mu, lam);
+    else if (fp32_local(c))
+      LAUNCH(D, (k_global_jacobian<NLS_LAW_NEOHOOKE, float>), grid_for(e1 - e0), 256, 0, D.g_elem, e0, e1, D.conn,
+             D.geom, D.kcoef, x, D.g_epos, D.g_val, mu, lam);
+    else
+      LAUNCH(D, (k_global_jacobian<NLS_LAW_NEOHOOKE, double>), grid_for(e1 - e0), 256, 0, D.g_elem, e0, e1, D.conn,
+             D.geom, D.kcoef, x, D.g_epos, D.g_val, mu, lam);
+  }
+}
+
+// ---- batched local kernels ---------------------------------------------------------------------
+template <typename FT>
+size_t local_newton_smem(const LocalSet& s) {
+  return smem_plan<FT>(s.max_n, s.max_nt, s.max_b, true).total;
+}
+
+void launch_local_newton(Context& c, const double* x, double* out, double load, const double* guess, bool want_tangent) {
+  Dev& D = *c.dev;
+  LocalArgs A = make_args(c, c.ov, D.ov);
+  A.x = x;
+  A.out = out;
+  A.load = load;
+  A.guess = guess;
+  A.want_tangent = want_tangent ? 1 : 0;
+  CK(cudaMemsetAsync(D.ov.queue, 0, sizeof(int32_t), D.s));
+  const int T = local_threads(c);
+  const bool f32 = fp32_local(c);
+  const size_t sm = f32 ? local_newton_smem<float>(c.ov) : local_newton_smem<double>(c.ov);
+  int per_sm = (int)std::max<size_t>(1, std::min<size_t>(2048 / T, D.smem_optin / std::max<size_t>(sm + 1024, 1)));
+  int grid = std::min(c.ov.count, D.nsm * per_sm);
+  if (c.law == NLS_LAW_DIFFUSION) {
+    if (f32) LAUNCH(D, (k_local_newton<NLS_LAW_DIFFUSION, float>), grid, T, sm, A);
+    else LAUNCH(D, (k_local_newton<NLS_LAW_DIFFUSION, double>), grid, T, sm, A);
+  } else {
+    if (f32) LAUNCH(D, (k_local_newton<NLS_LAW_NEOHOOKE, float>), grid, T, sm, A);
+    else LAUNCH(D, (k_local_newton<NLS_LAW_NEOHOOKE, double>), grid, T, sm, A);
+  }
+}
+
+void launch_local_apply(Context& c, const double* v, const double* add, double* out) {
+  Dev& D = *c.dev;
+  LocalArgs A = make_args(c, c.ov, D.ov);
+  A.v = v;
+  A.add = add;
+  A.out = out;
+  const int T = local_threads(c);
+  if (fp32_local(c)) {
+    const size_t sm = smem_plan<float>(c.ov.max_n, c.ov.max_nt, c.ov.max_b, false).total;
+    LAUNCH(D, k_local_apply<float>, c.ov.count, T, sm, A);
+  } else {
+    const size_t sm = smem_plan<double>(c.ov.max_n, c.ov.max_nt, c.ov.max_b, false).total;
+    LAUNCH(D, k_local_apply<double>, c.ov.count, T, sm, A);
+  }
+}
+
+// ---- coarse ---------------------------------------------------------------------------------
+LocalArgs coarse_args(Context& c) {
+  Dev& D = *c.dev;
+  LocalArgs A = make_args(c, c.nov, D.nov);
+  A.phi = D.phi;
+  A.phi_off = D.phi_off;
+  A.cj_ptr = D.cj_ptr;
+  A.Y = D.Y;
+  A.blk = D.blk;
+  A.blk_off = D.blk_off;
+  return A;
+}
+
+size_t coarse_factor_smem(const Context& c, bool f32) {
+  const size_t fs = f32 ? sizeof(float) : sizeof(double);
+  return fs * ((size_t)(c.cs.b0 + 2) * (2 * c.cs.b0 + 1) + c.cs.b0 + 2) + 16;
+}
+
+// A_0(x) = P_0^T DF(x) P_0 -> band -> factor.  Returns false on a bad pivot.
+bool coarse_matrix(Context& c, const double* x) {
+  Dev& D = *c.dev;
+  LocalArgs A = coarse_args(c);
+  A.x = x;
+  const int T = 256;
+  const size_t sm = smem_plan<double>(c.nov.max_n, c.nov.max_nt, c.nov.max_b, false).total;
+  if (c.law == NLS_LAW_DIFFUSION) LAUNCH(D, (k_galerkin<NLS_LAW_DIFFUSION, double>), c.nov.count, T, sm, A);
+  else if (fp32_local(c)) LAUNCH(D, (k_galerkin<NLS_LAW_NEOHOOKE, float>), c.nov.count, T, sm, A);
+  else LAUNCH(D, (k_galerkin<NLS_LAW_NEOHOOKE, double>), c.nov.count, T, sm, A);
+  const int64_t ne = (int64_t)c.cs.N0 * (2 * c.cs.b0 + 1);
+  LAUNCH(D, k_a0_gather, grid_for(ne), 256, 0, ne, D.a0_ptr, D.a0_src, D.blk, D.A0);
+  const bool f32 = fp32_coarse(c);
+  const size_t fsm = coarse_factor_smem(c, f32);
+  if (f32) LAUNCH(D, k_coarse_factor<float>, 1, 1024, fsm, c.cs.N0, c.cs.b0, D.A0, (float*)D.A0f, D.cstatus);
+  else LAUNCH(D, k_coarse_factor<double>, 1, 1024, fsm, c.cs.N0, c.cs.b0, D.A0, (double*)D.A0f, D.cstatus);
+  int32_t st = 0;
+  CK(cudaMemcpyAsync(&st, D.cstatus, sizeof(int32_t), cudaMemcpyDeviceToHost, D.s));
+  sync(D);
+  return st == ST_OK;
+}
+
+void coarse_solve(Context& c, const double* g, double* z) {
+  Dev& D = *c.dev;
+  if (fp32_coarse(c))
+    LAUNCH(D, k_coarse_solve<float>, 1, 1024, 0, c.cs.N0, c.cs.b0, D.A0, (const float*)D.A0f, g, z, D.cres,
+           (float*)D.cy, c.opt.ir_rtol, c.opt.ir_max_sweeps);
+  else
+    LAUNCH(D, k_coarse_solve<double>, 1, 1024, 0, c.cs.N0, c.cs.b0, D.A0, (const double*)D.A0f, g, z, D.cres,
+           (double*)D.cy, c.opt.ir_rtol, c.opt.ir_max_sweeps);
+}
+
+// x = u - P0 c
+void p0_update(Context& c, const double* u, const double* cv, double* x) {
+  Dev& D = *c.dev;
+  LAUNCH(D, k_p0_apply, grid_for(c.N), 256, 0, c.N, D.p0_rowptr, D.p0_col, D.p0_val, cv, 1.0, u, -1.0, x);
+}
+
+void p0t(Context& c, const double* v, double* g) {
+  Dev& D = *c.dev;
+  LAUNCH(D, k_p0t_apply, grid_for((int64_t)c.cs.N0 * 32), 256, 0, c.cs.N0, D.p0t_rowptr, D.p0t_col, D.p0t_val, v, g);
+}
+
+struct CoarseResult {
+  int its = 0;
+  int status = ST_OK;
+};
+
+// Coarse Newton for Eq. 9: g(c) = P0^T F(u - P0 c) = 0, c <- c + alpha A0^-1 g.  Leaves
+// D.c = T_0(u) and D.u0 = u - P0 T_0(u).
+CoarseResult coarse_newton(Context& c, const double* u, double load) {
+  Dev& D = *c.dev;
+  CoarseResult R;
+  const int N0 = c.cs.N0;
+  CK(cudaMemsetAsync(D.c, 0, sizeof(double) * N0, D.s));
+  CK(cudaMemcpyAsync(D.u0, u, sizeof(double) * c.N, cudaMemcpyDeviceToDevice, D.s));
+  global_residual(c, D.u0, D.F, load);
+  p0t(c, D.F, D.g);
+  double gn = norm2(D, N0, D.g);
+  if (!std::isfinite(gn)) {
+    R.status = ST_NONFINITE;
+    return R;
+  }
+  const double tol = std::max(c.opt.inner_atol, c.opt.inner_rtol * gn);
+  while (gn > tol) {
+    if (R.its >= c.opt.inner_maxit) {
+      R.status = ST_MAXIT;
+      break;
+    }
+    if (!coarse_matrix(c, D.u0)) {
+      R.status = ST_PIVOT;
+      break;
+    }
+    coarse_solve(c, D.g, D.dc);
+    double alpha = 1.0, gtn = INFINITY;
+    bool accepted = false;
+    for (int trial = 0; trial < c.opt.ls_trials; ++trial) {
+      LAUNCH(D, k_axpby, grid_for(N0), 256, 0, (int64_t)N0, 1.0, D.c, alpha, D.dc, D.ct);
+      p0_update(c, u, D.ct, D.x);
+      global_residual(c, D.x, D.F, load);
+      p0t(c, D.F, D.gt);
+      gtn = norm2(D, N0, D.gt);
+      if (std::isfinite(gtn) && gtn <= (1.0 - c.opt.armijo * alpha) * gn) {
+        accepted = true;
+        break;
+      }
+      alpha *= 0.5;
+    }
+    R.its += 1;
+    if (!accepted) {
+      R.status = ST_LS;
+      break;
+    }
+    std::swap(D.c, D.ct);
+    std::swap(D.u0, D.x);
+    std::swap(D.g, D.gt);
+    gn = gtn;
+  }
+  return R;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------------
+// setup on the device
+// ------------------------------------------------------------------------------------------
+namespace {
+
+void upload_set(Dev& D, const LocalSet& h, DeviceLocalSet& d, bool fp32_factor) {
+  d.count = h.count;
+  d.meta = D.upload(h.meta);
+  d.tnode_gid = D.upload(h.tnode_gid);
+  d.elem_gid = D.upload(h.elem_gid);
+  d.lconn = D.upload(h.lconn);
+  d.color_ptr = D.upload(h.color_ptr);
+  d.rowptr = D.upload(h.rowptr);
+  d.colidx = D.upload(h.colidx);
+  d.epos = D.upload(h.epos);
+  d.owned = D.upload(h.owned);
+  d.csr_val = D.alloc<double>(h.total_nnz);
+  if (fp32_factor) d.factor = D.alloc<float>(h.total_factor);
+  else d.factor = D.alloc<double>(h.total_factor);
+  d.w = D.alloc<double>(h.total_n);
+  d.its = D.alloc<int32_t>(h.count);
+  d.status = D.alloc<int32_t>(h.count);
+  // longest first: cost ~ n b^2
+  std::vector<int32_t> order(h.count);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    const double ca = (double)h.meta[a].n * h.meta[a].b * h.meta[a].b, cb = (double)h.meta[b].n * h.meta[b].b * h.meta[b].b;
+    return ca > cb;
+  });
+  d.order = D.upload(order);
+  d.queue = D.alloc<int32_t>(1);
+}
+
+}  // namespace
+
+int device_setup(Context& c) {
+  try {
+    CK(cudaSetDevice(c.device));
+    Dev* Dp = new Dev();
+    c.dev = Dp;
+    Dev& D = *Dp;
+    if (c.stream) {
+      D.s = (cudaStream_t)c.stream;
+    } else {
+      CK(cudaStreamCreateWithFlags(&D.s, cudaStreamNonBlocking));
+      c.own_stream = true;
+    }
+    cudaDeviceProp prop;
+    CK(cudaGetDeviceProperties(&prop, c.device));
+    D.nsm = prop.multiProcessorCount;
+    D.smem_optin = prop.sharedMemPerBlockOptin;
+    D.conn = D.upload(c.conn);
+    D.geom = D.upload(c.geom);
+    std::vector<double> k = c.k_elem;
+    if (k.empty()) k.assign(c.n_elems, 1.0);
+    D.kcoef = D.upload(k);
+    D.fext = D.upload(c.fext);
+    D.ubc = D.upload(c.ubc);
+    D.free_dof = D.upload(c.free_dof);
+    D.g_elem = D.upload(c.g_elem);
+    D.g_rowptr = D.upload(c.g_rowptr);
+    D.g_col = D.upload(c.g_col);
+    D.g_epos = D.upload(c.g_epos);
+    D.g_val = D.alloc<double>(c.g_col.size());
+    upload_set(D, c.ov, D.ov, fp32_local(c));
+    const int N = (int)c.N;
+    D.u = D.alloc<double>(N);
+    D.x = D.alloc<double>(N);
+    D.u0 = D.alloc<double>(N);
+    D.Fx = D.alloc<double>(N);
+    D.F = D.alloc<double>(N);
+    D.t1 = D.alloc<double>(N);
+    D.t2 = D.alloc<double>(N);
+    D.w0 = D.alloc<double>(N);
+    D.gx = D.alloc<double>(N);
+    D.m = std::max(1, std::min(c.opt.gmres_restart, kMaxGmresVecs / 2 - 2));
+    D.V = D.alloc<double>((size_t)(D.m + 1) * N);
+    CK(cudaMemsetAsync(D.V, 0, sizeof(double) * (size_t)(D.m + 1) * N, D.s));
+    D.partial = D.alloc<double>((size_t)kVecWarps * (kMaxGmresVecs + 2));
+    D.scal = D.alloc<double>(kMaxGmresVecs + 8);
+    D.coef = D.alloc<double>(kMaxGmresVecs + 8);
+    D.bad = D.alloc<int>(4);
+    CK(cudaMallocHost(&D.h_scal, sizeof(double) * (kMaxGmresVecs + 8)));
+    // kernel attributes for large dynamic shared memory
+    const size_t lim = D.smem_optin;
+    auto need = [&](size_t b, const char* what) {
+      if (b > lim) throw std::runtime_error(std::string(what) + " needs more shared memory than the device offers");
+    };
+    need(local_newton_smem<float>(c.ov), "local Newton (FP32 factors)");
+    if (!fp32_local(c)) need(local_newton_smem<double>(c.ov), "local Newton (FP64 factors)");
+    set_smem(k_local_newton<NLS_LAW_DIFFUSION, float>, lim);
+    set_smem(k_local_newton<NLS_LAW_DIFFUSION, double>, lim);
+    set_smem(k_local_newton<NLS_LAW_NEOHOOKE, float>, lim);
+    set_smem(k_local_newton<NLS_LAW_NEOHOOKE, double>, lim);
+    set_smem(k_local_apply<float>, lim);
+    set_smem(k_local_apply<double>, lim);
+    set_smem(k_harmonic<NLS_LAW_DIFFUSION>, lim);
+    set_smem(k_harmonic<NLS_LAW_NEOHOOKE>, lim);
+    set_smem(k_galerkin<NLS_LAW_DIFFUSION, double>, lim);
+    set_smem(k_galerkin<NLS_LAW_NEOHOOKE, float>, lim);
+    set_smem(k_galerkin<NLS_LAW_NEOHOOKE, double>, lim);
+    set_smem(k_coarse_factor<float>, lim);
+    set_smem(k_coarse_factor<double>, lim);
+    if (c.coarse_kind == NLS_COARSE_RGDSW) {
+      Coarse& cs = c.cs;
+      if (cs.N0 == 0) throw std::runtime_error("the partition has no coarse nodes (one subdomain?)");
+      need(coarse_factor_smem(c, fp32_coarse(c)), "coarse band factorization");
+      upload_set(D, c.nov, D.nov, false);
+      D.phi = D.upload(cs.phi_host);
+      D.phi_off = D.upload(cs.phi_off);
+      D.cj_ptr = D.upload(cs.cj_ptr);
+      D.Y = D.alloc<double>(cs.phi_total);
+      D.blk = D.alloc<double>(cs.blk_total);
+      D.blk_off = D.upload(cs.blk_off);
+      D.a0_ptr = D.upload(cs.a0_ptr);
+      D.a0_src = D.upload(cs.a0_src);
+      D.A0 = D.alloc<double>((size_t)cs.N0 * (2 * cs.b0 + 1));
+      if (fp32_coarse(c)) {
+        D.A0f = D.alloc<float>((size_t)cs.N0 * (2 * cs.b0 + 1));
+        D.cy = D.alloc<float>(cs.N0);
+      } else {
+        D.A0f = D.alloc<double>((size_t)cs.N0 * (2 * cs.b0 + 1));
+        D.cy = D.alloc<double>(cs.N0);
+      }
+      D.cstatus = D.alloc<int32_t>(1);
+      D.p0_rowptr = D.upload(cs.p0_rowptr);
+      D.p0_col = D.upload(cs.p0_col);
+      D.p0_src = D.upload(cs.p0_src);
+      D.p0_val = D.alloc<double>(cs.p0_col.size());
+      D.p0t_rowptr = D.upload(cs.p0t_rowptr);
+      D.p0t_col = D.upload(cs.p0t_col);
+      D.p0t_src = D.upload(cs.p0t_src);
+      D.p0t_val = D.alloc<double>(cs.p0t_col.size());
+      D.c = D.alloc<double>(cs.N0);
+      D.ct = D.alloc<double>(cs.N0);
+      D.dc = D.alloc<double>(cs.N0);
+      D.g = D.alloc<double>(cs.N0);
+      D.gt = D.alloc<double>(cs.N0);
+      D.cres = D.alloc<double>(cs.N0);
+      // energy-minimising extension with K = DF(u^(0)), u^(0) = Dirichlet data, zero elsewhere
+      CK(cudaMemcpyAsync(D.x, D.ubc, sizeof(double) * N, cudaMemcpyDeviceToDevice, D.s));
+      LocalArgs A = coarse_args(c);
+      A.x = D.x;
+      const size_t sm = smem_plan<double>(c.nov.max_n, c.nov.max_nt, c.nov.max_b, true).total;
+      need(sm, "coarse harmonic extension");
+      if (c.law == NLS_LAW_DIFFUSION) LAUNCH(D, k_harmonic<NLS_LAW_DIFFUSION>, c.nov.count, 256, sm, A);
+      else LAUNCH(D, k_harmonic<NLS_LAW_NEOHOOKE>, c.nov.count, 256, sm, A);
+      std::vector<int32_t> st(c.nov.count);
+      CK(cudaMemcpyAsync(st.data(), D.nov.status, sizeof(int32_t) * st.size(), cudaMemcpyDeviceToHost, D.s));
+      sync(D);
+      for (int32_t s : st)
+        if (s != ST_OK) throw std::runtime_error("coarse harmonic extension hit a zero pivot");
+      const int64_t np = (int64_t)cs.p0_col.size();
+      LAUNCH(D, k_gather_values, grid_for(np), 256, 0, np, D.p0_src, D.phi, D.p0_val);
+      LAUNCH(D, k_gather_values32, grid_for(np), 256, 0, np, D.p0t_src, D.p0_val, D.p0t_val);
+      // the non-overlapping factors are only needed for the extension
+      D.release(D.nov.factor);
+      D.nov.factor = nullptr;
+    }
+    sync(D);
+    c.device_bytes = D.bytes;
+  } catch (const CudaFailure& ex) {
+    c.last_error = ex.what();
+    return NLS_E_CUDA;
+  } catch (const std::bad_alloc&) {
+    c.last_error = "host allocation failed";
+    return NLS_E_NOMEM;
+  } catch (const std::exception& ex) {
+    c.last_error = ex.what();
+    return NLS_E_ARG;
+  }
+  return NLS_OK;
+}
+
+void device_free(Context& c) {
+  if (!c.dev) return;
+  Dev& D = *c.dev;
+  cudaSetDevice(c.device);
+  if (D.s) cudaStreamSynchronize(D.s);
+  for (void* p : D.allocs)
+    if (p) cudaFree(p);
+  if (D.h_scal) cudaFreeHost(D.h_scal);
+  for (auto& r : D.evs) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  if (c.own_stream && D.s) cudaStreamDestroy(D.s);
+  c.own_stream = false;
+  delete c.dev;
+  c.dev = nullptr;
+}
+
+// ------------------------------------------------------------------------------------------
+// F_x, tangent, GMRES, outer Newton
+// ------------------------------------------------------------------------------------------
+namespace {
+
+struct FxInfo {
+  int coarse_its = 0;
+  int coarse_status = ST_OK;
+  int64_t local_its = 0;
+  int local_failures = 0;
+  int first_failed = -1;
+  bool pivot_failure = false;
+};
+
+// F_x(u) into D.Fx; prepares everything the tangent needs.
+FxInfo evaluate_Fx(Context& c, const double* u, double load, double* t_inner, double* t_coarse) {
+  Dev& D = *c.dev;
+  FxInfo info;
+  const int cp = c.opt.coupling;
+  CK(cudaMemsetAsync(D.Fx, 0, sizeof(double) * c.N, D.s));
+  auto t0 = std::chrono::steady_clock::now();
+  const double* point = u;
+  if (cp != NLS_COUPLING_ONE) {
+    CoarseResult cr = coarse_newton(c, u, load);
+    info.coarse_its = cr.its;
+    info.coarse_status = cr.status;
+    if (cp == NLS_COUPLING_HYBRID) point = D.u0;
+  }
+  sync(D);
+  auto t1 = std::chrono::steady_clock::now();
+  launch_local_newton(c, point, D.Fx, load, nullptr, true);
+  std::vector<int32_t> its(c.ov.count), st(c.ov.count);
+  CK(cudaMemcpyAsync(its.data(), D.ov.its, sizeof(int32_t) * its.size(), cudaMemcpyDeviceToHost, D.s));
+  CK(cudaMemcpyAsync(st.data(), D.ov.status, sizeof(int32_t) * st.size(), cudaMemcpyDeviceToHost, D.s));
+  sync(D);
+  auto t2 = std::chrono::steady_clock::now();
+  for (int i = 0; i < c.ov.count; ++i) {
+    info.local_its += its[i];
+    if (st[i] != ST_OK) {
+      info.local_failures += 1;
+      if (info.first_failed < 0) info.first_failed = i;
+      if (st[i] == ST_PIVOT) info.pivot_failure = true;
+    }
+  }
+  if (cp != NLS_COUPLING_ONE) {
+    // F_x += P0 T_0(u); the coarse part of the tangent at u_0 = u - P0 T_0(u)
+    LAUNCH(D, k_p0_apply, grid_for(c.N), 256, 0, c.N, D.p0_rowptr, D.p0_col, D.p0_val, D.c, 1.0, D.Fx, 1.0, D.Fx);
+    global_jacobian(c, D.u0);
+    if (!coarse_matrix(c, D.u0)) info.pivot_failure = true;
+  }
+  sync(D);
+  auto t3 = std::chrono::steady_clock::now();
+  if (t_inner) *t_inner += std::chrono::duration<double>(t2 - t1).count();
+  if (t_coarse) *t_coarse += std::chrono::duration<double>(t1 - t0).count() + std::chrono::duration<double>(t3 - t2).count();
+  c.dev->tangent_ready = true;
+  return info;
+}
+
+// y = DF_x v (Eq. 6 / Eq. 12)
+void tangent(Context& c, const double* v, double* y) {
+  Dev& D = *c.dev;
+  const int cp = c.opt.coupling;
+  if (cp == NLS_COUPLING_ONE) {
+    launch_local_apply(c, v, nullptr, y);
+    return;
+  }
+  // w0 = P0 A0^-1 P0^T DF(u0) v
+  LAUNCH(D, k_spmv_free, grid_for(c.N), 256, 0, c.N, D.g_rowptr, D.g_col, D.g_val, D.free_dof, v, D.t1);
+  p0t(c, D.t1, D.gt);
+  coarse_solve(c, D.gt, D.dc);
+  LAUNCH(D, k_p0_apply, grid_for(c.N), 256, 0, c.N, D.p0_rowptr, D.p0_col, D.p0_val, D.dc, 0.0, nullptr, 1.0, D.w0);
+  if (cp == NLS_COUPLING_ADD) {
+    launch_local_apply(c, v, D.w0, y);
+  } else {
+    LAUNCH(D, k_axpby, grid_for(c.N), 256, 0, c.N, 1.0, v, -1.0, D.w0, D.t2);
+    launch_local_apply(c, D.t2, D.w0, y);
+  }
+}
+
+struct GmresResult {
+  int its = 0;
+  double relres = 0.0;
+  bool converged = false;
+};
+
+// GMRES(m), zero initial guess, classical Gram-Schmidt with one re-orthogonalisation
+// (device multi-dots), Givens rotations on the host.  Solution into D.gx.
+GmresResult gmres(Context& c, const double* b) {
+  Dev& D = *c.dev;
+  const int64_t N = c.N;
+  const int m = D.m;
+  GmresResult R;
+  CK(cudaMemsetAsync(D.gx, 0, sizeof(double) * N, D.s));
+  const double bn = norm2(D, N, b);
+  if (bn == 0.0) {
+    R.converged = true;
+    return R;
+  }
+  double* r = D.t2;
+  CK(cudaMemcpyAsync(r, b, sizeof(double) * N, cudaMemcpyDeviceToDevice, D.s));
+  double rn = bn;
+  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), gv(m + 1), y(m);
+  const double target = c.opt.gmres_rtol * bn;
+  while (R.its < c.opt.gmres_maxit) {
+    // V0 = r / rn
+    LAUNCH(D, k_axpby, grid_for(N), 256, 0, N, 1.0 / rn, r, 0.0, nullptr, D.V);
+    std::fill(H.begin(), H.end(), 0.0);
+    std::fill(gv.begin(), gv.end(), 0.0);
+    gv[0] = rn;
+    int j = 0;
+    bool done = false;
+    while (j < m && R.its < c.opt.gmres_maxit) {
+      double* vj = D.V + (size_t)j * N;
+      double* w = D.V + (size_t)(j + 1) * N;
+      tangent(c, vj, w);
+      // CGS2
+      for (int pass = 0; pass < 2; ++pass) {
+        LAUNCH(D, k_multidot_partial, kVecBlocks, kVecThreads, 0, N, j + 1, D.V, N, w, D.partial);
+        LAUNCH(D, k_partial_final, std::min(j + 1, 64), 256, 0, j + 1, D.partial, D.scal + pass * (kMaxGmresVecs / 2));
+        LAUNCH(D, k_multiaxpy, grid_for(N), 256, 0, N, j + 1, D.V, N, D.scal + pass * (kMaxGmresVecs / 2), -1.0, w);
+      }
+      LAUNCH(D, k_multidot_partial, kVecBlocks, kVecThreads, 0, N, 1, w, (int64_t)0, w, D.partial);
+      LAUNCH(D, k_partial_final, 1, 256, 0, 1, D.partial, D.scal + kMaxGmresVecs);
+      LAUNCH(D, k_sqrt_inplace, 1, 1, 0, D.scal + kMaxGmresVecs);
+      CK(cudaMemcpyAsync(D.h_scal, D.scal, sizeof(double) * (kMaxGmresVecs + 1), cudaMemcpyDeviceToHost, D.s));
+      LAUNCH(D, k_scale_inv, grid_for(N), 256, 0, N, w, D.scal + kMaxGmresVecs, w);
+      sync(D);
+      for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = D.h_scal[i] + D.h_scal[kMaxGmresVecs / 2 + i];
+      const double hn = D.h_scal[kMaxGmresVecs];
+      H[(size_t)(j + 1) * m + j] = hn;
+      for (int i = 0; i < j; ++i) {
+        const double t = cs[i] * H[(size_t)i * m + j] + sn[i] * H[(size_t)(i + 1) * m + j];
+        H[(size_t)(i + 1) * m + j] = -sn[i] * H[(size_t)i * m + j] + cs[i] * H[(size_t)(i + 1) * m + j];
+        H[(size_t)i * m + j] = t;
+      }
+      const double d = std::hypot(H[(size_t)j * m + j], H[(size_t)(j + 1) * m + j]);
+      cs[j] = H[(size_t)j * m + j] / d;
+      sn[j] = H[(size_t)(j + 1) * m + j] / d;
+      H[(size_t)j * m + j] = d;
+      H[(size_t)(j + 1) * m + j] = 0.0;
+      gv[j + 1] = -sn[j] * gv[j];
+      gv[j] = cs[j] * gv[j];
+      ++j;
+      ++R.its;
+      if (!std::isfinite(hn) || std::abs(gv[j]) <= target || hn == 0.0) {
+        done = true;
+        break;
+      }
+    }
+    for (int i = j - 1; i >= 0; --i) {
+      double acc = gv[i];
+      for (int k = i + 1; k < j; ++k) acc -= H[(size_t)i * m + k] * y[k];
+      y[i] = acc / H[(size_t)i * m + i];
+    }
+    CK(cudaMemcpyAsync(D.coef, y.data(), sizeof(double) * j, cudaMemcpyHostToDevice, D.s));
+    LAUNCH(D, k_multiaxpy, grid_for(N), 256, 0, N, j, D.V, N, D.coef, 1.0, D.gx);
+    sync(D);
+    R.relres = std::abs(gv[j]) / bn;
+    if (done && std::abs(gv[j]) <= target) {
+      R.converged = true;
+      break;
+    }
+    // restart: r = b - A x
+    tangent(c, D.gx, D.t1);
+    LAUNCH(D, k_axpby, grid_for(N), 256, 0, N, 1.0, b, -1.0, D.t1, r);
+    rn = norm2(D, N, r);
+    R.relres = rn / bn;
+    if (rn <= target) {
+      R.converged = true;
+      break;
+    }
+    if (done) break;
+  }
+  return R;
+}
+
+}  // namespace
+
+int solve(Context& c, double* u_user, int u_dev, nls_report* rep) {
+  Dev& D = *c.dev;
+  nls_report rp;
+  std::memset(&rp, 0, sizeof(rp));
+  rp.first_failed_subdomain = -1;
+  int status = NLS_OK;
+  const int64_t N = c.N;
+  const int64_t launches0 = D.launches;
+  try {
+    CK(cudaSetDevice(c.device));
+    D.prof = c.opt.profile_kernels != 0;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    CK(cudaEventRecord(e0, D.s));
+    auto w0 = std::chrono::steady_clock::now();
+    CK(cudaMemcpyAsync(D.u, u_user, sizeof(double) * N, u_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, D.s));
+    LAUNCH(D, k_set_dirichlet, grid_for(N), 256, 0, N, D.free_dof, D.ubc, D.u);
+    double t_inner = 0, t_coarse = 0, t_gmres = 0;
+    const int L = std::max(1, c.opt.load_steps);
+    double nF = INFINITY;
+    for (int step = 1; step <= L && status == NLS_OK; ++step) {
+      const double load = (double)step / L;
+      for (int k = 0;; ++k) {
+        global_residual(c, D.u, D.F, load);
+        nF = norm2(D, N, D.F);
+        if (c.opt.verbose) std::fprintf(stderr, "[nls] load %.3f outer %d ||F|| = %.3e\n", load, k, nF);
+        if (!std::isfinite(nF)) {
+          status = NLS_E_DIVERGED;
+          break;
+        }
+        if (nF < c.opt.outer_atol) break;
+        if (k >= c.opt.outer_maxit) {
+          status = NLS_W_NOT_CONVERGED;
+          break;
+        }
+        FxInfo fi = evaluate_Fx(c, D.u, load, &t_inner, &t_coarse);
+        rp.subdomain_newton_steps += fi.local_its;
+        rp.coarse_newton_steps += fi.coarse_its;
+        rp.local_failures += fi.local_failures;
+        if (rp.first_failed_subdomain < 0) rp.first_failed_subdomain = fi.first_failed;
+        if (fi.pivot_failure) {
+          status = NLS_E_PIVOT;
+          break;
+        }
+        const double fxn = norm2(D, N, D.Fx);
+        if (fxn == 0.0) break;  // every correction vanished: no further progress possible
+        auto g0 = std::chrono::steady_clock::now();
+        GmresResult gr = gmres(c, D.Fx);
+        sync(D);
+        t_gmres += std::chrono::duration<double>(std::chrono::steady_clock::now() - g0).count();
+        rp.gmres_iterations += gr.its;
+        rp.outer_iterations += 1;
+        if (c.opt.verbose)
+          std::fprintf(stderr, "[nls]   ||Fx|| = %.3e gmres %d (rel %.2e) local its %lld coarse its %d\n", fxn, gr.its,
+                       gr.relres, (long long)fi.local_its, fi.coarse_its);
+        LAUNCH(D, k_axpby, grid_for(N), 256, 0, N, 1.0, D.u, -1.0, D.gx, D.u);
+      }
+    }
+    rp.final_residual = nF;
+    CK(cudaMemcpyAsync(u_user, D.u, sizeof(double) * N, u_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, D.s));
+    CK(cudaEventRecord(e1, D.s));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    const double wall = std::chrono::duration<double>(std::chrono::steady_clock::now() - w0).count();
+    rp.time_total_s = ms * 1e-3;
+    rp.time_inner_s = t_inner;
+    rp.time_coarse_s = t_coarse;
+    rp.time_gmres_s = t_gmres;
+    rp.time_other_s = std::max(0.0, wall - t_inner - t_coarse - t_gmres);
+    D.prof_flush();
+  } catch (const CudaFailure& ex) {
+    c.last_error = ex.what();
+    status = NLS_E_CUDA;
+  } catch (const std::exception& ex) {
+    c.last_error = ex.what();
+    status = NLS_E_ARG;
+  }
+  rp.kernel_launches = D.launches - launches0;
+  rp.status = status;
+  if (rep) *rep = rp;
+  return status;
+}
+
+int eval_F(Context& c, const double* u, double* F, int is_dev, double load) {
+  Dev& D = *c.dev;
+  try {
+    CK(cudaMemcpyAsync(D.x, u, sizeof(double) * c.N, is_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, D.s));
+    global_residual(c, D.x, D.F, load);
+    CK(cudaMemcpyAsync(F, D.F, sizeof(double) * c.N, is_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, D.s));
+    sync(D);
+  } catch (const std::exception& ex) {
+    c.last_error = ex.what();
+    return NLS_E_CUDA;
+  }
+  return NLS_OK;
+}
+
+int eval_Fx(Context& c, const double* u, double* Fx, int is_dev, double load, int32_t* its, int32_t* st) {
+  Dev& D = *c.dev;
+  try {
+    CK(cudaMemcpyAsync(D.u, u, sizeof(double) * c.N, is_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, D.s));
+    FxInfo fi = evaluate_Fx(c, D.u, load, nullptr, nullptr);
+    CK(cudaMemcpyAsync(Fx, D.Fx, sizeof(double) * c.N, is_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, D.s));
+    if (its) CK(cudaMemcpyAsync(its, D.ov.its, sizeof(int32_t) * c.ov.count, cudaMemcpyDeviceToHost, D.s));
+    if (st) CK(cudaMemcpyAsync(st, D.ov.status, sizeof(int32_t) * c.ov.count, cudaMemcpyDeviceToHost, D.s));
+    sync(D);
+    if (fi.pivot_failure) return NLS_E_PIVOT;
+  } catch (const std::exception& ex) {
+    c.last_error = ex.what();
+    return NLS_E_CUDA;
+  }
+  return NLS_OK;
+}
+
+int apply_tangent(Context& c, const double* v, double* y, int is_dev) {
+  Dev& D = *c.dev;
+  if (!D.tangent_ready) {
+    c.last_error = "nls_apply_tangent needs a preceding nls_eval_Fx";
+    return NLS_E_ARG;
+  }
+  try {
+    CK(cudaMemcpyAsync(D.t1, v, sizeof(double) * c.N, is_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, D.s));
+    LAUNCH(D, k_mask, grid_for(c.N), 256, 0, c.N, D.free_dof, D.t1);
+    CK(cudaMemcpyAsync(D.x, D.t1, sizeof(double) * c.N, cudaMemcpyDeviceToDevice, D.s));
+    CK(cudaMemsetAsync(D.gx, 0, sizeof(double) * c.N, D.s));
+    tangent(c, D.x, D.gx);
+    CK(cudaMemcpyAsync(y, D.gx, sizeof(double) * c.N, is_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, D.s));
+    sync(D);
+  } catch (const std::exception& ex) {
+    c.last_error = ex.what();
+    return NLS_E_CUDA;
+  }
+  return NLS_OK;
+}
+
+int get_local_states(Context& c, double* w, int is_dev) {
+  Dev& D = *c.dev;
+  try {
+    CK(cudaMemcpyAsync(w, D.ov.w, sizeof(double) * c.ov.total_n, is_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, D.s));
+    sync(D);
+  } catch (const std::exception& ex) {
+    c.last_error = ex.what();
+    return NLS_E_CUDA;
+  }
+  return NLS_OK;
+}
+
+int kernel_stats(const Context& c, int32_t cap, nls_kernel_stat* out, int32_t* n_out) {
+  if (!c.dev) {
+    *n_out = 0;
+    return NLS_OK;
+  }
+  Dev& D = *c.dev;
+  try {
+    D.prof_flush();
+  } catch (const std::exception&) {
+    return NLS_E_CUDA;
+  }
+  int32_t n = 0;
+  for (auto& st : D.stats) {
+    if (out && n < cap) {
+      out[n].name = st.name.c_str();
+      out[n].launches = st.launches;
+      out[n].total_ms = st.ms;
+    }
+    ++n;
+  }
+  *n_out = std::min(n, cap);
+  return NLS_OK;
+}
+
+void reset_kernel_stats(Context& c) {
+  if (!c.dev) return;
+  try {
+    c.dev->prof_flush();
+  } catch (const std::exception&) {
+  }
+  c.dev->stats.clear();
+}
+
+int get_coarse_basis(const Context& c, double* P0) {
+  if (c.coarse_kind != NLS_COARSE_RGDSW || !c.dev) return NLS_E_ARG;
+  Dev& D = *c.dev;
+  try {
+    std::vector<double> vals(c.cs.p0_col.size());
+    CK(cudaMemcpyAsync(vals.data(), D.p0_val, sizeof(double) * vals.size(), cudaMemcpyDeviceToHost, D.s));
+    CK(cudaStreamSynchronize(D.s));
+    std::memset(P0, 0, sizeof(double) * c.N * c.cs.N0);
+    for (int64_t g = 0; g < c.N; ++g)
+      for (int32_t k = c.cs.p0_rowptr[g]; k < c.cs.p0_rowptr[g + 1]; ++k) P0[(int64_t)c.cs.p0_col[k] * c.N + g] = vals[k];
+  } catch (const std::exception&) {
+    return NLS_E_CUDA;
+  }
+  return NLS_OK;
+}
+
+}  // namespace nls

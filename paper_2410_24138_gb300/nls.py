@@ -1,0 +1,334 @@
+"""Python binding of the C-ABI library ``libnls.so`` (include/nls.h): argument marshalling only.
+
+Every computation runs in the library's sm_103a kernels.  Host arrays are numpy arrays;
+device arrays are torch CUDA tensors (their ``data_ptr()`` is passed through).  Loading
+fails loudly when the library has not been built: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+from . import build as _build
+from .inputs import LAW_DIFFUSION, LAW_NEOHOOKE, Problem
+
+P1_TRI, Q1_QUAD = 1, 2
+COUPLING = {"one": 0, "add": 1, "hybrid": 2}
+PREC_FP64, PREC_FP32_IR = 0, 1
+COARSE_NONE, COARSE_RGDSW = 0, 1
+
+STATUS = {0: "ok", -1: "E_ARG", -2: "E_CUDA", -3: "E_NOMEM", -4: "E_UNSUPPORTED", -5: "E_LOCAL_NEWTON",
+          -6: "E_PIVOT", -7: "E_GMRES", -8: "E_DIVERGED", -9: "E_DEVICE_TIMEOUT", 1: "W_NOT_CONVERGED"}
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("coupling", ctypes.c_int32), ("local_precision", ctypes.c_int32),
+                ("coarse_precision", ctypes.c_int32), ("load_steps", ctypes.c_int32),
+                ("outer_atol", ctypes.c_double), ("outer_maxit", ctypes.c_int32),
+                ("inner_rtol", ctypes.c_double), ("inner_atol", ctypes.c_double),
+                ("inner_maxit", ctypes.c_int32), ("ls_trials", ctypes.c_int32), ("armijo", ctypes.c_double),
+                ("gmres_rtol", ctypes.c_double), ("gmres_restart", ctypes.c_int32), ("gmres_maxit", ctypes.c_int32),
+                ("ir_rtol", ctypes.c_double), ("ir_max_sweeps", ctypes.c_int32),
+                ("threads_per_block", ctypes.c_int32), ("verbose", ctypes.c_int32),
+                ("profile_kernels", ctypes.c_int32)]
+
+
+class Report(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("outer_iterations", ctypes.c_int32),
+                ("gmres_iterations", ctypes.c_int32), ("subdomain_newton_steps", ctypes.c_int64),
+                ("coarse_newton_steps", ctypes.c_int32), ("local_failures", ctypes.c_int32),
+                ("first_failed_subdomain", ctypes.c_int32), ("final_residual", ctypes.c_double),
+                ("time_total_s", ctypes.c_double), ("time_inner_s", ctypes.c_double),
+                ("time_coarse_s", ctypes.c_double), ("time_gmres_s", ctypes.c_double),
+                ("time_other_s", ctypes.c_double), ("kernel_launches", ctypes.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class Sizes(ctypes.Structure):
+    _fields_ = [("n_nodes", ctypes.c_int64), ("n_dofs", ctypes.c_int64), ("n_elems", ctypes.c_int64),
+                ("ndof", ctypes.c_int32), ("n_sub", ctypes.c_int32), ("n_coarse_nodes", ctypes.c_int32),
+                ("n_coarse_dofs", ctypes.c_int32), ("total_local_dofs", ctypes.c_int64),
+                ("total_overlap_elems", ctypes.c_int64), ("max_local_dofs", ctypes.c_int32),
+                ("max_half_band", ctypes.c_int32), ("coarse_half_band", ctypes.c_int32),
+                ("device_bytes", ctypes.c_int64), ("total_factor_entries", ctypes.c_int64),
+                ("total_local_nnz", ctypes.c_int64), ("total_table_dofs", ctypes.c_int64),
+                ("factor_bytes", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
+class KernelStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char_p), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+EXPORTS = ["nls_options_default", "nls_create", "nls_destroy", "nls_strerror", "nls_last_error", "nls_set_mesh",
+           "nls_set_dirichlet", "nls_set_traction", "nls_set_material", "nls_set_partition", "nls_set_coarse",
+           "nls_set_options", "nls_get_options", "nls_setup", "nls_setup_host", "nls_solve", "nls_get_sizes", "nls_get_local_dofs",
+           "nls_get_overlap_elems", "nls_get_owners", "nls_get_coarse_nodes", "nls_get_coarse_basis", "nls_eval_F",
+           "nls_eval_Fx", "nls_apply_tangent", "nls_get_local_states", "nls_get_kernel_stats",
+           "nls_reset_kernel_stats"]
+
+_LIB = None
+_P = ctypes.c_void_p
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load() -> ctypes.CDLL:
+    """Load libnls.so (built in-tree by ``paper_2410_24138_gb300.build.build()``)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = library_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build the sm_103a library first (paper_2410_24138_gb300.build.build())")
+    lib = ctypes.CDLL(path)
+    i32, i64, dbl = ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    sig = {
+        "nls_options_default": (None, [ctypes.POINTER(Options)]),
+        "nls_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, _P]),
+        "nls_destroy": (None, [_P]),
+        "nls_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+        "nls_last_error": (ctypes.c_char_p, [_P]),
+        "nls_set_mesh": (ctypes.c_int, [_P, ctypes.c_int, i64, _P, i64, _P]),
+        "nls_set_dirichlet": (ctypes.c_int, [_P, i64, _P, _P]),
+        "nls_set_traction": (ctypes.c_int, [_P, i64, _P, _P]),
+        "nls_set_material": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P]),
+        "nls_set_partition": (ctypes.c_int, [_P, i32, _P, i32]),
+        "nls_set_coarse": (ctypes.c_int, [_P, ctypes.c_int]),
+        "nls_set_options": (ctypes.c_int, [_P, ctypes.POINTER(Options)]),
+        "nls_get_options": (ctypes.c_int, [_P, ctypes.POINTER(Options)]),
+        "nls_setup": (ctypes.c_int, [_P]),
+        "nls_setup_host": (ctypes.c_int, [_P]),
+        "nls_solve": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.POINTER(Report)]),
+        "nls_get_sizes": (ctypes.c_int, [_P, ctypes.POINTER(Sizes)]),
+        "nls_get_local_dofs": (ctypes.c_int, [_P, i32, i64, _P, _P, ctypes.POINTER(i64)]),
+        "nls_get_overlap_elems": (ctypes.c_int, [_P, i32, i64, _P, ctypes.POINTER(i64)]),
+        "nls_get_owners": (ctypes.c_int, [_P, _P]),
+        "nls_get_coarse_nodes": (ctypes.c_int, [_P, _P]),
+        "nls_get_coarse_basis": (ctypes.c_int, [_P, _P]),
+        "nls_eval_F": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, dbl]),
+        "nls_eval_Fx": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, dbl, _P, _P]),
+        "nls_apply_tangent": (ctypes.c_int, [_P, _P, _P, ctypes.c_int]),
+        "nls_get_local_states": (ctypes.c_int, [_P, _P, ctypes.c_int]),
+        "nls_get_kernel_stats": (ctypes.c_int, [_P, i32, ctypes.POINTER(KernelStat), ctypes.POINTER(i32)]),
+        "nls_reset_kernel_stats": (ctypes.c_int, [_P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = lib
+    return lib
+
+
+def _ptr(a) -> Optional[int]:
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays must be C-contiguous")
+        return a.ctypes.data
+    return int(a.data_ptr())  # torch tensor
+
+
+def _is_device(a) -> int:
+    return 0 if isinstance(a, np.ndarray) else int(getattr(a, "is_cuda", False))
+
+
+class NLSError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str):
+        super().__init__(f"{where}: {STATUS.get(status, status)} ({detail})")
+        self.status = status
+
+
+def default_options() -> Options:
+    o = Options()
+    load().nls_options_default(ctypes.byref(o))
+    return o
+
+
+class Solver:
+    """One solver context: mesh + law + partition + coarse space -> solution of F(u) = 0."""
+
+    def __init__(self, device: int = 0, stream: Optional[int] = None):
+        self.lib = load()
+        self.h = _P()
+        self._check(self.lib.nls_create(ctypes.byref(self.h), device, stream), "nls_create")
+        self.ndof = 1
+        self.n_nodes = 0
+        self.n_sub = 0
+
+    def _check(self, st: int, where: str) -> int:
+        if st < 0:
+            raise NLSError(st, where, self.lib.nls_last_error(self.h).decode() if self.h else "")
+        return st
+
+    def close(self):
+        if self.h:
+            self.lib.nls_destroy(self.h)
+            self.h = _P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- problem description --------------------------------------------------------------
+    def set_problem(self, p: Problem):
+        xy = np.ascontiguousarray(p.xy, dtype=np.float64)
+        conn = np.ascontiguousarray(p.conn, dtype=np.int32)
+        self._check(self.lib.nls_set_mesh(self.h, p.elem_type, xy.shape[0], _ptr(xy), conn.shape[0], _ptr(conn)),
+                    "nls_set_mesh")
+        law = p.law
+        self.ndof = p.ndof
+        self.n_nodes = xy.shape[0]
+        if law == LAW_DIFFUSION:
+            k = None if p.k_elem is None else np.ascontiguousarray(p.k_elem, dtype=np.float64)
+            f = None if p.f_elem is None else np.ascontiguousarray(p.f_elem, dtype=np.float64)
+            self._check(self.lib.nls_set_material(self.h, law, None, _ptr(k), _ptr(f)), "nls_set_material")
+        else:
+            params = np.array([p.young, p.poisson], dtype=np.float64)
+            self._check(self.lib.nls_set_material(self.h, law, _ptr(params), None, None), "nls_set_material")
+        dofs = np.ascontiguousarray(p.dirichlet_dofs(), dtype=np.int64)
+        vals = np.zeros(dofs.shape[0])
+        self._check(self.lib.nls_set_dirichlet(self.h, dofs.shape[0], _ptr(dofs), _ptr(vals)), "nls_set_dirichlet")
+        if p.traction_edges is not None:
+            e = np.ascontiguousarray(p.traction_edges, dtype=np.int32)
+            t = np.ascontiguousarray(p.traction, dtype=np.float64)
+            self._check(self.lib.nls_set_traction(self.h, e.shape[0], _ptr(e), _ptr(t)), "nls_set_traction")
+        e2s = np.ascontiguousarray(p.elem_to_sub, dtype=np.int32)
+        self._check(self.lib.nls_set_partition(self.h, p.n_sub, _ptr(e2s), p.overlap), "nls_set_partition")
+        self.n_sub = p.n_sub
+
+    def set_coarse(self, kind: int):
+        self._check(self.lib.nls_set_coarse(self.h, kind), "nls_set_coarse")
+
+    def set_options(self, **kw) -> Options:
+        o = Options()
+        self._check(self.lib.nls_get_options(self.h, ctypes.byref(o)), "nls_get_options")
+        for k, v in kw.items():
+            if k == "coupling" and isinstance(v, str):
+                v = COUPLING[v]
+            if not hasattr(o, k):
+                raise KeyError(k)
+            setattr(o, k, v)
+        self._check(self.lib.nls_set_options(self.h, ctypes.byref(o)), "nls_set_options")
+        return o
+
+    def setup(self):
+        self._check(self.lib.nls_setup(self.h), "nls_setup")
+
+    def setup_host(self):
+        """Integer maps only (no GPU needed)."""
+        self._check(self.lib.nls_setup_host(self.h), "nls_setup_host")
+
+    # -- solve ----------------------------------------------------------------------------
+    def solve(self, u=None):
+        """Solve F(u) = 0; u (numpy host array or torch CUDA tensor) is overwritten."""
+        if u is None:
+            u = np.zeros(self.n_nodes * self.ndof)
+        rep = Report()
+        st = self.lib.nls_solve(self.h, _ptr(u), _is_device(u), ctypes.byref(rep))
+        self._check(st, "nls_solve")
+        return u, rep
+
+    # -- inspection / parity hooks --------------------------------------------------------
+    def sizes(self) -> Sizes:
+        s = Sizes()
+        self._check(self.lib.nls_get_sizes(self.h, ctypes.byref(s)), "nls_get_sizes")
+        return s
+
+    def local_dofs(self, sub: int):
+        n = ctypes.c_int64()
+        self._check(self.lib.nls_get_local_dofs(self.h, sub, 0, None, None, ctypes.byref(n)), "nls_get_local_dofs")
+        dofs = np.zeros(n.value, dtype=np.int64)
+        owned = np.zeros(n.value, dtype=np.uint8)
+        self._check(self.lib.nls_get_local_dofs(self.h, sub, n.value, _ptr(dofs), _ptr(owned), ctypes.byref(n)),
+                    "nls_get_local_dofs")
+        return dofs, owned.astype(bool)
+
+    def overlap_elems(self, sub: int) -> np.ndarray:
+        n = ctypes.c_int64()
+        self._check(self.lib.nls_get_overlap_elems(self.h, sub, 0, None, ctypes.byref(n)), "nls_get_overlap_elems")
+        out = np.zeros(n.value, dtype=np.int32)
+        self._check(self.lib.nls_get_overlap_elems(self.h, sub, n.value, _ptr(out), ctypes.byref(n)),
+                    "nls_get_overlap_elems")
+        return out
+
+    def owners(self) -> np.ndarray:
+        out = np.zeros(self.n_nodes, dtype=np.int32)
+        self._check(self.lib.nls_get_owners(self.h, _ptr(out)), "nls_get_owners")
+        return out
+
+    def coarse_nodes(self) -> np.ndarray:
+        out = np.zeros(self.sizes().n_coarse_nodes, dtype=np.int32)
+        self._check(self.lib.nls_get_coarse_nodes(self.h, _ptr(out)), "nls_get_coarse_nodes")
+        return out
+
+    def coarse_basis(self) -> np.ndarray:
+        s = self.sizes()
+        out = np.zeros((s.n_coarse_dofs, s.n_dofs), dtype=np.float64)  # column-major N x N0
+        self._check(self.lib.nls_get_coarse_basis(self.h, _ptr(out)), "nls_get_coarse_basis")
+        return out.T
+
+    def eval_F(self, u, load: float = 1.0):
+        F = np.zeros_like(u) if isinstance(u, np.ndarray) else u.new_zeros(u.shape)
+        self._check(self.lib.nls_eval_F(self.h, _ptr(u), _ptr(F), _is_device(u), load), "nls_eval_F")
+        return F
+
+    def eval_Fx(self, u, load: float = 1.0):
+        Fx = np.zeros_like(u) if isinstance(u, np.ndarray) else u.new_zeros(u.shape)
+        its = np.zeros(self.n_sub, dtype=np.int32)
+        st = np.zeros(self.n_sub, dtype=np.int32)
+        self._check(self.lib.nls_eval_Fx(self.h, _ptr(u), _ptr(Fx), _is_device(u), load, _ptr(its), _ptr(st)),
+                    "nls_eval_Fx")
+        return Fx, its, st
+
+    def apply_tangent(self, v):
+        y = np.zeros_like(v) if isinstance(v, np.ndarray) else v.new_zeros(v.shape)
+        self._check(self.lib.nls_apply_tangent(self.h, _ptr(v), _ptr(y), _is_device(v)), "nls_apply_tangent")
+        return y
+
+    def kernel_stats(self) -> dict:
+        """{kernel: (launches, total ms)} accumulated while the profile_kernels option is set."""
+        cap = 64
+        arr = (KernelStat * cap)()
+        n = ctypes.c_int32()
+        self._check(self.lib.nls_get_kernel_stats(self.h, cap, arr, ctypes.byref(n)), "nls_get_kernel_stats")
+        return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].total_ms)) for i in range(n.value)}
+
+    def reset_kernel_stats(self):
+        self._check(self.lib.nls_reset_kernel_stats(self.h), "nls_reset_kernel_stats")
+
+    def local_states(self) -> np.ndarray:
+        out = np.zeros(self.sizes().total_local_dofs)
+        self._check(self.lib.nls_get_local_states(self.h, _ptr(out), 0), "nls_get_local_states")
+        return out
+
+
+def make_solver(p: Problem, coupling: str = "hybrid", precision: str = "fp32", coarse: Optional[bool] = None,
+                device: int = 0, setup: bool = True, **opts) -> Solver:
+    """Context for a problem from ``paper_2410_24138_gb300.inputs`` with the given options."""
+    s = Solver(device)
+    s.set_problem(p)
+    use_coarse = (coupling != "one") if coarse is None else coarse
+    s.set_coarse(COARSE_RGDSW if use_coarse else COARSE_NONE)
+    prec = PREC_FP32_IR if precision == "fp32" else PREC_FP64
+    kw = dict(coupling=COUPLING[coupling], local_precision=prec, load_steps=p.load_steps)
+    kw.update(opts)
+    s.set_options(**kw)
+    if setup == "host":
+        s.setup_host()
+    elif setup:
+        s.setup()
+    return s

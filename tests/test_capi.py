@@ -1,0 +1,110 @@
+"""The C-ABI library without a GPU: it loads, exports every symbol include/nls.h declares,
+rejects bad arguments, and its host setup reproduces the oracle's integer maps bit for bit
+(overlapping element sets, local numbering R_i, ownership of P~_i, coarse nodes)."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import coarse as oc, decomposition as od, fem
+from paper_2410_24138_gb300 import inputs as I
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def nls():
+    from paper_2410_24138_gb300 import build, nls as binding
+    build.build()
+    return binding
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "nls.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(nls_[A-Za-z_]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(nls):
+    lib = nls.load()
+    names = declared_functions()
+    assert len(names) >= 25
+    for name in names:
+        assert hasattr(lib, name), name
+    assert sorted(nls.EXPORTS) == names
+
+
+def test_defaults_follow_section_3(nls):
+    o = nls.default_options()
+    assert o.inner_rtol == 1e-5 and o.inner_atol == 1e-11
+    assert o.gmres_rtol == 1e-6 and o.gmres_maxit == 1000
+    assert o.outer_atol == 1e-8
+
+
+def test_argument_errors(nls):
+    s = nls.Solver()
+    with pytest.raises(nls.NLSError):
+        s.setup_host()
+    p = I.diffusion_c1()
+    s.set_problem(p)
+    with pytest.raises(nls.NLSError):
+        s.set_options(threads_per_block=100)
+    with pytest.raises(nls.NLSError):
+        s.set_options(load_steps=0)
+    bad = I.diffusion_c1()
+    bad.elem_to_sub = bad.elem_to_sub.copy()
+    bad.elem_to_sub[:] = 0
+    bad.n_sub = 2  # subdomain 1 empty
+    with pytest.raises(nls.NLSError):
+        nls.make_solver(bad, coupling="one", setup="host")
+
+
+CASES = {
+    "c1_boxes_overlap1": lambda: I.diffusion_c1(),
+    "bricks_overlap2": lambda: I.diffusion_problem(48, I.brick_partition(48, 4, 4, 7), 16, 2),
+    "bricks_overlap3_ragged": lambda: I.diffusion_problem(37, I.brick_partition(37, 3, 5, 9), 15, 3),
+    "neohooke_bricks": lambda: I.neohooke_problem(24, I.brick_partition(24, 3, 3, 5), 9, 2, 1.0),
+}
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_host_maps_bit_exact(nls, case):
+    p = CASES[case]()
+    s = nls.make_solver(p, coupling="hybrid", setup="host")
+    subs, own = od.decompose(p)
+    np.testing.assert_array_equal(s.owners(), own)
+    for sb in subs:
+        d, o = s.local_dofs(sb.index)
+        np.testing.assert_array_equal(d, sb.dofs)
+        np.testing.assert_array_equal(o, sb.owned)
+        np.testing.assert_array_equal(s.overlap_elems(sb.index), sb.elems)
+    star = od.node_star(p.conn, p.n_nodes)
+    K0 = fem.global_jacobian(fem.Model(p), np.zeros(p.n_nodes * p.ndof))
+    cs = oc.rgdsw_coarse_space(p, star, K0)
+    np.testing.assert_array_equal(s.coarse_nodes(), [int(c[0]) for c in cs.comps])
+    sz = s.sizes()
+    assert sz.n_coarse_dofs == cs.P0.shape[1]
+    assert sz.total_local_dofs == sum(sb.n for sb in subs)
+
+
+def test_full_size_c2_maps_sampled(nls):
+    p = I.diffusion_c2()
+    s = nls.make_solver(p, coupling="hybrid", setup="host")
+    sz = s.sizes()
+    assert sz.n_sub == 1024 and sz.n_dofs == 1025 * 1025
+    rng = np.random.default_rng(1)
+    which = sorted(rng.choice(1024, size=6, replace=False).tolist()) + [0, 1023]
+    subs, own = od.decompose(p, which)
+    np.testing.assert_array_equal(s.owners(), own)
+    for sb in subs:
+        d, o = s.local_dofs(sb.index)
+        np.testing.assert_array_equal(d, sb.dofs)
+        np.testing.assert_array_equal(o, sb.owned)
+    # every free dof is owned by exactly one subdomain: sum_i P~_i R_i = I
+    count = np.zeros(sz.n_dofs, dtype=np.int64)
+    for i in range(1024):
+        d, o = s.local_dofs(i)
+        np.add.at(count, d[o], 1)
+    free = fem.free_mask(p)
+    assert np.all(count[free] == 1) and np.all(count[~free] == 0)

@@ -1,0 +1,172 @@
+"""Parity of the sm_103a path (through the C ABI) with the FP64 oracle.
+
+Tolerances (derived in the design notes):
+* F(u) of Eq. 3: both sides evaluate the same element formulas in FP64 and only the
+  summation order differs -> 1e-13 relative to max |F|.
+* the coarse basis: FP64 energy-minimising extension, band LU without pivoting against a
+  sparse LU -> 1e-11 absolute (basis values are O(1)).
+* F_x (Eqs. 5, 10, 11) with both sides' local and coarse Newton loops driven to 1e-14:
+  1e-9 relative.  The FP32-factor path refines to the same FP64 residual -> same bound.
+* the tangent (Eqs. 6, 12): FP64 factors 1e-9; FP32 factors refined to 1e-10 -> 1e-7.
+* converged solutions: 1e-8 (FP64 path) and 1e-6 (FP32 + refinement) relative l2, the
+  bounds the benchmark spec's target states; both sides are driven to ||F|| < 1e-12 first so that
+  the bound measures the method, not the stopping test.
+"""
+import numpy as np
+import pytest
+
+from oracle import coarse as oc, decomposition as od, fem, schwarz as S
+from paper_2410_24138_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def nls():
+    from paper_2410_24138_gb300 import build, nls as binding
+    build.build()
+    return binding
+
+
+TIGHT = dict(inner_rtol=1e-14, inner_atol=1e-15)
+
+
+def _random_state(p, seed, scale):
+    rng = np.random.default_rng(seed)
+    free = fem.free_mask(p)
+    return np.where(free, scale * rng.random(p.n_nodes * p.ndof), 0.0), free
+
+
+def _small_problems():
+    return {
+        "c1": I.diffusion_c1(),
+        "brick": I.diffusion_problem(40, I.brick_partition(40, 3, 4, 11), 12, 2),
+        "nh": I.neohooke_problem(16, I.brick_partition(16, 2, 3, 5), 6, 2, traction_max=4.0),
+    }
+
+
+@pytest.mark.parametrize("name", ["c1", "brick", "nh"])
+def test_global_residual(nls, name):
+    p = _small_problems()[name]
+    s = nls.make_solver(p, coupling="one")
+    u, _ = _random_state(p, 1, 0.05)
+    for load in (1.0, 0.4):
+        F = s.eval_F(u, load)
+        Fo = fem.global_residual(fem.Model(p), u, load)
+        assert np.max(np.abs(F - Fo)) <= 1e-13 * np.max(np.abs(Fo))
+
+
+@pytest.mark.parametrize("name", ["c1", "brick", "nh"])
+def test_coarse_basis(nls, name):
+    p = _small_problems()[name]
+    s = nls.make_solver(p, coupling="hybrid")
+    star = od.node_star(p.conn, p.n_nodes)
+    K0 = fem.global_jacobian(fem.Model(p), np.zeros(p.n_nodes * p.ndof))
+    cs = oc.rgdsw_coarse_space(p, star, K0)
+    np.testing.assert_array_equal(s.coarse_nodes(), [int(c[0]) for c in cs.comps])
+    P0 = s.coarse_basis()
+    assert P0.shape == cs.P0.shape
+    assert np.max(np.abs(P0 - cs.P0.toarray())) < 1e-11
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("coupling", ["one", "add", "hybrid"])
+@pytest.mark.parametrize("name", ["c1", "brick", "nh"])
+def test_Fx_and_tangent(nls, name, coupling, precision):
+    p = _small_problems()[name]
+    s = nls.make_solver(p, coupling=coupling, precision=precision, **TIGHT)
+    sw = S.Schwarz(p, S.Options(coupling=coupling, **TIGHT))
+    scale = 0.05 if p.ndof == 1 else 0.01
+    u, free = _random_state(p, 2, scale)
+    load = 1.0 if p.ndof == 1 else 0.6
+    Fx, its, st = s.eval_Fx(u, load)
+    Fo, sto = sw.evaluate(u, load)
+    assert np.all(st == 0)
+    assert np.linalg.norm(Fx - Fo) <= 1e-9 * np.linalg.norm(Fo)
+    # local Newton iteration counts agree (same rules, same FP64 residual tests)
+    its_o = np.array([r.its for r in sto["local"]])
+    assert np.max(np.abs(its - its_o)) <= 1
+    v, _ = _random_state(p, 3, 1.0)
+    y = s.apply_tangent(v)
+    yo = sw.tangent(sto)(v)
+    # FP64 factors: 1e-9.  FP32 factors refined to 1e-10: 1e-7 for Eq. 1, whose local Jacobian is
+    # assembled in FP64; Eq. 2 assembles the element tangents in FP32 in this form, so the tangent
+    # itself carries a relative perturbation of a few unit roundoffs of FP32 (bound 1e-5).
+    tol = 1e-9 if precision == "fp64" else (1e-7 if p.ndof == 1 else 1e-5)
+    assert np.linalg.norm(y - yo) <= tol * np.linalg.norm(yo)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("coupling", ["one", "hybrid", "add"])
+def test_converged_solution_c1(nls, coupling, precision):
+    p = I.diffusion_c1()
+    ustar, _ = S.plain_newton(p, tol=1e-14)
+    s = nls.make_solver(p, coupling=coupling, precision=precision, outer_atol=1e-12, inner_atol=1e-15)
+    u, rep = s.solve()
+    assert rep.status == 0 and rep.final_residual < 1e-12
+    tol = 1e-8 if precision == "fp64" else 1e-6
+    assert np.linalg.norm(u - ustar) / np.linalg.norm(ustar) < tol
+    # the oracle's own iteration: same outer iteration count
+    sw = S.Schwarz(p, S.Options(coupling=coupling, outer_atol=1e-12, inner_atol=1e-15))
+    _, hist, _ = sw.solve()
+    outer = [h for h in hist if "gmres_its" in h]
+    assert abs(rep.outer_iterations - len(outer)) <= 1
+    assert rep.subdomain_newton_steps > 0 and rep.kernel_launches > 0
+
+
+def test_metric_tolerance_c1(nls):
+    """The configuration the metric is quoted on, at C1 size: ||F|| < 1e-8 from u = 0."""
+    p = I.diffusion_c1()
+    s = nls.make_solver(p, coupling="hybrid", precision="fp32")
+    u, rep = s.solve()
+    assert rep.status == 0 and rep.final_residual < 1e-8
+    F = fem.global_residual(fem.Model(p), u)
+    assert np.linalg.norm(F) < 1e-8
+    assert 2 <= rep.outer_iterations <= 5
+
+
+def test_single_subdomain(nls):
+    """One subdomain: T_1(u) = u - u*, so F_1(u) = u - u* and DF_1 = I."""
+    p = I.diffusion_problem(16, I.box_partition(16, 1, 1), 1, 1)
+    ustar, _ = S.plain_newton(p, tol=1e-15)
+    s = nls.make_solver(p, coupling="one", precision="fp64", **TIGHT)
+    u, _ = _random_state(p, 4, 0.02)
+    Fx, _, st = s.eval_Fx(u)
+    assert np.all(st == 0)
+    np.testing.assert_allclose(Fx, u - ustar, atol=1e-13)
+    v, _ = _random_state(p, 5, 1.0)
+    np.testing.assert_allclose(s.apply_tangent(v), v, atol=1e-12)
+
+
+def test_neohooke_load_steps(nls):
+    p = I.neohooke_problem(16, I.brick_partition(16, 2, 2, 3), 4, 2, traction_max=8.0, load_steps=5)
+    ustar, _ = S.plain_newton(p, tol=1e-12, load_steps=5)
+    for precision, tol in (("fp64", 1e-8), ("fp32", 1e-6)):
+        s = nls.make_solver(p, coupling="hybrid", precision=precision, outer_atol=1e-10, gmres_maxit=100)
+        u, rep = s.solve()
+        assert rep.status == 0
+        assert np.linalg.norm(u - ustar) / np.linalg.norm(ustar) < tol
+
+
+def test_device_arrays(nls):
+    torch = pytest.importorskip("torch")
+    p = I.diffusion_c1()
+    s = nls.make_solver(p, coupling="hybrid")
+    u = torch.zeros(p.n_nodes, dtype=torch.float64, device="cuda")
+    u, rep = s.solve(u)
+    assert rep.final_residual < 1e-8
+    F = fem.global_residual(fem.Model(p), u.cpu().numpy())
+    assert np.linalg.norm(F) < 1e-8
+
+
+def test_bad_arguments(nls):
+    s = nls.Solver()
+    with pytest.raises(nls.NLSError):
+        s.setup()
+    p = I.diffusion_c1()
+    s.set_problem(p)
+    with pytest.raises(nls.NLSError):
+        s.set_options(threads_per_block=100)
+    with pytest.raises(nls.NLSError):
+        s.set_options(coupling=1)  # additive without a coarse space
+        s.setup()
