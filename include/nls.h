@@ -106,8 +106,9 @@ typedef struct nls_ctx nls_ctx;
 /* Fill *opt with the defaults described above. */
 void nls_options_default(nls_options* opt);
 
-/* Create a context on CUDA device `device`, using `cuda_stream` (a cudaStream_t, or NULL for
- * a stream the library creates).  *out receives the context. */
+/* Create a context on CUDA device `device`.  Every kernel and copy of the context is issued
+ * on `cuda_stream` (a cudaStream_t; NULL selects the legacy default stream).  Device arrays
+ * passed to the context must be ready on that stream.  *out receives the context. */
 int nls_create(nls_ctx** out, int device, void* cuda_stream);
 void nls_destroy(nls_ctx* ctx);
 const char* nls_strerror(int status);

@@ -1152,12 +1152,10 @@ int device_setup(Context& c) {
     Dev* Dp = new Dev();
     c.dev = Dp;
     Dev& D = *Dp;
-    if (c.stream) {
-      D.s = (cudaStream_t)c.stream;
-    } else {
-      CK(cudaStreamCreateWithFlags(&D.s, cudaStreamNonBlocking));
-      c.own_stream = true;
-    }
+    // NULL selects the legacy default stream, which orders against every blocking stream of
+    // the caller (a torch tensor filled on the default stream is complete before we read it).
+    D.s = (cudaStream_t)c.stream;
+    c.own_stream = false;
     cudaDeviceProp prop;
     CK(cudaGetDeviceProperties(&prop, c.device));
     D.nsm = prop.multiProcessorCount;
