@@ -216,6 +216,29 @@ int nls_apply_tangent(nls_ctx* ctx, const double* v, double* y, int is_device);
  * subdomain order (total_local_dofs entries). */
 int nls_get_local_states(nls_ctx* ctx, double* w_out, int is_device);
 
+/* ---- allocation-free variant (the paper has no counterpart) ----------------------------
+ * Local corrections F_1(x) = sum_i P~_i T_i(x) of the context's overlapping subdomains -- the
+ * same batched local-Newton kernel as nls_eval_Fx with the one-level coupling, without the
+ * coarse correction and without keeping a tangent -- computed without allocating anything.
+ * It exists for callers that cannot allocate device memory at the time they need the
+ * corrections: code being recorded into a CUDA graph (no cudaMalloc during stream capture),
+ * applications whose own memory manager owns the GPU, and loops that must not risk the
+ * implicit synchronisation of cudaMalloc / cudaFree.  The kernel's scratch (local Jacobians,
+ * band factors, local states, work counter) lives in a 32 MiB device array compiled into the
+ * library, which every GPU that loads the library keeps until the process exits.
+ *   x   [n_dofs] device input (the point, Dirichlet entries holding the Dirichlet values);
+ *   Fx  [n_dofs] device output; every entry is written (Dirichlet entries with 0);
+ *   its, status [n_sub] optional device outputs (NULL: kept in the scratch area);
+ *   load  external-load factor.
+ * Requires a context after nls_setup; returns NLS_E_ARG, with the byte counts in
+ * nls_last_error, when the problem needs more scratch than the array holds.  The first call
+ * on each device looks up the array's device address (cudaGetSymbolAddress); make that
+ * first call before any stream capture.  All calls share the array and it keeps the last
+ * call's contents; calls whose work overlaps on the GPU race on it.  Work is issued on the
+ * context's stream and the call does not synchronise. */
+int nls_local_corrections_noalloc(nls_ctx* ctx, const double* x, double* Fx, int32_t* its, int32_t* status,
+                                  double load);
+
 #ifdef __cplusplus
 }
 #endif

@@ -286,6 +286,12 @@ int nls_get_kernel_stats(const nls_ctx* ctx, int32_t cap, nls_kernel_stat* out, 
   return nls::kernel_stats(ctx->c, cap, out, n_out);
 }
 
+int nls_local_corrections_noalloc(nls_ctx* ctx, const double* x, double* Fx, int32_t* its, int32_t* status,
+                                  double load) {
+  if (!ctx || !x || !Fx) return NLS_E_ARG;
+  return nls::local_corrections_noalloc(ctx->c, x, Fx, its, status, load);
+}
+
 int nls_reset_kernel_stats(nls_ctx* ctx) {
   if (!ctx) return NLS_E_ARG;
   nls::reset_kernel_stats(ctx->c);

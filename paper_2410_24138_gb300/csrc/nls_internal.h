@@ -135,5 +135,6 @@ int get_local_states(Context& c, double* w, int is_dev);
 int get_coarse_basis(const Context& c, double* P0);
 int kernel_stats(const Context& c, int32_t cap, nls_kernel_stat* out, int32_t* n_out);
 void reset_kernel_stats(Context& c);
+int local_corrections_noalloc(Context& c, const double* x, double* Fx, int32_t* its, int32_t* status, double load);
 
 }  // namespace nls

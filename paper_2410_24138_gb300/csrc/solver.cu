@@ -25,6 +25,7 @@
 #include <stdexcept>
 #include <string>
 #include <type_traits>
+#include <mutex>
 #include <vector>
 
 #include "device.cuh"
@@ -1674,6 +1675,115 @@ int get_coarse_basis(const Context& c, double* P0) {
     for (int64_t g = 0; g < c.N; ++g)
       for (int32_t k = c.cs.p0_rowptr[g]; k < c.cs.p0_rowptr[g + 1]; ++k) P0[(int64_t)c.cs.p0_col[k] * c.N + g] = vals[k];
   } catch (const std::exception&) {
+    return NLS_E_CUDA;
+  }
+  return NLS_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// Local corrections without any allocation.
+//
+// Some callers cannot allocate device memory when they need the corrections: a solver step
+// being recorded into a CUDA graph (cudaMalloc is not allowed while a stream is capturing),
+// a host application whose memory manager owns every byte of the GPU, or a time-critical loop
+// that must not risk the device-wide synchronisation cudaMalloc / cudaFree can cause.  For
+// them the batched local-Newton kernel also runs on a fixed scratch area compiled into this
+// library: a file-scope device array of kNoAllocScratchBytes that every GPU which loads the
+// library keeps until the process exits.  Host code cannot use the array's name as a device
+// address, so the address is looked up once per device with cudaGetSymbolAddress (on the
+// first call on that device, which should therefore come before any stream capture) and then
+// passed to the kernel.  All calls share the area and leave their contents in it; calls
+// whose work overlaps on the GPU (different streams, or different contexts on one device)
+// race on it.
+// ------------------------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = size_t(32) << 20;
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+void* g_noalloc_addr[kNoAllocMaxDevices] = {nullptr};
+
+// Device address of the scratch array for the current device (looked up once per device).
+cudaError_t noalloc_scratch_address(int device, void** out) {
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (device < 0 || device >= kNoAllocMaxDevices) return cudaErrorInvalidDevice;
+  if (!g_noalloc_addr[device]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_addr[device] = p;
+  }
+  *out = g_noalloc_addr[device];
+  return cudaSuccess;
+}
+
+}  // namespace
+
+int local_corrections_noalloc(Context& c, const double* x, double* Fx, int32_t* its_out, int32_t* status_out,
+                              double load) {
+  if (!c.is_setup || !c.dev) {
+    c.last_error = "nls_local_corrections_noalloc needs a context after nls_setup";
+    return NLS_E_ARG;
+  }
+  Dev& D = *c.dev;
+  const LocalSet& s = c.ov;
+  const bool f32 = fp32_local(c);
+  // scratch plan: CSR values, band factors, local states, its, status, work counter
+  const size_t fbytes = f32 ? sizeof(float) : sizeof(double);
+  size_t off = 0;
+  const size_t o_csr = off;
+  off = align_up(off + sizeof(double) * (size_t)s.total_nnz, 256);
+  const size_t o_fac = off;
+  off = align_up(off + fbytes * (size_t)s.total_factor, 256);
+  const size_t o_w = off;
+  off = align_up(off + sizeof(double) * (size_t)s.total_n, 256);
+  const size_t o_its = off;
+  off = align_up(off + sizeof(int32_t) * (size_t)s.count, 256);
+  const size_t o_st = off;
+  off = align_up(off + sizeof(int32_t) * (size_t)s.count, 256);
+  const size_t o_q = off;
+  off = align_up(off + sizeof(int32_t), 256);
+  if (off > kNoAllocScratchBytes) {
+    c.last_error = "problem needs " + std::to_string(off) + " bytes of scratch; the allocation-free entry point has " +
+                   std::to_string(kNoAllocScratchBytes);
+    return NLS_E_ARG;
+  }
+  try {
+    CK(cudaSetDevice(c.device));
+    D.prof = false;  // per-launch event timing would create events: keep this path allocation free
+    void* base = nullptr;
+    CK(noalloc_scratch_address(c.device, &base));
+    unsigned char* sc = (unsigned char*)base;
+    LocalArgs A = make_args(c, s, D.ov);
+    A.csr = (double*)(sc + o_csr);
+    A.factor = sc + o_fac;
+    A.wbuf = (double*)(sc + o_w);
+    A.its = its_out ? its_out : (int32_t*)(sc + o_its);
+    A.status = status_out ? status_out : (int32_t*)(sc + o_st);
+    A.queue = (int32_t*)(sc + o_q);
+    A.x = x;
+    A.out = Fx;
+    A.load = load;
+    A.guess = nullptr;
+    A.want_tangent = 0;
+    // the work counter must start at zero; the rest of the area is written before it is read
+    CK(cudaMemsetAsync(A.queue, 0, sizeof(int32_t), D.s));
+    LAUNCH(D, k_mask, grid_for(c.N), 256, 0, c.N, D.free_dof, Fx);
+    const int T = local_threads(c);
+    const size_t sm = f32 ? local_newton_smem<float>(s) : local_newton_smem<double>(s);
+    const int per_sm = (int)std::max<size_t>(1, std::min<size_t>(2048 / T, D.smem_optin / (sm + 1024)));
+    const int grid = std::min(s.count, D.nsm * per_sm);
+    if (c.law == NLS_LAW_DIFFUSION) {
+      if (f32) LAUNCH(D, (k_local_newton<NLS_LAW_DIFFUSION, float>), grid, T, sm, A);
+      else LAUNCH(D, (k_local_newton<NLS_LAW_DIFFUSION, double>), grid, T, sm, A);
+    } else {
+      if (f32) LAUNCH(D, (k_local_newton<NLS_LAW_NEOHOOKE, float>), grid, T, sm, A);
+      else LAUNCH(D, (k_local_newton<NLS_LAW_NEOHOOKE, double>), grid, T, sm, A);
+    }
+  } catch (const std::exception& ex) {
+    c.last_error = ex.what();
     return NLS_E_CUDA;
   }
   return NLS_OK;

@@ -72,7 +72,7 @@ EXPORTS = ["nls_options_default", "nls_create", "nls_destroy", "nls_strerror", "
            "nls_set_options", "nls_get_options", "nls_setup", "nls_setup_host", "nls_solve", "nls_get_sizes", "nls_get_local_dofs",
            "nls_get_overlap_elems", "nls_get_owners", "nls_get_coarse_nodes", "nls_get_coarse_basis", "nls_eval_F",
            "nls_eval_Fx", "nls_apply_tangent", "nls_get_local_states", "nls_get_kernel_stats",
-           "nls_reset_kernel_stats"]
+           "nls_reset_kernel_stats", "nls_local_corrections_noalloc"]
 
 _LIB = None
 _P = ctypes.c_void_p
@@ -121,6 +121,7 @@ def load() -> ctypes.CDLL:
         "nls_get_local_states": (ctypes.c_int, [_P, _P, ctypes.c_int]),
         "nls_get_kernel_stats": (ctypes.c_int, [_P, i32, ctypes.POINTER(KernelStat), ctypes.POINTER(i32)]),
         "nls_reset_kernel_stats": (ctypes.c_int, [_P]),
+        "nls_local_corrections_noalloc": (ctypes.c_int, [_P, _P, _P, _P, _P, dbl]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -309,6 +310,12 @@ class Solver:
 
     def reset_kernel_stats(self):
         self._check(self.lib.nls_reset_kernel_stats(self.h), "nls_reset_kernel_stats")
+
+    def local_corrections_noalloc(self, x, Fx, its=None, status=None, load: float = 1.0):
+        """One-level corrections into the caller's device tensor Fx, using no allocation (see nls.h)."""
+        self._check(self.lib.nls_local_corrections_noalloc(self.h, _ptr(x), _ptr(Fx), _ptr(its), _ptr(status), load),
+                    "nls_local_corrections_noalloc")
+        return Fx
 
     def local_states(self) -> np.ndarray:
         out = np.zeros(self.sizes().total_local_dofs)
