@@ -188,8 +188,8 @@ int nls_set_options(nls_ctx* ctx, const nls_options* o) {
     return fail(ctx, NLS_E_ARG, "unknown precision");
   if (o->load_steps < 1 || o->gmres_restart < 1 || o->gmres_maxit < 1 || o->inner_maxit < 0 || o->ls_trials < 1)
     return fail(ctx, NLS_E_ARG, "bad iteration limits");
-  if (o->threads_per_block != 0 && (o->threads_per_block < 64 || o->threads_per_block > 1024 || o->threads_per_block % 32))
-    return fail(ctx, NLS_E_ARG, "threads_per_block must be 0 or a multiple of 32 in [64, 1024]");
+  if (o->threads_per_block != 0 && (o->threads_per_block < 64 || o->threads_per_block > 512 || o->threads_per_block % 32))
+    return fail(ctx, NLS_E_ARG, "threads_per_block must be 0 or a multiple of 32 in [64, 512]");
   ctx->c.opt = *o;
   return NLS_OK;
 }

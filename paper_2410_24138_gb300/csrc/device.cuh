@@ -281,79 +281,235 @@ __device__ int band_lu(int n, int b, const RowSource& src, FT* __restrict__ F, F
 }
 
 // ------------------------------------------------------------------------------------------
-// Triangular solves with the band factors, in place on y[0..n) (shared memory).
+// In-place band LU with asynchronous row staging.  F holds the assembled band rows on entry
+// (row-major, W = 2b + 1) and the factors on exit (layout as above).  Rows are copied into the
+// shared-memory ring with cp.async PD rows ahead of use, so the global-memory latency of a
+// row overlaps the PD elimination steps before it is needed; each row is read exactly once
+// and written back exactly once.
+// smem: win [(b + 2 + PD) * W], rp [b + 2 + PD], flag [1].
 // ------------------------------------------------------------------------------------------
 template <typename FT>
-__device__ void band_solve(int n, int b, const FT* __restrict__ F, FT* y) {
-  const int W = 2 * b + 1, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  // forward: L (unit lower)
-  for (int k0 = 0; k0 < n; k0 += 32) {
-    const int kb = min(32, n - k0);
+__device__ inline void cp_async_elem(FT* sdst, const FT* gsrc) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
+  if (sizeof(FT) == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gsrc) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gsrc) : "memory");
+}
+__device__ inline void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ inline void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// One warp stages band row `row` (if it exists) into dst and commits one copy group per lane.
+template <typename FT>
+__device__ inline void stage_row_async(int row, int n, int W, const FT* F, FT* dst) {
+  const int lane = threadIdx.x & 31;
+  if (row < n) {
+    const FT* src = F + (int64_t)row * W;
+    for (int d = lane; d < W; d += 32) cp_async_elem<FT>(dst + d, src + d);
+  }
+  cp_async_commit();
+}
+
+constexpr int kLuPrefetch = 8;
+
+template <typename FT>
+__device__ int band_lu_inplace(int n, int b, FT* __restrict__ F, FT* win, FT* rp, int* flag) {
+  constexpr int PD = kLuPrefetch;
+  const int W = 2 * b + 1, R = b + 2 + PD;
+  const int tid = threadIdx.x, T = blockDim.x, wid = tid >> 5;
+  if (n <= 0) return 0;
+  if (tid == 0) *flag = 0;
+  if (wid == 0) {
+    for (int i = 0; i <= b + PD; ++i) stage_row_async<FT>(i, n, W, F, win + (i % R) * W);
+    cp_async_wait<PD>();
+  }
+  __syncthreads();
+  if (tid == 0) {
+    const FT p = win[b];
+    if (!(p != (FT)0) || !isfinite((double)p)) *flag = 1;
+    rp[0] = (FT)1 / p;
+  }
+  __syncthreads();
+  const int bb = b * b;
+  const int dq = (b > 0) ? T / b : 0, dr = (b > 0) ? T % b : 0;
+  const int ri0 = (b > 0) ? tid / b : 0, cj0 = (b > 0) ? tid % b : 0;
+  for (int k = 0; k < n; ++k) {
+    const int sk = k % R;
+    const FT* rowk = win + sk * W;
+    const FT rpk = rp[sk];
+    const int lim = min(b, n - 1 - k);
     if (wid == 0) {
-      FT yl = (lane < kb) ? y[k0 + lane] : (FT)0;
-      FT Lrow[32];
-#pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        const int d = j - lane + b;
-        Lrow[j] = (j < lane && lane < kb && d >= 0) ? F[(int64_t)(k0 + lane) * W + d] : (FT)0;
+      // row k is final: write it back in place (scaled L part, reciprocal pivot, U part)
+      FT* out = F + (int64_t)k * W;
+      for (int d = tid; d < W; d += 32) {
+        const int j = k - b + d;
+        FT v = rowk[d];
+        if (d < b) v = (j >= 0) ? v * rp[j % R] : (FT)0;
+        else if (d == b) v = rpk;
+        out[d] = v;
       }
+      // stage row k + b + 1 + PD into the slot row k - 1 used
+      stage_row_async<FT>(k + b + 1 + PD, n, W, F, win + ((k + b + 1 + PD) % R) * W);
+    }
+    if (lim > 0) {
+      const int base = (k + 1) % R;
+      int ri = ri0, cj = cj0;
+      for (int idx = tid; idx < bb; idx += T) {
+        if (ri < lim && cj < lim) {
+          int slot = base + ri;
+          if (slot >= R) slot -= R;
+          FT* rowi = win + slot * W;
+          const FT l = rowi[b - 1 - ri] * rpk;
+          const FT nv = rowi[cj - ri + b] - l * rowk[b + 1 + cj];
+          rowi[cj - ri + b] = nv;
+          if (idx == 0) {
+            if (!(nv != (FT)0) || !isfinite((double)nv)) *flag = 1;
+            rp[(k + 1) % R] = (FT)1 / nv;
+          }
+        }
+        cj += dr;
+        ri += dq;
+        if (cj >= b) {
+          cj -= b;
+          ri += 1;
+        }
+      }
+    } else if (tid == 0 && k + 1 < n) {
+      const FT nv = win[((k + 1) % R) * W + b];
+      if (!(nv != (FT)0) || !isfinite((double)nv)) *flag = 1;
+      rp[(k + 1) % R] = (FT)1 / nv;
+    }
+    // rows up to k + b + 1 must have landed before step k + 1
+    if (wid == 0) cp_async_wait<PD>();
+    __syncthreads();
+  }
+  if (wid == 0) cp_async_wait<0>();
+  __syncthreads();
+  return *flag;
+}
+
+// ------------------------------------------------------------------------------------------
+// Triangular solves with the band factors, in place on y[0..n) (shared memory).
+// ------------------------------------------------------------------------------------------
+// Block size of the triangular solves: 32 rows (one warp) for FP32 factors, 16 for FP64
+// (two register sets of BS values per thread stay within the register budget).
+template <typename FT>
+struct SolveBlock {
+  static constexpr int BS = sizeof(FT) == 4 ? 32 : 16;
+};
+
+// The factor values of block k0 + BS are loaded into registers while block k0 is solved, so
+// the global-memory latency of the next block overlaps the current one.
+//
+// Roles: warp 0 solves the BS x BS diagonal block; threads 32 .. 32 + b - 1 each own one of the
+// b rows coupled to the block.  Both roles keep their current and next values in the same two
+// register arrays (Dcur/Dnxt), so a thread holds 2 BS values.  Needs blockDim.x >= 32 + b.
+template <typename FT>
+__device__ void band_solve(int n, int b, const FT* __restrict__ F, FT* y) {
+  constexpr int BS = SolveBlock<FT>::BS;
+  const int W = 2 * b + 1, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const bool diag = wid == 0;
+  const bool offd = tid >= 32 && tid < 32 + b;
+  const int r = tid - 32;
+  FT cur[BS], nxt[BS];
+  // forward (unit lower L): block k0 = rows [k0, k0 + kb)
+#define NLS_LOAD_FWD(k0_, R_)                                                             \
+  {                                                                                       \
+    const int kb_ = min(BS, n - (k0_));                                                   \
+    if (diag) {                                                                           \
+      _Pragma("unroll") for (int j = 0; j < BS; ++j) {                                    \
+        const int d = j - lane + b;                                                       \
+        R_[j] = (j < lane && lane < kb_ && d >= 0) ? F[(int64_t)((k0_) + lane) * W + d] : (FT)0; \
+      }                                                                                   \
+    } else if (offd) {                                                                    \
+      const int i_ = (k0_) + kb_ + r;                                                     \
+      _Pragma("unroll") for (int j = 0; j < BS; ++j) {                                    \
+        const int d = j + b - kb_ - r;                                                    \
+        R_[j] = (i_ < n && j < kb_ && d >= 0) ? F[(int64_t)i_ * W + d] : (FT)0;           \
+      }                                                                                   \
+    }                                                                                     \
+  }
+  if (n > 0) NLS_LOAD_FWD(0, cur);
+  for (int k0 = 0; k0 < n; k0 += BS) {
+    const int kb = min(BS, n - k0);
+    if (k0 + BS < n) NLS_LOAD_FWD(k0 + BS, nxt);
+    if (diag) {
+      FT yl = (lane < kb) ? y[k0 + lane] : (FT)0;
 #pragma unroll
-      for (int j = 0; j < 32; ++j) {
+      for (int j = 0; j < BS; ++j) {
         const FT yj = __shfl_sync(0xffffffffu, yl, j);
-        if (j < kb) yl -= Lrow[j] * yj;
+        if (j < kb) yl -= cur[j] * yj;
       }
       if (lane < kb) y[k0 + lane] = yl;
     }
     __syncthreads();
-    // rows k0+kb .. k0+kb+b-1 take the contribution of the finished block
-    for (int r = tid; r < b; r += blockDim.x) {
+    if (offd) {
       const int i = k0 + kb + r;
       if (i < n) {
-        const int j0 = max(k0, i - b);
         FT acc = 0;
-        const FT* Fi = F + (int64_t)i * W + (j0 - i + b);
-        for (int j = j0; j < k0 + kb; ++j) acc += Fi[j - j0] * y[j];
+#pragma unroll
+        for (int j = 0; j < BS; ++j)
+          if (j < kb) acc += cur[j] * y[k0 + j];
         y[i] -= acc;
       }
     }
     __syncthreads();
+#pragma unroll
+    for (int j = 0; j < BS; ++j) cur[j] = nxt[j];
   }
-  // backward: U (diagonal stored inverted)
-  for (int k1 = n; k1 > 0; k1 -= 32) {
-    const int k0 = max(0, k1 - 32), kb = k1 - k0;
-    if (wid == 0) {
+#undef NLS_LOAD_FWD
+  // backward (U, diagonal stored inverted): block rows [k0, k1)
+#define NLS_LOAD_BWD(k1_, R_)                                                             \
+  {                                                                                       \
+    const int k0_ = max(0, (k1_) - BS), kb_ = (k1_) - k0_;                                \
+    if (diag) {                                                                           \
+      _Pragma("unroll") for (int j = 0; j < BS; ++j) {                                    \
+        const int d = j - lane + b;                                                       \
+        R_[j] = (j >= lane && lane < kb_ && j < kb_ && d <= 2 * b) ? F[(int64_t)(k0_ + lane) * W + d] : (FT)0; \
+      }                                                                                   \
+    } else if (offd) {                                                                    \
+      const int i_ = k0_ - 1 - r;                                                         \
+      _Pragma("unroll") for (int j = 0; j < BS; ++j) {                                    \
+        R_[j] = (i_ >= 0 && j < kb_ && j + 1 + r <= b) ? F[(int64_t)i_ * W + (j + 1 + r + b)] : (FT)0; \
+      }                                                                                   \
+    }                                                                                     \
+  }
+  if (n > 0) NLS_LOAD_BWD(n, cur);
+  for (int k1 = n; k1 > 0; k1 -= BS) {
+    const int k0 = max(0, k1 - BS), kb = k1 - k0;
+    if (k0 > 0) NLS_LOAD_BWD(k0, nxt);
+    if (diag) {
       FT yl = (lane < kb) ? y[k0 + lane] : (FT)0;
-      FT Urow[32];
 #pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        const int d = j - lane + b;
-        Urow[j] = (j >= lane && lane < kb && j < kb && d <= 2 * b) ? F[(int64_t)(k0 + lane) * W + d] : (FT)0;
-      }
-#pragma unroll
-      for (int j = 31; j >= 0; --j) {
+      for (int j = BS - 1; j >= 0; --j) {
         if (j < kb) {
-          // lane j finishes x_j = y_j / U_jj, then everyone above subtracts U[l][j] x_j
-          FT xj = (lane == j) ? yl * Urow[j] : (FT)0;
+          FT xj = (lane == j) ? yl * cur[j] : (FT)0;
           xj = __shfl_sync(0xffffffffu, xj, j);
           if (lane == j) yl = xj;
-          else if (lane < j) yl -= Urow[j] * xj;
+          else if (lane < j) yl -= cur[j] * xj;
         }
       }
       if (lane < kb) y[k0 + lane] = yl;
     }
     __syncthreads();
-    for (int r = tid; r < b; r += blockDim.x) {
+    if (offd) {
       const int i = k0 - 1 - r;
       if (i >= 0) {
-        const int j1 = min(k1 - 1, i + b);
         FT acc = 0;
-        const FT* Fi = F + (int64_t)i * W + (k0 - i + b);
-        for (int j = k0; j <= j1; ++j) acc += Fi[j - k0] * y[j];
+#pragma unroll
+        for (int j = 0; j < BS; ++j)
+          if (j < kb) acc += cur[j] * y[k0 + j];
         y[i] -= acc;
       }
     }
     __syncthreads();
+#pragma unroll
+    for (int j = 0; j < BS; ++j) cur[j] = nxt[j];
   }
+#undef NLS_LOAD_BWD
 }
 
 }  // namespace dev

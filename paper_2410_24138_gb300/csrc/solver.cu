@@ -103,8 +103,8 @@ __host__ __device__ inline SmemPlan smem_plan(int max_n, int max_nt, int max_b, 
   p.s = o; o += sizeof(double) * max_n;
   p.red = o; o += sizeof(double) * 40;
   p.yv = o; o += align_up(sizeof(FT) * max_n, 16);
-  p.win = o; o += with_window ? align_up(sizeof(FT) * (size_t)(max_b + 2) * (2 * max_b + 1), 16) : 0;
-  p.rp = o; o += with_window ? align_up(sizeof(FT) * (max_b + 2), 16) : 0;
+  p.win = o; o += with_window ? align_up(sizeof(FT) * (size_t)(max_b + 2 + dev::kLuPrefetch) * (2 * max_b + 1), 16) : 0;
+  p.rp = o; o += with_window ? align_up(sizeof(FT) * (max_b + 2 + dev::kLuPrefetch), 16) : 0;
   p.flag = o; o += 16;
   p.total = o;
   return p;
@@ -160,11 +160,17 @@ __device__ bool local_residual(const LocalArgs& A, const SubMeta& m, const doubl
   return __syncthreads_and(ok ? 1 : 0) != 0;
 }
 
-// Local Jacobian into the CSR block of the subdomain (rows per m.nrows).
-template <int LAW, typename JT>
-__device__ void local_jacobian(const LocalArgs& A, const SubMeta& m, const double* xt, double* csr) {
-  const int nen = A.nen, ned = nen * A.ndof, ned2 = ned * ned;
+// Local Jacobian into the CSR block of the subdomain (rows per m.nrows) and, when `band` is
+// given, also into the band rows of the local matrix (row-major, 2 b + 1 per row, local
+// unknowns only) that the in-place band LU then factors.
+template <int LAW, typename JT, typename FT = double>
+__device__ void local_jacobian(const LocalArgs& A, const SubMeta& m, const double* xt, double* csr,
+                               FT* band = nullptr) {
+  const int nen = A.nen, nd = A.ndof, ned = nen * nd, ned2 = ned * ned;
+  const int W = 2 * m.b + 1, n = m.n;
   for (int64_t k = threadIdx.x; k < m.nnz; k += blockDim.x) csr[k] = 0.0;
+  if (band)
+    for (int64_t k = threadIdx.x; k < (int64_t)n * W; k += blockDim.x) band[k] = (FT)0;
   __syncthreads();
   const int32_t* cp = A.color_ptr + m.color_off;
   for (int c = 0; c < m.ncolor; ++c) {
@@ -181,6 +187,13 @@ __device__ void local_jacobian(const LocalArgs& A, const SubMeta& m, const doubl
 #pragma unroll
         for (int q = 0; q < 9; ++q)
           if (ep[q] >= 0) csr[ep[q]] += K[q];
+        if (band) {
+#pragma unroll
+          for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b)
+              if (lc[a] < n && lc[b] < n) band[(int64_t)lc[a] * W + (lc[b] - lc[a] + m.b)] += (FT)K[a * 3 + b];
+        }
       } else {
         const double* geo = A.geom + (int64_t)gid * 40;
         double ue[8];
@@ -194,6 +207,21 @@ __device__ void local_jacobian(const LocalArgs& A, const SubMeta& m, const doubl
 #pragma unroll
         for (int q = 0; q < 64; ++q)
           if (ep[q] >= 0) csr[ep[q]] += (double)K[q];
+        if (band) {
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b)
+              if (lc[a] < m.nV && lc[b] < m.nV) {
+#pragma unroll
+                for (int da = 0; da < 2; ++da)
+#pragma unroll
+                  for (int db = 0; db < 2; ++db) {
+                    const int row = 2 * lc[a] + da, col = 2 * lc[b] + db;
+                    band[(int64_t)row * W + (col - row + m.b)] += (FT)K[(2 * a + da) * 8 + 2 * b + db];
+                  }
+              }
+        }
       }
     }
     __syncthreads();
@@ -242,7 +270,7 @@ __device__ int local_solve(const LocalArgs& A, const SubMeta& m, const int32_t* 
 // k_local_newton: the batched local corrections T_i of Eq. 4
 // ------------------------------------------------------------------------------------------
 template <int LAW, typename FT>
-__global__ void __launch_bounds__(1024) k_local_newton(LocalArgs A) {
+__global__ void __launch_bounds__(512) k_local_newton(LocalArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
   const SmemPlan P = smem_plan<FT>(A.max_n, A.max_nt, A.max_b, true);
   double* xt = (double*)(smem + P.xt);
@@ -290,9 +318,8 @@ __global__ void __launch_bounds__(1024) k_local_newton(LocalArgs A) {
         status = ST_MAXIT;
         break;
       }
-      local_jacobian<LAW, JT>(A, m, xt, csr);
-      dev::RowSource src{rowptr, colidx, csr};
-      if (dev::band_lu<FT>(n, m.b, src, F, win, rp, flag)) {
+      local_jacobian<LAW, JT, FT>(A, m, xt, csr, F);
+      if (dev::band_lu_inplace<FT>(n, m.b, F, win, rp, flag)) {
         status = ST_PIVOT;
         break;
       }
@@ -328,9 +355,8 @@ __global__ void __launch_bounds__(1024) k_local_newton(LocalArgs A) {
       rn = rtn;
     }
     if (A.want_tangent && status != ST_NONFINITE && status != ST_PIVOT) {
-      local_jacobian<LAW, JT>(A, m, xt, csr);
-      dev::RowSource src{rowptr, colidx, csr};
-      if (dev::band_lu<FT>(n, m.b, src, F, win, rp, flag)) status = ST_PIVOT;
+      local_jacobian<LAW, JT, FT>(A, m, xt, csr, F);
+      if (dev::band_lu_inplace<FT>(n, m.b, F, win, rp, flag)) status = ST_PIVOT;
     }
     for (int a = tid; a < n; a += blockDim.x) {
       wb[a] = xt[a];
@@ -354,7 +380,7 @@ __global__ void __launch_bounds__(1024) k_local_newton(LocalArgs A) {
 // k_local_apply: out[owned] = (R_i DF(v_i) P_i)^-1 R_i DF(v_i) v  (+ add[owned])
 // ------------------------------------------------------------------------------------------
 template <typename FT>
-__global__ void __launch_bounds__(1024) k_local_apply(LocalArgs A) {
+__global__ void __launch_bounds__(512) k_local_apply(LocalArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
   const SmemPlan P = smem_plan<FT>(A.max_n, A.max_nt, A.max_b, false);
   double* yt = (double*)(smem + P.xt);
@@ -392,7 +418,7 @@ __global__ void __launch_bounds__(1024) k_local_apply(LocalArgs A) {
 // coarse space: harmonic extension (setup) and Galerkin blocks
 // ------------------------------------------------------------------------------------------
 template <int LAW>
-__global__ void __launch_bounds__(1024) k_harmonic(LocalArgs A) {
+__global__ void __launch_bounds__(512) k_harmonic(LocalArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
   const SmemPlan P = smem_plan<double>(A.max_n, A.max_nt, A.max_b, true);
   double* xt = (double*)(smem + P.xt);
@@ -499,16 +525,18 @@ template <typename FT>
 __global__ void __launch_bounds__(1024) k_coarse_factor(int N0, int b0, const double* A0, FT* F, int* status) {
   extern __shared__ __align__(16) unsigned char smem[];
   FT* win = (FT*)smem;
-  FT* rp = win + (size_t)(b0 + 2) * (2 * b0 + 1);
-  int* flag = (int*)(rp + b0 + 2);
-  dev::RowSource src{nullptr, nullptr, A0};
-  const int bad = dev::band_lu<FT>(N0, b0, src, F, win, rp, flag);
+  FT* rp = win + (size_t)(b0 + 2 + dev::kLuPrefetch) * (2 * b0 + 1);
+  int* flag = (int*)(rp + b0 + 2 + dev::kLuPrefetch);
+  const int64_t total = (int64_t)N0 * (2 * b0 + 1);
+  for (int64_t k = threadIdx.x; k < total; k += blockDim.x) F[k] = (FT)A0[k];
+  __syncthreads();
+  const int bad = dev::band_lu_inplace<FT>(N0, b0, F, win, rp, flag);
   if (threadIdx.x == 0) *status = bad ? ST_PIVOT : ST_OK;
 }
 
 // coarse solve z = A0^-1 g (global-memory vectors), FP64 refinement against the band A0
 template <typename FT>
-__global__ void __launch_bounds__(1024) k_coarse_solve(int N0, int b0, const double* A0, const FT* F, const double* g,
+__global__ void __launch_bounds__(256) k_coarse_solve(int N0, int b0, const double* A0, const FT* F, const double* g,
                                                        double* z, double* res, FT* y, double ir_rtol, int ir_max) {
   __shared__ double red[40];
   const int W = 2 * b0 + 1;
@@ -1006,7 +1034,8 @@ LocalArgs coarse_args(Context& c) {
 
 size_t coarse_factor_smem(const Context& c, bool f32) {
   const size_t fs = f32 ? sizeof(float) : sizeof(double);
-  return fs * ((size_t)(c.cs.b0 + 2) * (2 * c.cs.b0 + 1) + c.cs.b0 + 2) + 16;
+  const size_t R = (size_t)c.cs.b0 + 2 + dev::kLuPrefetch;
+  return fs * (R * (2 * c.cs.b0 + 1) + R) + 16;
 }
 
 // A_0(x) = P_0^T DF(x) P_0 -> band -> factor.  Returns false on a bad pivot.
@@ -1034,10 +1063,10 @@ bool coarse_matrix(Context& c, const double* x) {
 void coarse_solve(Context& c, const double* g, double* z) {
   Dev& D = *c.dev;
   if (fp32_coarse(c))
-    LAUNCH(D, k_coarse_solve<float>, 1, 1024, 0, c.cs.N0, c.cs.b0, D.A0, (const float*)D.A0f, g, z, D.cres,
+    LAUNCH(D, k_coarse_solve<float>, 1, 256, 0, c.cs.N0, c.cs.b0, D.A0, (const float*)D.A0f, g, z, D.cres,
            (float*)D.cy, c.opt.ir_rtol, c.opt.ir_max_sweeps);
   else
-    LAUNCH(D, k_coarse_solve<double>, 1, 1024, 0, c.cs.N0, c.cs.b0, D.A0, (const double*)D.A0f, g, z, D.cres,
+    LAUNCH(D, k_coarse_solve<double>, 1, 256, 0, c.cs.N0, c.cs.b0, D.A0, (const double*)D.A0f, g, z, D.cres,
            (double*)D.cy, c.opt.ir_rtol, c.opt.ir_max_sweeps);
 }
 
