@@ -203,6 +203,7 @@ def run_gpu(args):
         s.set_coarse(nls.COARSE_RGDSW)
         s.set_options(coupling=nls.COUPLING["hybrid"], load_steps=p.load_steps,
                       local_precision=nls.PREC_FP32_IR if precision == "fp32" else nls.PREC_FP64,
+                      coarse_precision=nls.PREC_FP32_IR if precision == "fp32" else nls.PREC_FP64,
                       profile_kernels=profile)
         t0 = time.perf_counter()
         s.setup()
@@ -240,7 +241,9 @@ def run_gpu(args):
     timed_solves(torch, prof, n_dofs, 1, flush_buf)
     prof.reset_kernel_stats()
     ptimes, preps = timed_solves(torch, prof, n_dofs, 1, flush_buf)
-    kstats = prof.kernel_stats()
+    kstats_all = prof.kernel_stats()
+    phases = {k[6:]: round(v[1], 3) for k, v in kstats_all.items() if k.startswith("phase:")}
+    kstats = {k: v for k, v in kstats_all.items() if not k.startswith("phase:")}
     prof.close()
 
     # plain FP64 form on the same mesh
@@ -281,7 +284,7 @@ def run_gpu(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
-            "config": {"workload": desc, "coupling": "hybrid", "precision": "FP32 band factors + FP64 refinement",
+            "config": {"workload": desc, "coupling": "hybrid", "precision": "FP32 local and coarse band factors + FP64 iterative refinement; FP64 residuals, GMRES, coarse matrix",
                        "l2": "512 MB buffer written between steps; working set > L2",
                        "parallelism": "replicas" if world > 1 else "single GPU", "setup_s": setup_s,
                        "n_dofs": n_dofs, "n_sub": sizes.n_sub, "coarse_dofs": sizes.n_coarse_dofs},
@@ -295,6 +298,7 @@ def run_gpu(args):
                            "final_residual": rep0.final_residual, "local_failures": rep0.local_failures},
             "phases_s": {"inner": rep0.time_inner_s, "coarse": rep0.time_coarse_s, "gmres": rep0.time_gmres_s,
                          "other": rep0.time_other_s},
+            "local_newton_phases_cta_ms": phases,
             "kernels_ms": {k: [v[0], round(v[1], 3), round(100.0 * v[1] / total_prof_ms, 1)] for k, v in
                            sorted(kstats.items(), key=lambda kv: -kv[1][1])[:8]},
             "roofline": roof,

@@ -216,6 +216,53 @@ int nls_apply_tangent(nls_ctx* ctx, const double* v, double* y, int is_device);
  * subdomain order (total_local_dofs entries). */
 int nls_get_local_states(nls_ctx* ctx, double* w_out, int is_device);
 
+/* ---- learned initial guess (not in the paper) ------------------------------------------
+ * A small fully connected network proposes the starting point of every local Newton solve
+ * (Eq. 4).  Inputs (391 values per subdomain, structured P1 meshes of Eq. 1 only): the local
+ * Dirichlet data on the ring of nodes around the box of local unknowns, sampled at 33 points
+ * on each of its four sides, log k sampled on 16 x 16 points of the box, f, and the box width
+ * and height.  Output: a 32 x 32 correction, on a canonical grid of the box, to the Coons
+ * (bilinear transfinite) patch of the side data; the guess at a node is the patch plus the
+ * bilinearly interpolated correction.  Layers: 391 -> h1 -> h2 -> 1024, tanh-form GELU.
+ * Training: BF16 operands on the tensor cores with FP32 accumulation, FP32 master weights,
+ * Adam, loss 1/(2B) sum ||y - t||^2 on normalised inputs and targets.  Inference: FP32.
+ * A guess is used only where its local residual is smaller than that of R_i x (the start the
+ * method uses otherwise), so convergence to tolerance does not depend on the network.
+ * The network lives on one device; every array below is a host pointer. */
+typedef struct nls_guess_net nls_guess_net;
+#define NLS_GUESS_FEATURES 391
+#define NLS_GUESS_OUTPUTS 1024
+#define NLS_GUESS_USE 1      /* propose starting points in nls_solve / nls_eval_Fx */
+#define NLS_GUESS_HARVEST 2  /* record (features, converged local state) pairs after every local solve */
+
+/* Create a network with hidden widths h1, h2 (multiples of 16), weights drawn from splitmix64
+ * `seed`, on `device`, with room for `capacity` training pairs. */
+int nls_guess_create(nls_guess_net** out, int device, int32_t h1, int32_t h2, uint64_t seed, int64_t capacity);
+void nls_guess_destroy(nls_guess_net* net);
+/* Attach a network to a context (after nls_setup) with NLS_GUESS_* mode bits, or detach (net NULL). */
+int nls_guess_attach(nls_ctx* ctx, nls_guess_net* net, int32_t mode);
+/* Train on the harvested pairs: `steps` Adam steps on random minibatches of `batch` pairs
+ * (splitmix64 `seed`), learning rate lr.  loss_out[steps] (may be NULL) receives the losses. */
+int nls_guess_train(nls_guess_net* net, int32_t steps, int32_t batch, double lr, uint64_t seed, float* loss_out);
+/* Number of harvested pairs. */
+int nls_guess_pairs(const nls_guess_net* net, int64_t* n_out);
+/* Parameters as one FP32 array in the order W1 [h1 x 391], b1, W2 [h2 x h1], b2, W3 [1024 x h2],
+ * b3 (row-major); *count receives the length.  set_params also resets the Adam state. */
+int nls_guess_get_params(const nls_guess_net* net, float* params, int64_t* count);
+int nls_guess_set_params(nls_guess_net* net, const float* params, int64_t count);
+/* Normalisation of inputs and targets: x_norm = (x - mean) / scale per input, t_norm = t / tscale. */
+int nls_guess_get_normalisation(const nls_guess_net* net, float* mean, float* scale, float* tscale);
+int nls_guess_set_normalisation(nls_guess_net* net, const float* mean, const float* scale, float tscale);
+/* Gradient of the loss on a given batch of normalised inputs X [B x 391] and targets
+ * T [B x 1024] (host arrays), in the parameter order above, with FP32 (precision 0) or BF16
+ * (precision 1) GEMM operands; *loss receives the loss.  Test hook for the gradient checks. */
+int nls_guess_gradient(nls_guess_net* net, int32_t B, const float* X, const float* T, int32_t precision, float* grad,
+                       float* loss);
+/* Network output (FP32 inference) for normalised inputs X [B x 391] into Y [B x 1024]. */
+int nls_guess_forward(nls_guess_net* net, int32_t B, const float* X, float* Y);
+/* Guesses proposed and accepted by the local solves since the last call (then reset). */
+int nls_guess_counts(nls_ctx* ctx, int64_t* proposed, int64_t* accepted);
+
 /* ---- allocation-free variant (the paper has no counterpart) ----------------------------
  * Local corrections F_1(x) = sum_i P~_i T_i(x) of the context's overlapping subdomains -- the
  * same batched local-Newton kernel as nls_eval_Fx with the one-level coupling, without the

@@ -292,6 +292,16 @@ int nls_local_corrections_noalloc(nls_ctx* ctx, const double* x, double* Fx, int
   return nls::local_corrections_noalloc(ctx->c, x, Fx, its, status, load);
 }
 
+int nls_guess_attach(nls_ctx* ctx, nls_guess_net* net, int32_t mode) {
+  if (!ctx) return NLS_E_ARG;
+  return nls::guess_attach(ctx->c, net, mode);
+}
+
+int nls_guess_counts(nls_ctx* ctx, int64_t* proposed, int64_t* accepted) {
+  if (!ctx) return NLS_E_ARG;
+  return nls::guess_counts(ctx->c, proposed, accepted);
+}
+
 int nls_reset_kernel_stats(nls_ctx* ctx) {
   if (!ctx) return NLS_E_ARG;
   nls::reset_kernel_stats(ctx->c);

@@ -1,0 +1,146 @@
+// Device-side state of one solver context and the launch / error helpers shared by the
+// translation units that launch kernels (solver.cu, guess.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "nls_internal.h"
+
+namespace nls {
+
+struct CudaFailure : std::runtime_error {
+  explicit CudaFailure(const std::string& s) : std::runtime_error(s) {}
+};
+
+#define CK(call)                                                                                  \
+  do {                                                                                            \
+    cudaError_t e_ = (call);                                                                      \
+    if (e_ != cudaSuccess) throw ::nls::CudaFailure(std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+#define LAUNCH(D, kernel, grid, block, smem, ...)                          \
+  do {                                                                     \
+    const bool prof_ = (D).prof;                                           \
+    if (prof_) (D).prof_begin(#kernel);                                    \
+    kernel<<<(grid), (block), (smem), (D).s>>>(__VA_ARGS__);               \
+    if (prof_) (D).prof_end();                                             \
+    (D).launches += 1;                                                     \
+    CK(cudaGetLastError());                                                \
+  } while (0)
+
+// ------------------------------------------------------------------------------------------
+// device state
+// ------------------------------------------------------------------------------------------
+struct Dev {
+  cudaStream_t s = nullptr;
+  std::vector<void*> allocs;
+  int64_t bytes = 0;
+  int64_t launches = 0;
+  int nsm = 152;
+  size_t smem_optin = 0;
+  template <typename T>
+  T* alloc(size_t n) {
+    void* p = nullptr;
+    if (n == 0) n = 1;
+    CK(cudaMalloc(&p, n * sizeof(T)));
+    allocs.push_back(p);
+    bytes += (int64_t)(n * sizeof(T));
+    return (T*)p;
+  }
+  template <typename T>
+  T* upload(const std::vector<T>& v) {
+    T* p = alloc<T>(v.size());
+    if (!v.empty()) CK(cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+    return p;
+  }
+  void release(void* p) {
+    for (auto& q : allocs)
+      if (q == p) {
+        cudaFree(q);
+        q = nullptr;
+      }
+  }
+  // mesh
+  int32_t *conn = nullptr, *g_elem = nullptr, *g_rowptr = nullptr, *g_col = nullptr, *g_epos = nullptr;
+  double *geom = nullptr, *kcoef = nullptr, *fext = nullptr, *ubc = nullptr, *g_val = nullptr;
+  uint8_t* free_dof = nullptr;
+  DeviceLocalSet ov, nov;
+  // coarse
+  int32_t *p0_rowptr = nullptr, *p0_col = nullptr, *p0t_rowptr = nullptr, *p0t_col = nullptr, *p0t_src = nullptr;
+  int64_t* p0_src = nullptr;
+  double *p0_val = nullptr, *p0t_val = nullptr, *phi = nullptr, *Y = nullptr, *blk = nullptr, *A0 = nullptr;
+  int64_t *phi_off = nullptr, *blk_off = nullptr, *a0_src = nullptr;
+  int32_t *cj_ptr = nullptr, *a0_ptr = nullptr;
+  void* A0f = nullptr;
+  void* A0dinv = nullptr;
+  int32_t* cstatus = nullptr;
+  // vectors
+  double *u = nullptr, *x = nullptr, *u0 = nullptr, *Fx = nullptr, *F = nullptr, *t1 = nullptr, *t2 = nullptr,
+         *w0 = nullptr, *gx = nullptr;
+  double *c = nullptr, *ct = nullptr, *dc = nullptr, *g = nullptr, *gt = nullptr, *cres = nullptr;
+  void* cy = nullptr;
+  double *V = nullptr, *partial = nullptr, *scal = nullptr, *coef = nullptr;
+  int* bad = nullptr;
+  unsigned long long* phase = nullptr;  // k_local_newton phase clocks (profiling)
+  double* ainv = nullptr;               // explicit A_0^-1 (transposed) for the tangent phase
+  double* gpart = nullptr;              // GEMV chunk partials
+  bool ainv_valid = false;
+  int clock_khz = 1;
+  double* h_scal = nullptr;  // pinned
+  int m = 0;                 // GMRES restart length allocated
+  bool tangent_ready = false;
+  void* guess = nullptr;  // learned-guess attachment (guess.cu)
+  double last_load = 1.0;
+  // per-launch CUDA-event timing (nls_options.profile_kernels)
+  bool prof = false;
+  struct EvRec {
+    cudaEvent_t a, b;
+    const char* name;
+  };
+  std::vector<EvRec> evs;
+  size_t ev_used = 0;
+  struct Stat {
+    std::string name;
+    int64_t launches;
+    double ms;
+  };
+  std::vector<Stat> stats;
+  void prof_begin(const char* name) {
+    if (ev_used == evs.size()) {
+      EvRec r;
+      CK(cudaEventCreate(&r.a));
+      CK(cudaEventCreate(&r.b));
+      evs.push_back(r);
+    }
+    evs[ev_used].name = name;
+    CK(cudaEventRecord(evs[ev_used].a, s));
+  }
+  void prof_end() {
+    CK(cudaEventRecord(evs[ev_used].b, s));
+    ++ev_used;
+    if (ev_used >= 65536) prof_flush();
+  }
+  void prof_flush() {
+    if (!ev_used) return;
+    CK(cudaStreamSynchronize(s));
+    for (size_t i = 0; i < ev_used; ++i) {
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, evs[i].a, evs[i].b));
+      Stat* st = nullptr;
+      for (auto& x : stats)
+        if (x.name == evs[i].name) st = &x;
+      if (!st) {
+        stats.push_back(Stat{evs[i].name, 0, 0.0});
+        st = &stats.back();
+      }
+      st->launches += 1;
+      st->ms += ms;
+    }
+    ev_used = 0;
+  }
+};
+
+}  // namespace nls

@@ -315,17 +315,23 @@ __device__ inline void stage_row_async(int row, int n, int W, const FT* F, FT* d
 
 constexpr int kLuPrefetch = 8;
 
-template <typename FT>
-__device__ int band_lu_inplace(int n, int b, FT* __restrict__ F, FT* win, FT* rp, int* flag) {
+// Thread mapping of one elimination step: warp w updates rows k+1+ri with ri = w, w + NW, ...;
+// lane l updates columns k+1+cj with cj = l, l + 32, ... (CJ slots, b <= 32 CJ).  Each thread
+// loads its pivot-row values once per step and its multiplier once per row, so the inner
+// work is one shared load, one FMA and one shared store per matrix entry.
+template <typename FT, int CJ>
+__device__ int band_lu_inplace_cj(int n, int b, FT* __restrict__ F, FT* win, FT* rp, int* flag) {
   constexpr int PD = kLuPrefetch;
   const int W = 2 * b + 1, R = b + 2 + PD;
-  const int tid = threadIdx.x, T = blockDim.x, wid = tid >> 5;
-  if (n <= 0) return 0;
+  const int tid = threadIdx.x, T = blockDim.x, lane = tid & 31, wid = tid >> 5, NW = T >> 5;
   if (tid == 0) *flag = 0;
-  if (wid == 0) {
-    for (int i = 0; i <= b + PD; ++i) stage_row_async<FT>(i, n, W, F, win + (i % R) * W);
-    cp_async_wait<PD>();
+  // stage rows 0 .. b + PD (one copy group per row and thread)
+  for (int i = 0; i <= b + PD; ++i) {
+    if (i < n)
+      for (int d = tid; d < W; d += T) cp_async_elem<FT>(win + i * W + d, F + (int64_t)i * W + d);
+    cp_async_commit();
   }
+  cp_async_wait<PD>();
   __syncthreads();
   if (tid == 0) {
     const FT p = win[b];
@@ -333,62 +339,72 @@ __device__ int band_lu_inplace(int n, int b, FT* __restrict__ F, FT* win, FT* rp
     rp[0] = (FT)1 / p;
   }
   __syncthreads();
-  const int bb = b * b;
-  const int dq = (b > 0) ? T / b : 0, dr = (b > 0) ? T % b : 0;
-  const int ri0 = (b > 0) ? tid / b : 0, cj0 = (b > 0) ? tid % b : 0;
+  int sk = 0, s1 = 1;  // ring slots of rows k and k + 1 (R >= b + 2 >= 2)
   for (int k = 0; k < n; ++k) {
-    const int sk = k % R;
     const FT* rowk = win + sk * W;
     const FT rpk = rp[sk];
     const int lim = min(b, n - 1 - k);
-    if (wid == 0) {
-      // row k is final: write it back in place (scaled L part, reciprocal pivot, U part)
-      FT* out = F + (int64_t)k * W;
-      for (int d = tid; d < W; d += 32) {
-        const int j = k - b + d;
-        FT v = rowk[d];
-        if (d < b) v = (j >= 0) ? v * rp[j % R] : (FT)0;
-        else if (d == b) v = rpk;
-        out[d] = v;
+    // row k is final: write it back in place (scaled L part, reciprocal pivot, U part)
+    for (int d = tid; d < W; d += T) {
+      FT v = rowk[d];
+      if (d < b) {
+        int sj = sk - b + d;
+        if (sj < 0) sj += R;
+        v = (k - b + d >= 0) ? v * rp[sj] : (FT)0;
+      } else if (d == b) {
+        v = rpk;
       }
-      // stage row k + b + 1 + PD into the slot row k - 1 used
-      stage_row_async<FT>(k + b + 1 + PD, n, W, F, win + ((k + b + 1 + PD) % R) * W);
+      F[(int64_t)k * W + d] = v;
     }
-    if (lim > 0) {
-      const int base = (k + 1) % R;
-      int ri = ri0, cj = cj0;
-      for (int idx = tid; idx < bb; idx += T) {
-        if (ri < lim && cj < lim) {
-          int slot = base + ri;
-          if (slot >= R) slot -= R;
-          FT* rowi = win + slot * W;
-          const FT l = rowi[b - 1 - ri] * rpk;
-          const FT nv = rowi[cj - ri + b] - l * rowk[b + 1 + cj];
-          rowi[cj - ri + b] = nv;
-          if (idx == 0) {
-            if (!(nv != (FT)0) || !isfinite((double)nv)) *flag = 1;
-            rp[(k + 1) % R] = (FT)1 / nv;
-          }
-        }
-        cj += dr;
-        ri += dq;
-        if (cj >= b) {
-          cj -= b;
-          ri += 1;
-        }
+    // stage row k + b + 1 + PD into the slot row k - 1 used
+    {
+      const int rs = k + b + 1 + PD;
+      const int ss = (sk == 0) ? R - 1 : sk - 1;
+      if (rs < n)
+        for (int d = tid; d < W; d += T) cp_async_elem<FT>(win + ss * W + d, F + (int64_t)rs * W + d);
+      cp_async_commit();
+    }
+    // rank-1 update of rows k+1..k+lim, columns k+1..k+lim: warp w takes rows w, w+NW, ...,
+    // lane l takes columns l, l+32, ...; one shared load, FMA and store per entry
+    FT u[CJ];
+#pragma unroll
+    for (int c = 0; c < CJ; ++c) u[c] = (lane + 32 * c < lim) ? rowk[b + 1 + lane + 32 * c] : (FT)0;
+    for (int ri = wid; ri < lim; ri += NW) {
+      int slot = s1 + ri;
+      if (slot >= R) slot -= R;
+      FT* rowi = win + slot * W + b - ri;
+      const FT l = rowi[-1] * rpk;
+#pragma unroll
+      for (int c = 0; c < CJ; ++c) {
+        const int cj = lane + 32 * c;
+        if (cj < lim) rowi[cj] -= l * u[c];
       }
-    } else if (tid == 0 && k + 1 < n) {
-      const FT nv = win[((k + 1) % R) * W + b];
+    }
+    // thread 0 updated the new pivot A[k+1][k+1] itself (row 0, column 0 of the update)
+    if (tid == 0 && k + 1 < n) {
+      const FT nv = win[s1 * W + b];
       if (!(nv != (FT)0) || !isfinite((double)nv)) *flag = 1;
-      rp[(k + 1) % R] = (FT)1 / nv;
+      rp[s1] = (FT)1 / nv;
     }
     // rows up to k + b + 1 must have landed before step k + 1
-    if (wid == 0) cp_async_wait<PD>();
+    cp_async_wait<PD>();
     __syncthreads();
+    sk = s1;
+    s1 = (s1 + 1 == R) ? 0 : s1 + 1;
   }
-  if (wid == 0) cp_async_wait<0>();
+  cp_async_wait<0>();
   __syncthreads();
   return *flag;
+}
+
+// Dispatch on the number of column slots per lane (half bandwidth up to 128).
+template <typename FT>
+__device__ int band_lu_inplace(int n, int b, FT* __restrict__ F, FT* win, FT* rp, int* flag) {
+  if (n <= 0) return 0;
+  if (b <= 32) return band_lu_inplace_cj<FT, 1>(n, b, F, win, rp, flag);
+  if (b <= 64) return band_lu_inplace_cj<FT, 2>(n, b, F, win, rp, flag);
+  if (b <= 96) return band_lu_inplace_cj<FT, 3>(n, b, F, win, rp, flag);
+  return band_lu_inplace_cj<FT, 4>(n, b, F, win, rp, flag);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -510,6 +526,184 @@ __device__ void band_solve(int n, int b, const FT* __restrict__ F, FT* y) {
     for (int j = 0; j < BS; ++j) cur[j] = nxt[j];
   }
 #undef NLS_LOAD_BWD
+}
+
+// ------------------------------------------------------------------------------------------
+// Explicit inverses of the BS x BS diagonal blocks of the band factors.  Block t (rows
+// t BS .. t BS + bs - 1) stores inv(L_tt) then inv(U_tt), each BS x BS row-major (padded with
+// the identity beyond bs), so that the solve replaces the BS-step dependent shuffle chain of a
+// diagonal block by one short dot product per row.  One warp per block; `tmp` holds
+// (BS x (BS + 1)) FT per warp that takes part (`nwarps`).
+// ------------------------------------------------------------------------------------------
+template <typename FT>
+__device__ void band_diag_inverses(int n, int b, const FT* __restrict__ F, FT* __restrict__ Dinv, FT* tmp, int nwarps) {
+  constexpr int BS = SolveBlock<FT>::BS;
+  const int W = 2 * b + 1, lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nblk = (n + BS - 1) / BS;
+  if (wid < nwarps) {
+    FT* M = tmp + wid * BS * (BS + 1);
+    for (int t = wid; t < nblk; t += nwarps) {
+      const int k0 = t * BS, bs = min(BS, n - k0);
+      FT* out = Dinv + (int64_t)t * 2 * BS * BS;
+      // lower: M[i][j] = L[k0+i][k0+j] (j < i), unit diagonal
+      for (int e = lane; e < BS * BS; e += 32) {
+        const int i = e / BS, j = e % BS;
+        FT v = (FT)0;
+        if (i < bs && j < i && i - j <= b) v = F[(int64_t)(k0 + i) * W + (j - i + b)];
+        M[i * (BS + 1) + j] = v;
+      }
+      __syncwarp();
+      if (lane < BS) {
+        // column `lane` of inv(L): forward substitution with e_lane
+        FT x[BS];
+#pragma unroll
+        for (int i = 0; i < BS; ++i) {
+          FT acc = (i == lane) ? (FT)1 : (FT)0;
+#pragma unroll
+          for (int j = 0; j < i; ++j) acc -= M[i * (BS + 1) + j] * x[j];
+          x[i] = acc;
+        }
+#pragma unroll
+        for (int i = 0; i < BS; ++i) out[i * BS + lane] = x[i];
+      }
+      __syncwarp();
+      // upper: M[i][j] = U[k0+i][k0+j] (j > i), M[i][i] = 1/U_ii (stored reciprocal)
+      for (int e = lane; e < BS * BS; e += 32) {
+        const int i = e / BS, j = e % BS;
+        FT v = (i == j) ? (FT)1 : (FT)0;
+        if (i < bs && j < bs && j >= i && j - i <= b) v = F[(int64_t)(k0 + i) * W + (j - i + b)];
+        M[i * (BS + 1) + j] = v;
+      }
+      __syncwarp();
+      if (lane < BS) {
+        // column `lane` of inv(U): backward substitution with e_lane (diagonal given inverted)
+        FT x[BS];
+#pragma unroll
+        for (int i = BS - 1; i >= 0; --i) {
+          FT acc = (i == lane) ? (FT)1 : (FT)0;
+#pragma unroll
+          for (int j = i + 1; j < BS; ++j) acc -= M[i * (BS + 1) + j] * x[j];
+          x[i] = acc * M[i * (BS + 1) + i];
+        }
+        FT* ou = out + BS * BS;
+#pragma unroll
+        for (int i = 0; i < BS; ++i) ou[i * BS + lane] = x[i];
+      }
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+}
+
+// Triangular solves with the band factors and the explicit diagonal-block inverses: warp 0
+// applies the block inverse (lane l: row l of inv(L_tt) or inv(U_tt) dotted with the block of
+// y), threads 32 .. 32 + b - 1 apply the coupling to the next b rows.  Register prefetch of
+// the next block as in band_solve.  Needs blockDim.x >= 32 + b.
+template <typename FT>
+__device__ void band_solve_inv(int n, int b, const FT* __restrict__ F, const FT* __restrict__ Dinv, FT* y) {
+  constexpr int BS = SolveBlock<FT>::BS;
+  const int W = 2 * b + 1, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const bool diag = wid == 0 && lane < BS;
+  const bool offd = tid >= 32 && tid < 32 + b;
+  const int r = tid - 32;
+  FT cur[BS], nxt[BS];
+#define NLS_LOAD_FWDI(k0_, R_)                                                            \
+  {                                                                                       \
+    const int kb_ = min(BS, n - (k0_));                                                   \
+    if (diag) {                                                                           \
+      const FT* Li_ = Dinv + (int64_t)((k0_) / BS) * 2 * BS * BS + lane * BS;             \
+      _Pragma("unroll") for (int j = 0; j < BS; ++j) R_[j] = Li_[j];                      \
+    } else if (offd) {                                                                    \
+      const int i_ = (k0_) + kb_ + r;                                                     \
+      _Pragma("unroll") for (int j = 0; j < BS; ++j) {                                    \
+        const int d = j + b - kb_ - r;                                                    \
+        R_[j] = (i_ < n && j < kb_ && d >= 0) ? F[(int64_t)i_ * W + d] : (FT)0;           \
+      }                                                                                   \
+    }                                                                                     \
+  }
+  if (n > 0) NLS_LOAD_FWDI(0, cur);
+  for (int k0 = 0; k0 < n; k0 += BS) {
+    const int kb = min(BS, n - k0);
+    if (k0 + BS < n) NLS_LOAD_FWDI(k0 + BS, nxt);
+    if (wid == 0) {  // the whole warp reaches __syncwarp; only lanes < BS hold a block row
+      FT a0 = 0, a1 = 0;
+      if (diag) {
+#pragma unroll
+        for (int j = 0; j < BS; j += 2) {
+          a0 += cur[j] * ((j < kb) ? y[k0 + j] : (FT)0);
+          a1 += cur[j + 1] * ((j + 1 < kb) ? y[k0 + j + 1] : (FT)0);
+        }
+      }
+      __syncwarp();
+      if (lane < kb) y[k0 + lane] = a0 + a1;
+    }
+    __syncthreads();
+    if (offd) {
+      const int i = k0 + kb + r;
+      if (i < n) {
+        FT a0 = 0, a1 = 0;
+#pragma unroll
+        for (int j = 0; j < BS; j += 2) {
+          if (j < kb) a0 += cur[j] * y[k0 + j];
+          if (j + 1 < kb) a1 += cur[j + 1] * y[k0 + j + 1];
+        }
+        y[i] -= a0 + a1;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < BS; ++j) cur[j] = nxt[j];
+  }
+#undef NLS_LOAD_FWDI
+#define NLS_LOAD_BWDI(t_, R_)                                                             \
+  {                                                                                       \
+    const int k0_ = (t_) * BS, kb_ = min(BS, n - k0_);                                     \
+    if (diag) {                                                                           \
+      const FT* Ui_ = Dinv + (int64_t)(t_) * 2 * BS * BS + BS * BS + lane * BS;          \
+      _Pragma("unroll") for (int j = 0; j < BS; ++j) R_[j] = Ui_[j];                      \
+    } else if (offd) {                                                                    \
+      const int i_ = k0_ - 1 - r;                                                         \
+      _Pragma("unroll") for (int j = 0; j < BS; ++j) {                                    \
+        R_[j] = (i_ >= 0 && j < kb_ && j + 1 + r <= b) ? F[(int64_t)i_ * W + (j + 1 + r + b)] : (FT)0; \
+      }                                                                                   \
+    }                                                                                     \
+  }
+  // blocks are aligned to multiples of BS (the last one may be partial), as in the inverses
+  const int nblk = (n + BS - 1) / BS;
+  if (n > 0) NLS_LOAD_BWDI(nblk - 1, cur);
+  for (int t = nblk - 1; t >= 0; --t) {
+    const int k0 = t * BS, k1 = min(n, k0 + BS), kb = k1 - k0;
+    if (t > 0) NLS_LOAD_BWDI(t - 1, nxt);
+    if (wid == 0) {  // the whole warp reaches __syncwarp; only lanes < BS hold a block row
+      FT a0 = 0, a1 = 0;
+      if (diag) {
+#pragma unroll
+        for (int j = 0; j < BS; j += 2) {
+          a0 += cur[j] * ((j < kb) ? y[k0 + j] : (FT)0);
+          a1 += cur[j + 1] * ((j + 1 < kb) ? y[k0 + j + 1] : (FT)0);
+        }
+      }
+      __syncwarp();
+      if (lane < kb) y[k0 + lane] = a0 + a1;
+    }
+    __syncthreads();
+    if (offd) {
+      const int i = k0 - 1 - r;
+      if (i >= 0) {
+        FT a0 = 0, a1 = 0;
+#pragma unroll
+        for (int j = 0; j < BS; j += 2) {
+          if (j < kb) a0 += cur[j] * y[k0 + j];
+          if (j + 1 < kb) a1 += cur[j + 1] * y[k0 + j + 1];
+        }
+        y[i] -= a0 + a1;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < BS; ++j) cur[j] = nxt[j];
+  }
+#undef NLS_LOAD_BWDI
 }
 
 }  // namespace dev

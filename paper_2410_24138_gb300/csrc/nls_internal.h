@@ -19,6 +19,7 @@ struct SubMeta {
   int32_t ncolor;  // element colours (no two elements of one colour share a node)
   int32_t nrows;   // CSR rows: n (local rows only) or nt (full Neumann rows)
   int64_t tnode_off, elem_off, color_off, rowptr_off, nnz_off, nnz, factor_off, vec_off, epos_off;
+  int64_t dinv_off;  // diagonal-block inverses of the band factors: 2048 * ceil(n / 32) entries
 };
 
 // A batch of subdomain-local problems: overlapping subdomains (rows = local unknowns) or
@@ -38,7 +39,7 @@ struct LocalSet {
   std::vector<uint8_t> owned;       // per local unknown
   std::vector<int32_t> overlap_sorted_elems;  // elements ascending (for inspection)
   std::vector<int64_t> overlap_sorted_off;
-  int64_t total_n = 0, total_nt = 0, total_nnz = 0, total_factor = 0, total_epos = 0;
+  int64_t total_n = 0, total_nt = 0, total_nnz = 0, total_factor = 0, total_epos = 0, total_dinv = 0;
   int max_n = 0, max_nt = 0, max_b = 0, max_ne = 0, max_nrows = 0;
 };
 
@@ -50,6 +51,7 @@ struct DeviceLocalSet {
   uint8_t* owned = nullptr;
   double* csr_val = nullptr;       // FP64 local Jacobian (rows per meta.nrows)
   void* factor = nullptr;          // band factors, float or double per precision
+  void* dinv = nullptr;            // explicit inverses of the diagonal blocks of the factors
   double* w = nullptr;             // local states, concatenated (total_n)
   int32_t *its = nullptr, *status = nullptr;
   int32_t* order = nullptr;        // processing order (longest first)
@@ -136,5 +138,11 @@ int get_coarse_basis(const Context& c, double* P0);
 int kernel_stats(const Context& c, int32_t cap, nls_kernel_stat* out, int32_t* n_out);
 void reset_kernel_stats(Context& c);
 int local_corrections_noalloc(Context& c, const double* x, double* Fx, int32_t* its, int32_t* status, double load);
+// guess.cu
+int guess_attach(Context& c, nls_guess_net* net, int32_t mode);
+int guess_counts(Context& c, int64_t* proposed, int64_t* accepted);
+const double* guess_propose(Context& c, const double* x, double load, int32_t** accepted);
+void guess_after_local(Context& c, const double* x, double load, bool proposed);
+void guess_free(Context& c);
 
 }  // namespace nls

@@ -201,7 +201,7 @@ void build_local_set(Context& c, LocalSet& s, int layers, bool neumann_rows, boo
     if (!e.empty()) throw std::runtime_error(e);
   const int nd = c.ndof, ned = c.nen * c.ndof;
   s.meta.resize(c.n_sub);
-  int64_t tn = 0, el = 0, co = 0, rp = 0, nz = 0, fa = 0, ve = 0, ep = 0;
+  int64_t tn = 0, el = 0, co = 0, rp = 0, nz = 0, fa = 0, ve = 0, ep = 0, di = 0;
   for (int i = 0; i < c.n_sub; ++i) {
     SubBuild& p = parts[i];
     SubMeta& m = s.meta[i];
@@ -222,6 +222,7 @@ void build_local_set(Context& c, LocalSet& s, int layers, bool neumann_rows, boo
     m.factor_off = fa;
     m.vec_off = ve;
     m.epos_off = ep;
+    m.dinv_off = di;
     tn += m.nT;
     el += m.ne;
     co += m.ncolor + 1;
@@ -230,6 +231,7 @@ void build_local_set(Context& c, LocalSet& s, int layers, bool neumann_rows, boo
     fa += (int64_t)m.n * (2 * m.b + 1);
     ve += m.n;
     ep += (int64_t)m.ne * ned * ned;
+    di += 2048 * (int64_t)((m.n + 31) / 32);
     s.max_n = std::max(s.max_n, m.n);
     s.max_nt = std::max(s.max_nt, m.nt);
     s.max_b = std::max(s.max_b, m.b);
@@ -254,6 +256,7 @@ void build_local_set(Context& c, LocalSet& s, int layers, bool neumann_rows, boo
   s.total_nnz = nz;
   s.total_factor = fa;
   s.total_epos = ep;
+  s.total_dinv = di;
 }
 
 namespace {

@@ -28,6 +28,7 @@
 #include <mutex>
 #include <vector>
 
+#include "dev_state.cuh"
 #include "device.cuh"
 #include "nls_internal.h"
 
@@ -35,15 +36,7 @@ namespace nls {
 
 namespace {
 
-struct CudaFailure : std::runtime_error {
-  explicit CudaFailure(const std::string& s) : std::runtime_error(s) {}
-};
 
-#define CK(call)                                                                                  \
-  do {                                                                                            \
-    cudaError_t e_ = (call);                                                                      \
-    if (e_ != cudaSuccess) throw CudaFailure(std::string(#call) + ": " + cudaGetErrorString(e_)); \
-  } while (0)
 
 constexpr int kVecBlocks = 1216;  // 8 per SM on 152 SMs
 constexpr int kVecThreads = 256;
@@ -61,6 +54,7 @@ struct LocalArgs {
   const uint8_t* owned;
   double* csr;
   void* factor;
+  void* dinv;
   double* wbuf;
   int32_t *its, *status;
   const int32_t* order;
@@ -74,6 +68,8 @@ struct LocalArgs {
   double* out;            // F_x: owned entries receive x - w
   const double* guess;    // optional start states (concatenated local vectors)
   int want_tangent;
+  int32_t* accepted;          // per subdomain: 1 where the proposed start was taken
+  unsigned long long* phase;  // optional per-phase clock counters (profiling), see kPhaseNames
   // tangent application
   const double* v;
   const double* add;
@@ -103,7 +99,12 @@ __host__ __device__ inline SmemPlan smem_plan(int max_n, int max_nt, int max_b, 
   p.s = o; o += sizeof(double) * max_n;
   p.red = o; o += sizeof(double) * 40;
   p.yv = o; o += align_up(sizeof(FT) * max_n, 16);
-  p.win = o; o += with_window ? align_up(sizeof(FT) * (size_t)(max_b + 2 + dev::kLuPrefetch) * (2 * max_b + 1), 16) : 0;
+  {
+    const size_t lu = (size_t)(max_b + 2 + dev::kLuPrefetch) * (2 * max_b + 1);
+    const size_t inv = 2 * (size_t)dev::SolveBlock<FT>::BS * (dev::SolveBlock<FT>::BS + 1);
+    p.win = o;
+    o += with_window ? align_up(sizeof(FT) * (lu > inv ? lu : inv), 16) : 0;
+  }
   p.rp = o; o += with_window ? align_up(sizeof(FT) * (max_b + 2 + dev::kLuPrefetch), 16) : 0;
   p.flag = o; o += 16;
   p.total = o;
@@ -184,15 +185,28 @@ __device__ void local_jacobian(const LocalArgs& A, const SubMeta& m, const doubl
         const dev::P1State st = dev::p1_state(geo, A.kcoef[gid], xt[lc[0]], xt[lc[1]], xt[lc[2]]);
         double K[9];
         dev::p1_jacobian<double>(geo, st, K);
+        // the nine (row, col) targets of one element are distinct: issue every load before any
+        // store so that one memory latency is paid per element, not one per entry
+        double oc[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) oc[q] = (ep[q] >= 0) ? csr[ep[q]] : 0.0;
 #pragma unroll
         for (int q = 0; q < 9; ++q)
-          if (ep[q] >= 0) csr[ep[q]] += K[q];
+          if (ep[q] >= 0) csr[ep[q]] = oc[q] + K[q];
         if (band) {
+          FT ob[9];
+          int64_t bp[9];
 #pragma unroll
           for (int a = 0; a < 3; ++a)
 #pragma unroll
-            for (int b = 0; b < 3; ++b)
-              if (lc[a] < n && lc[b] < n) band[(int64_t)lc[a] * W + (lc[b] - lc[a] + m.b)] += (FT)K[a * 3 + b];
+            for (int b = 0; b < 3; ++b) {
+              const bool in = lc[a] < n && lc[b] < n;
+              bp[a * 3 + b] = in ? (int64_t)lc[a] * W + (lc[b] - lc[a] + m.b) : -1;
+              ob[a * 3 + b] = in ? band[bp[a * 3 + b]] : (FT)0;
+            }
+#pragma unroll
+          for (int q = 0; q < 9; ++q)
+            if (bp[q] >= 0) band[bp[q]] = ob[q] + (FT)K[q];
         }
       } else {
         const double* geo = A.geom + (int64_t)gid * 40;
@@ -204,9 +218,14 @@ __device__ void local_jacobian(const LocalArgs& A, const SubMeta& m, const doubl
         }
         JT K[64];
         dev::nh_jacobian<JT>(geo, ue, A.mu, A.lam, K);
+        {
+          double oc[64];
 #pragma unroll
-        for (int q = 0; q < 64; ++q)
-          if (ep[q] >= 0) csr[ep[q]] += (double)K[q];
+          for (int q = 0; q < 64; ++q) oc[q] = (ep[q] >= 0) ? csr[ep[q]] : 0.0;
+#pragma unroll
+          for (int q = 0; q < 64; ++q)
+            if (ep[q] >= 0) csr[ep[q]] = oc[q] + (double)K[q];
+        }
         if (band) {
 #pragma unroll
           for (int a = 0; a < 4; ++a)
@@ -232,12 +251,12 @@ __device__ void local_jacobian(const LocalArgs& A, const SubMeta& m, const doubl
 // (columns < n) when the factors are FP32.  `res` is an n-vector of scratch.
 template <typename FT>
 __device__ int local_solve(const LocalArgs& A, const SubMeta& m, const int32_t* rowptr, const int32_t* colidx,
-                           const double* csr, const FT* F, const double* rhs, double rhs_norm, double* s, double* res,
-                           FT* yv, double* red) {
+                           const double* csr, const FT* F, const FT* Dv, const double* rhs, double rhs_norm, double* s,
+                           double* res, FT* yv, double* red) {
   const int n = m.n;
   for (int a = threadIdx.x; a < n; a += blockDim.x) yv[a] = (FT)rhs[a];
   __syncthreads();
-  dev::band_solve<FT>(n, m.b, F, yv);
+  dev::band_solve_inv<FT>(n, m.b, F, Dv, yv);
   for (int a = threadIdx.x; a < n; a += blockDim.x) s[a] = (double)yv[a];
   __syncthreads();
   int sweeps = 0;
@@ -257,7 +276,7 @@ __device__ int local_solve(const LocalArgs& A, const SubMeta& m, const int32_t* 
       if (!(rn > A.ir_rtol * rhs_norm)) break;
       for (int a = threadIdx.x; a < n; a += blockDim.x) yv[a] = (FT)res[a];
       __syncthreads();
-      dev::band_solve<FT>(n, m.b, F, yv);
+      dev::band_solve_inv<FT>(n, m.b, F, Dv, yv);
       for (int a = threadIdx.x; a < n; a += blockDim.x) s[a] += (double)yv[a];
       __syncthreads();
       ++sweeps;
@@ -285,6 +304,18 @@ __global__ void __launch_bounds__(512) k_local_newton(LocalArgs A) {
   __shared__ int s_item;
   using JT = typename std::conditional<LAW == NLS_LAW_DIFFUSION, double, FT>::type;
   const int tid = threadIdx.x, nd = A.ndof;
+  constexpr int BSI = dev::SolveBlock<FT>::BS;
+  const int inv_warps = min((int)(blockDim.x >> 5),
+                            (int)((P.rp - P.win) / (sizeof(FT) * BSI * (BSI + 1))));
+  long long tp = clock64();
+  // thread 0 charges the cycles since the last mark to phase `id` (profiling only)
+  auto mark = [&](int id) {
+    if (A.phase && tid == 0) {
+      const long long t = clock64();
+      atomicAdd(A.phase + id, (unsigned long long)(t - tp));
+      tp = t;
+    }
+  };
   for (;;) {
     if (tid == 0) s_item = atomicAdd(A.queue, 1);
     __syncthreads();
@@ -298,32 +329,61 @@ __global__ void __launch_bounds__(512) k_local_newton(LocalArgs A) {
     const int32_t* colidx = A.colidx + m.nnz_off;
     double* csr = A.csr + m.nnz_off;
     FT* F = (FT*)A.factor + m.factor_off;
+    FT* Dv = (FT*)A.dinv + m.dinv_off;
     double* wb = A.wbuf + m.vec_off;
     for (int t = tid; t < m.nt; t += blockDim.x)
       xt[t] = A.x[(int64_t)A.tnode_gid[m.tnode_off + t / nd] * nd + t % nd];
-    __syncthreads();
-    if (A.guess)
-      for (int a = tid; a < n; a += blockDim.x) xt[a] = A.guess[m.vec_off + a];
     __syncthreads();
     bool ok = local_residual<LAW>(A, m, xt, r);
     double loc = 0.0;
     for (int a = tid; a < n; a += blockDim.x) loc += r[a] * r[a];
     double rn = sqrt(dev::block_sum(loc, red));
     if (!ok) rn = INFINITY;
+    // the stopping test is relative to the residual of the method's own start R_i x, with or
+    // without a proposed start, so the proposal cannot change the accuracy of T_i
     const double tol = fmax(A.atol, A.rtol * rn);
+    if (A.guess) {
+      // acceptance test: take the proposed start only if its local residual is smaller
+      for (int a = tid; a < n; a += blockDim.x) {
+        wb[a] = xt[a];
+        xt[a] = A.guess[m.vec_off + a];
+      }
+      __syncthreads();
+      const bool okg = local_residual<LAW>(A, m, xt, rt);
+      double lg = 0.0;
+      for (int a = tid; a < n; a += blockDim.x) lg += rt[a] * rt[a];
+      double rng = sqrt(dev::block_sum(lg, red));
+      if (!okg) rng = INFINITY;
+      const bool take = isfinite(rng) && rng < rn;
+      if (take) {
+        double* tmp = r;
+        r = rt;
+        rt = tmp;
+        rn = rng;
+      } else {
+        for (int a = tid; a < n; a += blockDim.x) xt[a] = wb[a];
+        __syncthreads();
+      }
+      if (tid == 0 && A.accepted) A.accepted[sub] = take ? 1 : 0;
+    }
     int its = 0, status = ST_OK;
     if (!isfinite(rn)) status = ST_NONFINITE;
+    mark(0);
     while (status == ST_OK && rn > tol) {
       if (its >= A.maxit) {
         status = ST_MAXIT;
         break;
       }
       local_jacobian<LAW, JT, FT>(A, m, xt, csr, F);
+      mark(1);
       if (dev::band_lu_inplace<FT>(n, m.b, F, win, rp, flag)) {
         status = ST_PIVOT;
         break;
       }
-      local_solve<FT>(A, m, rowptr, colidx, csr, F, r, rn, s, rt, yv, red);
+      dev::band_diag_inverses<FT>(n, m.b, F, Dv, win, inv_warps);
+      mark(2);
+      local_solve<FT>(A, m, rowptr, colidx, csr, F, Dv, r, rn, s, rt, yv, red);
+      mark(3);
       for (int a = tid; a < n; a += blockDim.x) wb[a] = xt[a];
       __syncthreads();
       double alpha = 1.0, rtn = INFINITY;
@@ -343,6 +403,7 @@ __global__ void __launch_bounds__(512) k_local_newton(LocalArgs A) {
         alpha *= 0.5;
       }
       ++its;
+      mark(4);
       if (!accepted) {
         for (int a = tid; a < n; a += blockDim.x) xt[a] = wb[a];
         __syncthreads();
@@ -356,7 +417,10 @@ __global__ void __launch_bounds__(512) k_local_newton(LocalArgs A) {
     }
     if (A.want_tangent && status != ST_NONFINITE && status != ST_PIVOT) {
       local_jacobian<LAW, JT, FT>(A, m, xt, csr, F);
+      mark(5);
       if (dev::band_lu_inplace<FT>(n, m.b, F, win, rp, flag)) status = ST_PIVOT;
+      else dev::band_diag_inverses<FT>(n, m.b, F, Dv, win, inv_warps);
+      mark(6);
     }
     for (int a = tid; a < n; a += blockDim.x) {
       wb[a] = xt[a];
@@ -370,6 +434,7 @@ __global__ void __launch_bounds__(512) k_local_newton(LocalArgs A) {
       A.status[sub] = status;
     }
     __syncthreads();
+    mark(7);
     // restore the ping-pong buffers for the next subdomain
     r = (double*)(smem + P.r);
     rt = (double*)(smem + P.rt);
@@ -396,6 +461,7 @@ __global__ void __launch_bounds__(512) k_local_apply(LocalArgs A) {
   const int32_t* colidx = A.colidx + m.nnz_off;
   const double* csr = A.csr + m.nnz_off;
   const FT* F = (const FT*)A.factor + m.factor_off;
+  const FT* Dv = (const FT*)A.dinv + m.dinv_off;
   for (int t = tid; t < m.nt; t += blockDim.x) yt[t] = A.v[(int64_t)A.tnode_gid[m.tnode_off + t / nd] * nd + t % nd];
   __syncthreads();
   double loc = 0.0;
@@ -406,7 +472,7 @@ __global__ void __launch_bounds__(512) k_local_apply(LocalArgs A) {
     loc += acc * acc;
   }
   const double qn = sqrt(dev::block_sum(loc, red));
-  local_solve<FT>(A, m, rowptr, colidx, csr, F, q, qn, z, res, yv, red);
+  local_solve<FT>(A, m, rowptr, colidx, csr, F, Dv, q, qn, z, res, yv, red);
   for (int a = tid; a < n; a += blockDim.x)
     if (A.owned[m.vec_off + a]) {
       const int64_t g = (int64_t)A.tnode_gid[m.tnode_off + a / nd] * nd + a % nd;
@@ -522,22 +588,103 @@ __global__ void k_gather_values32(int64_t n, const int32_t* src, const double* f
 
 // coarse band factorization (one CTA)
 template <typename FT>
-__global__ void __launch_bounds__(1024) k_coarse_factor(int N0, int b0, const double* A0, FT* F, int* status) {
+__global__ void __launch_bounds__(1024) k_coarse_factor(int N0, int b0, const double* A0, FT* F, FT* Dinv, int* status) {
   extern __shared__ __align__(16) unsigned char smem[];
+  constexpr int BS = dev::SolveBlock<FT>::BS;
+  const size_t R = (size_t)b0 + 2 + dev::kLuPrefetch;
   FT* win = (FT*)smem;
-  FT* rp = win + (size_t)(b0 + 2 + dev::kLuPrefetch) * (2 * b0 + 1);
-  int* flag = (int*)(rp + b0 + 2 + dev::kLuPrefetch);
+  FT* rp = win + R * (2 * b0 + 1);
+  FT* tmp = rp + R;
+  int* flag = (int*)(tmp + 4 * BS * (BS + 1));
   const int64_t total = (int64_t)N0 * (2 * b0 + 1);
   for (int64_t k = threadIdx.x; k < total; k += blockDim.x) F[k] = (FT)A0[k];
   __syncthreads();
   const int bad = dev::band_lu_inplace<FT>(N0, b0, F, win, rp, flag);
+  if (!bad) dev::band_diag_inverses<FT>(N0, b0, F, Dinv, tmp, 4);
   if (threadIdx.x == 0) *status = bad ? ST_PIVOT : ST_OK;
+}
+
+// Columns of A_0^-1 (one CTA per column, shared-memory vectors): the band factors solve
+// A_0 z = e_col, FP64 refinement against the band A_0 brings every column to FP64 accuracy.
+// Stored transposed (AinvT[col][row]) so that the GEMV below reads it coalesced.
+template <typename FT>
+__global__ void __launch_bounds__(256) k_coarse_inverse(int N0, int b0, const double* A0, const FT* F, const FT* Dinv,
+                                                         double* AinvT, double ir_rtol, int ir_max) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  double* z = (double*)smem;
+  double* res = z + N0;
+  double* red = res + N0;
+  FT* y = (FT*)(red + 40);
+  const int W = 2 * b0 + 1;
+  for (int col = blockIdx.x; col < N0; col += gridDim.x) {
+    for (int a = threadIdx.x; a < N0; a += blockDim.x) y[a] = (a == col) ? (FT)1 : (FT)0;
+    __syncthreads();
+    dev::band_solve_inv<FT>(N0, b0, F, Dinv, y);
+    for (int a = threadIdx.x; a < N0; a += blockDim.x) z[a] = (double)y[a];
+    __syncthreads();
+    if (sizeof(FT) == 4) {
+      for (int sw = 0; sw < ir_max; ++sw) {
+        double l2 = 0.0;
+        for (int a = threadIdx.x; a < N0; a += blockDim.x) {
+          double acc = (a == col) ? 1.0 : 0.0;
+          for (int d = 0; d < W; ++d) {
+            const int cc = a - b0 + d;
+            if (cc >= 0 && cc < N0) acc -= A0[(int64_t)a * W + d] * z[cc];
+          }
+          res[a] = acc;
+          l2 += acc * acc;
+        }
+        const double rn = sqrt(dev::block_sum(l2, red));
+        if (!(rn > ir_rtol)) break;
+        for (int a = threadIdx.x; a < N0; a += blockDim.x) y[a] = (FT)res[a];
+        __syncthreads();
+        dev::band_solve_inv<FT>(N0, b0, F, Dinv, y);
+        for (int a = threadIdx.x; a < N0; a += blockDim.x) z[a] += (double)y[a];
+        __syncthreads();
+      }
+    }
+    for (int a = threadIdx.x; a < N0; a += blockDim.x) AinvT[(int64_t)col * N0 + a] = z[a];
+    __syncthreads();
+  }
+}
+
+// z = A_0^-1 g with the explicit inverse (stored transposed).  Grid (row tiles of 32, column
+// chunks): lane = row, the 8 warps of a CTA stride over the chunk's columns (coalesced rows of
+// AinvT), warp partials are summed in shared memory in warp order, chunk partials go to
+// `part` and k_gemv_finish adds them in chunk order (no atomics: the result is reproducible).
+constexpr int kGemvChunks = 16;
+__global__ void __launch_bounds__(256) k_dense_gemv_t(int N0, const double* AinvT, const double* g, double* part) {
+  __shared__ double acc_s[8][33];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int row = blockIdx.x * 32 + lane;
+  const int per = (N0 + gridDim.y - 1) / gridDim.y;
+  const int c0 = blockIdx.y * per, c1 = min(N0, c0 + per);
+  double acc = 0.0;
+  if (row < N0)
+    for (int col = c0 + wid; col < c1; col += 8) acc += AinvT[(int64_t)col * N0 + row] * g[col];
+  acc_s[wid][lane] = acc;
+  __syncthreads();
+  if (wid == 0 && row < N0) {
+    double t = 0.0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) t += acc_s[w][lane];
+    part[(int64_t)blockIdx.y * N0 + row] = t;
+  }
+}
+
+__global__ void k_gemv_finish(int N0, int chunks, const double* part, double* z) {
+  for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < N0; row += gridDim.x * blockDim.x) {
+    double t = 0.0;
+    for (int c = 0; c < chunks; ++c) t += part[(int64_t)c * N0 + row];
+    z[row] = t;
+  }
 }
 
 // coarse solve z = A0^-1 g (global-memory vectors), FP64 refinement against the band A0
 template <typename FT>
-__global__ void __launch_bounds__(256) k_coarse_solve(int N0, int b0, const double* A0, const FT* F, const double* g,
-                                                       double* z, double* res, FT* y, double ir_rtol, int ir_max) {
+__global__ void __launch_bounds__(256) k_coarse_solve(int N0, int b0, const double* A0, const FT* F, const FT* Dinv,
+                                                       const double* g, double* z, double* res, FT* y, double ir_rtol,
+                                                       int ir_max) {
   __shared__ double red[40];
   const int W = 2 * b0 + 1;
   double loc = 0.0;
@@ -546,7 +693,7 @@ __global__ void __launch_bounds__(256) k_coarse_solve(int N0, int b0, const doub
     loc += g[a] * g[a];
   }
   const double gn = sqrt(dev::block_sum(loc, red));
-  dev::band_solve<FT>(N0, b0, F, y);
+  dev::band_solve_inv<FT>(N0, b0, F, Dinv, y);
   for (int a = threadIdx.x; a < N0; a += blockDim.x) z[a] = (double)y[a];
   __syncthreads();
   if (sizeof(FT) == 4) {
@@ -565,7 +712,7 @@ __global__ void __launch_bounds__(256) k_coarse_solve(int N0, int b0, const doub
       if (!(rn > ir_rtol * gn)) break;
       for (int a = threadIdx.x; a < N0; a += blockDim.x) y[a] = (FT)res[a];
       __syncthreads();
-      dev::band_solve<FT>(N0, b0, F, y);
+      dev::band_solve_inv<FT>(N0, b0, F, Dinv, y);
       for (int a = threadIdx.x; a < N0; a += blockDim.x) z[a] += (double)y[a];
       __syncthreads();
     }
@@ -742,110 +889,6 @@ __global__ void k_sqrt_inplace(double* x) { *x = sqrt(*x); }
 
 }  // namespace
 
-// ------------------------------------------------------------------------------------------
-// device state
-// ------------------------------------------------------------------------------------------
-struct Dev {
-  cudaStream_t s = nullptr;
-  std::vector<void*> allocs;
-  int64_t bytes = 0;
-  int64_t launches = 0;
-  int nsm = 152;
-  size_t smem_optin = 0;
-  template <typename T>
-  T* alloc(size_t n) {
-    void* p = nullptr;
-    if (n == 0) n = 1;
-    CK(cudaMalloc(&p, n * sizeof(T)));
-    allocs.push_back(p);
-    bytes += (int64_t)(n * sizeof(T));
-    return (T*)p;
-  }
-  template <typename T>
-  T* upload(const std::vector<T>& v) {
-    T* p = alloc<T>(v.size());
-    if (!v.empty()) CK(cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s));
-    return p;
-  }
-  void release(void* p) {
-    for (auto& q : allocs)
-      if (q == p) {
-        cudaFree(q);
-        q = nullptr;
-      }
-  }
-  // mesh
-  int32_t *conn = nullptr, *g_elem = nullptr, *g_rowptr = nullptr, *g_col = nullptr, *g_epos = nullptr;
-  double *geom = nullptr, *kcoef = nullptr, *fext = nullptr, *ubc = nullptr, *g_val = nullptr;
-  uint8_t* free_dof = nullptr;
-  DeviceLocalSet ov, nov;
-  // coarse
-  int32_t *p0_rowptr = nullptr, *p0_col = nullptr, *p0t_rowptr = nullptr, *p0t_col = nullptr, *p0t_src = nullptr;
-  int64_t* p0_src = nullptr;
-  double *p0_val = nullptr, *p0t_val = nullptr, *phi = nullptr, *Y = nullptr, *blk = nullptr, *A0 = nullptr;
-  int64_t *phi_off = nullptr, *blk_off = nullptr, *a0_src = nullptr;
-  int32_t *cj_ptr = nullptr, *a0_ptr = nullptr;
-  void* A0f = nullptr;
-  int32_t* cstatus = nullptr;
-  // vectors
-  double *u = nullptr, *x = nullptr, *u0 = nullptr, *Fx = nullptr, *F = nullptr, *t1 = nullptr, *t2 = nullptr,
-         *w0 = nullptr, *gx = nullptr;
-  double *c = nullptr, *ct = nullptr, *dc = nullptr, *g = nullptr, *gt = nullptr, *cres = nullptr;
-  void* cy = nullptr;
-  double *V = nullptr, *partial = nullptr, *scal = nullptr, *coef = nullptr;
-  int* bad = nullptr;
-  double* h_scal = nullptr;  // pinned
-  int m = 0;                 // GMRES restart length allocated
-  bool tangent_ready = false;
-  double last_load = 1.0;
-  // per-launch CUDA-event timing (nls_options.profile_kernels)
-  bool prof = false;
-  struct EvRec {
-    cudaEvent_t a, b;
-    const char* name;
-  };
-  std::vector<EvRec> evs;
-  size_t ev_used = 0;
-  struct Stat {
-    std::string name;
-    int64_t launches;
-    double ms;
-  };
-  std::vector<Stat> stats;
-  void prof_begin(const char* name) {
-    if (ev_used == evs.size()) {
-      EvRec r;
-      CK(cudaEventCreate(&r.a));
-      CK(cudaEventCreate(&r.b));
-      evs.push_back(r);
-    }
-    evs[ev_used].name = name;
-    CK(cudaEventRecord(evs[ev_used].a, s));
-  }
-  void prof_end() {
-    CK(cudaEventRecord(evs[ev_used].b, s));
-    ++ev_used;
-    if (ev_used >= 65536) prof_flush();
-  }
-  void prof_flush() {
-    if (!ev_used) return;
-    CK(cudaStreamSynchronize(s));
-    for (size_t i = 0; i < ev_used; ++i) {
-      float ms = 0.f;
-      CK(cudaEventElapsedTime(&ms, evs[i].a, evs[i].b));
-      Stat* st = nullptr;
-      for (auto& x : stats)
-        if (x.name == evs[i].name) st = &x;
-      if (!st) {
-        stats.push_back(Stat{evs[i].name, 0, 0.0});
-        st = &stats.back();
-      }
-      st->launches += 1;
-      st->ms += ms;
-    }
-    ev_used = 0;
-  }
-};
 
 namespace {
 
@@ -854,19 +897,12 @@ inline int grid_for(int64_t n, int threads = 256) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(b, kVecBlocks));
 }
 
-#define LAUNCH(D, kernel, grid, block, smem, ...)                          \
-  do {                                                                     \
-    const bool prof_ = (D).prof;                                           \
-    if (prof_) (D).prof_begin(#kernel);                                    \
-    kernel<<<(grid), (block), (smem), (D).s>>>(__VA_ARGS__);               \
-    if (prof_) (D).prof_end();                                             \
-    (D).launches += 1;                                                     \
-    CK(cudaGetLastError());                                                \
-  } while (0)
 
+// The triangular solves need warp 0 plus one thread per coupled row (32 + b threads).
 int local_threads(const Context& c) {
-  if (c.opt.threads_per_block) return c.opt.threads_per_block;
-  return c.ndof == 1 ? 256 : 512;
+  const int need = ((32 + c.ov.max_b + 31) / 32) * 32;
+  const int pick = c.opt.threads_per_block ? c.opt.threads_per_block : (c.ndof == 1 ? 128 : 256);
+  return std::max(pick, need);
 }
 
 bool fp32_local(const Context& c) { return c.opt.local_precision == NLS_PREC_FP32_IR; }
@@ -887,6 +923,7 @@ LocalArgs make_args(const Context& c, const LocalSet& hs, const DeviceLocalSet& 
   A.owned = ds.owned;
   A.csr = ds.csr_val;
   A.factor = ds.factor;
+  A.dinv = ds.dinv;
   A.wbuf = ds.w;
   A.its = ds.its;
   A.status = ds.status;
@@ -980,14 +1017,17 @@ size_t local_newton_smem(const LocalSet& s) {
   return smem_plan<FT>(s.max_n, s.max_nt, s.max_b, true).total;
 }
 
-void launch_local_newton(Context& c, const double* x, double* out, double load, const double* guess, bool want_tangent) {
+void launch_local_newton(Context& c, const double* x, double* out, double load, const double* guess, bool want_tangent,
+                         int32_t* accepted = nullptr) {
   Dev& D = *c.dev;
   LocalArgs A = make_args(c, c.ov, D.ov);
   A.x = x;
   A.out = out;
   A.load = load;
   A.guess = guess;
+  A.accepted = accepted;
   A.want_tangent = want_tangent ? 1 : 0;
+  A.phase = D.prof ? D.phase : nullptr;
   CK(cudaMemsetAsync(D.ov.queue, 0, sizeof(int32_t), D.s));
   const int T = local_threads(c);
   const bool f32 = fp32_local(c);
@@ -1009,7 +1049,9 @@ void launch_local_apply(Context& c, const double* v, const double* add, double* 
   A.v = v;
   A.add = add;
   A.out = out;
-  const int T = local_threads(c);
+  // the solves need warp 0 plus one thread per coupled row (32 + b); small CTAs let more
+  // subdomains be in flight on every SM, which is what hides the latency of the solves
+  const int T = std::max(64, (32 + c.ov.max_b + 31) / 32 * 32);
   if (fp32_local(c)) {
     const size_t sm = smem_plan<float>(c.ov.max_n, c.ov.max_nt, c.ov.max_b, false).total;
     LAUNCH(D, k_local_apply<float>, c.ov.count, T, sm, A);
@@ -1034,8 +1076,9 @@ LocalArgs coarse_args(Context& c) {
 
 size_t coarse_factor_smem(const Context& c, bool f32) {
   const size_t fs = f32 ? sizeof(float) : sizeof(double);
+  const size_t BS = f32 ? dev::SolveBlock<float>::BS : dev::SolveBlock<double>::BS;
   const size_t R = (size_t)c.cs.b0 + 2 + dev::kLuPrefetch;
-  return fs * (R * (2 * c.cs.b0 + 1) + R) + 16;
+  return fs * (R * (2 * c.cs.b0 + 1) + R + 4 * BS * (BS + 1)) + 16;
 }
 
 // A_0(x) = P_0^T DF(x) P_0 -> band -> factor.  Returns false on a bad pivot.
@@ -1052,8 +1095,11 @@ bool coarse_matrix(Context& c, const double* x) {
   LAUNCH(D, k_a0_gather, grid_for(ne), 256, 0, ne, D.a0_ptr, D.a0_src, D.blk, D.A0);
   const bool f32 = fp32_coarse(c);
   const size_t fsm = coarse_factor_smem(c, f32);
-  if (f32) LAUNCH(D, k_coarse_factor<float>, 1, 1024, fsm, c.cs.N0, c.cs.b0, D.A0, (float*)D.A0f, D.cstatus);
-  else LAUNCH(D, k_coarse_factor<double>, 1, 1024, fsm, c.cs.N0, c.cs.b0, D.A0, (double*)D.A0f, D.cstatus);
+  if (f32)
+    LAUNCH(D, k_coarse_factor<float>, 1, 1024, fsm, c.cs.N0, c.cs.b0, D.A0, (float*)D.A0f, (float*)D.A0dinv, D.cstatus);
+  else
+    LAUNCH(D, k_coarse_factor<double>, 1, 1024, fsm, c.cs.N0, c.cs.b0, D.A0, (double*)D.A0f, (double*)D.A0dinv,
+           D.cstatus);
   int32_t st = 0;
   CK(cudaMemcpyAsync(&st, D.cstatus, sizeof(int32_t), cudaMemcpyDeviceToHost, D.s));
   sync(D);
@@ -1062,12 +1108,18 @@ bool coarse_matrix(Context& c, const double* x) {
 
 void coarse_solve(Context& c, const double* g, double* z) {
   Dev& D = *c.dev;
+  if (D.ainv_valid) {
+    const int N0 = c.cs.N0;
+    LAUNCH(D, k_dense_gemv_t, dim3((N0 + 31) / 32, kGemvChunks), 256, 0, N0, D.ainv, g, D.gpart);
+    LAUNCH(D, k_gemv_finish, grid_for(N0), 256, 0, N0, kGemvChunks, D.gpart, z);
+    return;
+  }
   if (fp32_coarse(c))
-    LAUNCH(D, k_coarse_solve<float>, 1, 256, 0, c.cs.N0, c.cs.b0, D.A0, (const float*)D.A0f, g, z, D.cres,
-           (float*)D.cy, c.opt.ir_rtol, c.opt.ir_max_sweeps);
+    LAUNCH(D, k_coarse_solve<float>, 1, 256, 0, c.cs.N0, c.cs.b0, D.A0, (const float*)D.A0f,
+           (const float*)D.A0dinv, g, z, D.cres, (float*)D.cy, c.opt.ir_rtol, c.opt.ir_max_sweeps);
   else
-    LAUNCH(D, k_coarse_solve<double>, 1, 256, 0, c.cs.N0, c.cs.b0, D.A0, (const double*)D.A0f, g, z, D.cres,
-           (double*)D.cy, c.opt.ir_rtol, c.opt.ir_max_sweeps);
+    LAUNCH(D, k_coarse_solve<double>, 1, 256, 0, c.cs.N0, c.cs.b0, D.A0, (const double*)D.A0f,
+           (const double*)D.A0dinv, g, z, D.cres, (double*)D.cy, c.opt.ir_rtol, c.opt.ir_max_sweeps);
 }
 
 // x = u - P0 c
@@ -1146,7 +1198,7 @@ CoarseResult coarse_newton(Context& c, const double* u, double load) {
 // ------------------------------------------------------------------------------------------
 namespace {
 
-void upload_set(Dev& D, const LocalSet& h, DeviceLocalSet& d, bool fp32_factor) {
+void upload_set(Dev& D, const LocalSet& h, DeviceLocalSet& d, bool fp32_factor, bool with_dinv = true) {
   d.count = h.count;
   d.meta = D.upload(h.meta);
   d.tnode_gid = D.upload(h.tnode_gid);
@@ -1158,8 +1210,13 @@ void upload_set(Dev& D, const LocalSet& h, DeviceLocalSet& d, bool fp32_factor) 
   d.epos = D.upload(h.epos);
   d.owned = D.upload(h.owned);
   d.csr_val = D.alloc<double>(h.total_nnz);
-  if (fp32_factor) d.factor = D.alloc<float>(h.total_factor);
-  else d.factor = D.alloc<double>(h.total_factor);
+  if (fp32_factor) {
+    d.factor = D.alloc<float>(h.total_factor);
+    if (with_dinv) d.dinv = D.alloc<float>(h.total_dinv);
+  } else {
+    d.factor = D.alloc<double>(h.total_factor);
+    if (with_dinv) d.dinv = D.alloc<double>(h.total_dinv);
+  }
   d.w = D.alloc<double>(h.total_n);
   d.its = D.alloc<int32_t>(h.count);
   d.status = D.alloc<int32_t>(h.count);
@@ -1221,12 +1278,18 @@ int device_setup(Context& c) {
     D.scal = D.alloc<double>(kMaxGmresVecs + 8);
     D.coef = D.alloc<double>(kMaxGmresVecs + 8);
     D.bad = D.alloc<int>(4);
+    D.phase = D.alloc<unsigned long long>(8);
+    CK(cudaMemsetAsync(D.phase, 0, sizeof(unsigned long long) * 8, D.s));
+    CK(cudaDeviceGetAttribute(&D.clock_khz, cudaDevAttrClockRate, c.device));
     CK(cudaMallocHost(&D.h_scal, sizeof(double) * (kMaxGmresVecs + 8)));
     // kernel attributes for large dynamic shared memory
     const size_t lim = D.smem_optin;
     auto need = [&](size_t b, const char* what) {
       if (b > lim) throw std::runtime_error(std::string(what) + " needs more shared memory than the device offers");
     };
+    if (c.ov.max_b > 128 || (c.coarse_kind == NLS_COARSE_RGDSW && c.cs.b0 > 128))
+      throw std::runtime_error("a band matrix has a half bandwidth above 128 (local " + std::to_string(c.ov.max_b) +
+                               ", coarse " + std::to_string(c.cs.b0) + "); the band factorisation supports 128");
     need(local_newton_smem<float>(c.ov), "local Newton (FP32 factors)");
     if (!fp32_local(c)) need(local_newton_smem<double>(c.ov), "local Newton (FP64 factors)");
     set_smem(k_local_newton<NLS_LAW_DIFFUSION, float>, lim);
@@ -1246,7 +1309,7 @@ int device_setup(Context& c) {
       Coarse& cs = c.cs;
       if (cs.N0 == 0) throw std::runtime_error("the partition has no coarse nodes (one subdomain?)");
       need(coarse_factor_smem(c, fp32_coarse(c)), "coarse band factorization");
-      upload_set(D, c.nov, D.nov, false);
+      upload_set(D, c.nov, D.nov, false, false);
       D.phi = D.upload(cs.phi_host);
       D.phi_off = D.upload(cs.phi_off);
       D.cj_ptr = D.upload(cs.cj_ptr);
@@ -1256,14 +1319,23 @@ int device_setup(Context& c) {
       D.a0_ptr = D.upload(cs.a0_ptr);
       D.a0_src = D.upload(cs.a0_src);
       D.A0 = D.alloc<double>((size_t)cs.N0 * (2 * cs.b0 + 1));
+      const size_t ndinv = 2048 * (size_t)((cs.N0 + 31) / 32);
       if (fp32_coarse(c)) {
         D.A0f = D.alloc<float>((size_t)cs.N0 * (2 * cs.b0 + 1));
+        D.A0dinv = D.alloc<float>(ndinv);
         D.cy = D.alloc<float>(cs.N0);
       } else {
         D.A0f = D.alloc<double>((size_t)cs.N0 * (2 * cs.b0 + 1));
+        D.A0dinv = D.alloc<double>(ndinv);
         D.cy = D.alloc<double>(cs.N0);
       }
       D.cstatus = D.alloc<int32_t>(1);
+      if (cs.N0 <= 8192 && (3 * sizeof(double)) * (size_t)cs.N0 + 40 * sizeof(double) <= lim) {
+        D.ainv = D.alloc<double>((size_t)cs.N0 * cs.N0);
+        D.gpart = D.alloc<double>((size_t)cs.N0 * kGemvChunks);
+        set_smem(k_coarse_inverse<float>, lim);
+        set_smem(k_coarse_inverse<double>, lim);
+      }
       D.p0_rowptr = D.upload(cs.p0_rowptr);
       D.p0_col = D.upload(cs.p0_col);
       D.p0_src = D.upload(cs.p0_src);
@@ -1318,6 +1390,7 @@ void device_free(Context& c) {
   Dev& D = *c.dev;
   cudaSetDevice(c.device);
   if (D.s) cudaStreamSynchronize(D.s);
+  guess_free(c);
   for (void* p : D.allocs)
     if (p) cudaFree(p);
   if (D.h_scal) cudaFreeHost(D.h_scal);
@@ -1350,6 +1423,7 @@ FxInfo evaluate_Fx(Context& c, const double* u, double load, double* t_inner, do
   Dev& D = *c.dev;
   FxInfo info;
   const int cp = c.opt.coupling;
+  D.ainv_valid = false;
   CK(cudaMemsetAsync(D.Fx, 0, sizeof(double) * c.N, D.s));
   auto t0 = std::chrono::steady_clock::now();
   const double* point = u;
@@ -1361,7 +1435,10 @@ FxInfo evaluate_Fx(Context& c, const double* u, double load, double* t_inner, do
   }
   sync(D);
   auto t1 = std::chrono::steady_clock::now();
-  launch_local_newton(c, point, D.Fx, load, nullptr, true);
+  int32_t* accepted = nullptr;
+  const double* proposal = guess_propose(c, point, load, &accepted);
+  launch_local_newton(c, point, D.Fx, load, proposal, true, accepted);
+  guess_after_local(c, point, load, proposal != nullptr);
   std::vector<int32_t> its(c.ov.count), st(c.ov.count);
   CK(cudaMemcpyAsync(its.data(), D.ov.its, sizeof(int32_t) * its.size(), cudaMemcpyDeviceToHost, D.s));
   CK(cudaMemcpyAsync(st.data(), D.ov.status, sizeof(int32_t) * st.size(), cudaMemcpyDeviceToHost, D.s));
@@ -1380,6 +1457,20 @@ FxInfo evaluate_Fx(Context& c, const double* u, double load, double* t_inner, do
     LAUNCH(D, k_p0_apply, grid_for(c.N), 256, 0, c.N, D.p0_rowptr, D.p0_col, D.p0_val, D.c, 1.0, D.Fx, 1.0, D.Fx);
     global_jacobian(c, D.u0);
     if (!coarse_matrix(c, D.u0)) info.pivot_failure = true;
+    // the tangent's coarse solves (one per GMRES iteration) reuse A_0(u_0): form its inverse
+    else if (D.ainv) {
+      const int N0 = c.cs.N0;
+      const size_t sm = (2 * sizeof(double) + (fp32_coarse(c) ? sizeof(float) : sizeof(double))) * N0 + 40 * sizeof(double);
+      const int T = std::max(64, (32 + c.cs.b0 + 31) / 32 * 32);
+      const int grid = std::min(N0, D.nsm * 8);
+      if (fp32_coarse(c))
+        LAUNCH(D, k_coarse_inverse<float>, grid, T, sm, N0, c.cs.b0, D.A0, (const float*)D.A0f,
+               (const float*)D.A0dinv, D.ainv, c.opt.ir_rtol, c.opt.ir_max_sweeps);
+      else
+        LAUNCH(D, k_coarse_inverse<double>, grid, T, sm, N0, c.cs.b0, D.A0, (const double*)D.A0f,
+               (const double*)D.A0dinv, D.ainv, c.opt.ir_rtol, c.opt.ir_max_sweeps);
+      D.ainv_valid = true;
+    }
   }
   sync(D);
   auto t3 = std::chrono::steady_clock::now();
@@ -1680,6 +1771,25 @@ int kernel_stats(const Context& c, int32_t cap, nls_kernel_stat* out, int32_t* n
     }
     ++n;
   }
+  // k_local_newton phases: CTA-milliseconds (sum over CTAs of thread 0's clock64 deltas)
+  static const char* kPhaseNames[8] = {"phase:gather+residual", "phase:jacobian", "phase:band_lu",
+                                       "phase:solve+refine",   "phase:line_search", "phase:tangent_jacobian",
+                                       "phase:tangent_band_lu", "phase:output"};
+  unsigned long long ph[8] = {0};
+  try {
+    CK(cudaMemcpy(ph, D.phase, sizeof(ph), cudaMemcpyDeviceToHost));
+  } catch (const std::exception&) {
+    return NLS_E_CUDA;
+  }
+  for (int k = 0; k < 8; ++k) {
+    if (!ph[k]) continue;
+    if (out && n < cap) {
+      out[n].name = kPhaseNames[k];
+      out[n].launches = 0;
+      out[n].total_ms = (double)ph[k] / (double)D.clock_khz;
+    }
+    ++n;
+  }
   *n_out = std::min(n, cap);
   return NLS_OK;
 }
@@ -1688,6 +1798,7 @@ void reset_kernel_stats(Context& c) {
   if (!c.dev) return;
   try {
     c.dev->prof_flush();
+    CK(cudaMemsetAsync(c.dev->phase, 0, sizeof(unsigned long long) * 8, c.dev->s));
   } catch (const std::exception&) {
   }
   c.dev->stats.clear();
@@ -1766,6 +1877,8 @@ int local_corrections_noalloc(Context& c, const double* x, double* Fx, int32_t* 
   off = align_up(off + sizeof(double) * (size_t)s.total_nnz, 256);
   const size_t o_fac = off;
   off = align_up(off + fbytes * (size_t)s.total_factor, 256);
+  const size_t o_dinv = off;
+  off = align_up(off + fbytes * (size_t)s.total_dinv, 256);
   const size_t o_w = off;
   off = align_up(off + sizeof(double) * (size_t)s.total_n, 256);
   const size_t o_its = off;
@@ -1788,6 +1901,7 @@ int local_corrections_noalloc(Context& c, const double* x, double* Fx, int32_t* 
     LocalArgs A = make_args(c, s, D.ov);
     A.csr = (double*)(sc + o_csr);
     A.factor = sc + o_fac;
+    A.dinv = sc + o_dinv;
     A.wbuf = (double*)(sc + o_w);
     A.its = its_out ? its_out : (int32_t*)(sc + o_its);
     A.status = status_out ? status_out : (int32_t*)(sc + o_st);

@@ -72,7 +72,10 @@ EXPORTS = ["nls_options_default", "nls_create", "nls_destroy", "nls_strerror", "
            "nls_set_options", "nls_get_options", "nls_setup", "nls_setup_host", "nls_solve", "nls_get_sizes", "nls_get_local_dofs",
            "nls_get_overlap_elems", "nls_get_owners", "nls_get_coarse_nodes", "nls_get_coarse_basis", "nls_eval_F",
            "nls_eval_Fx", "nls_apply_tangent", "nls_get_local_states", "nls_get_kernel_stats",
-           "nls_reset_kernel_stats", "nls_local_corrections_noalloc"]
+           "nls_reset_kernel_stats", "nls_local_corrections_noalloc", "nls_guess_create", "nls_guess_destroy",
+           "nls_guess_attach", "nls_guess_train", "nls_guess_pairs", "nls_guess_get_params", "nls_guess_set_params",
+           "nls_guess_get_normalisation", "nls_guess_set_normalisation", "nls_guess_gradient", "nls_guess_forward",
+           "nls_guess_counts"]
 
 _LIB = None
 _P = ctypes.c_void_p
@@ -122,6 +125,18 @@ def load() -> ctypes.CDLL:
         "nls_get_kernel_stats": (ctypes.c_int, [_P, i32, ctypes.POINTER(KernelStat), ctypes.POINTER(i32)]),
         "nls_reset_kernel_stats": (ctypes.c_int, [_P]),
         "nls_local_corrections_noalloc": (ctypes.c_int, [_P, _P, _P, _P, _P, dbl]),
+        "nls_guess_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, i32, i32, ctypes.c_uint64, i64]),
+        "nls_guess_destroy": (None, [_P]),
+        "nls_guess_attach": (ctypes.c_int, [_P, _P, i32]),
+        "nls_guess_train": (ctypes.c_int, [_P, i32, i32, dbl, ctypes.c_uint64, _P]),
+        "nls_guess_pairs": (ctypes.c_int, [_P, ctypes.POINTER(i64)]),
+        "nls_guess_get_params": (ctypes.c_int, [_P, _P, ctypes.POINTER(i64)]),
+        "nls_guess_set_params": (ctypes.c_int, [_P, _P, i64]),
+        "nls_guess_get_normalisation": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(ctypes.c_float)]),
+        "nls_guess_set_normalisation": (ctypes.c_int, [_P, _P, _P, ctypes.c_float]),
+        "nls_guess_gradient": (ctypes.c_int, [_P, i32, _P, _P, i32, _P, ctypes.POINTER(ctypes.c_float)]),
+        "nls_guess_forward": (ctypes.c_int, [_P, i32, _P, _P]),
+        "nls_guess_counts": (ctypes.c_int, [_P, ctypes.POINTER(i64), ctypes.POINTER(i64)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -323,6 +338,109 @@ class Solver:
         return out
 
 
+GUESS_USE, GUESS_HARVEST = 1, 2
+GUESS_FEATURES, GUESS_OUTPUTS = 391, 1024
+
+
+class GuessNet:
+    """The learned-initial-guess network (include/nls.h); host arrays are numpy float32."""
+
+    def __init__(self, h1: int = 512, h2: int = 512, seed: int = 1, capacity: int = 0, device: int = 0):
+        self.lib = load()
+        self.h = _P()
+        st = self.lib.nls_guess_create(ctypes.byref(self.h), device, h1, h2, seed, capacity)
+        if st < 0:
+            raise NLSError(st, "nls_guess_create", "")
+        self.h1, self.h2 = h1, h2
+
+    def close(self):
+        if self.h:
+            self.lib.nls_guess_destroy(self.h)
+            self.h = _P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st, where):
+        if st < 0:
+            raise NLSError(st, where, "")
+
+    def pairs(self) -> int:
+        n = ctypes.c_int64()
+        self._check(self.lib.nls_guess_pairs(self.h, ctypes.byref(n)), "nls_guess_pairs")
+        return n.value
+
+    def params(self) -> np.ndarray:
+        n = ctypes.c_int64()
+        self._check(self.lib.nls_guess_get_params(self.h, None, ctypes.byref(n)), "nls_guess_get_params")
+        out = np.zeros(n.value, dtype=np.float32)
+        self._check(self.lib.nls_guess_get_params(self.h, _ptr(out), ctypes.byref(n)), "nls_guess_get_params")
+        return out
+
+    def set_params(self, p: np.ndarray):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        self._check(self.lib.nls_guess_set_params(self.h, _ptr(p), p.shape[0]), "nls_guess_set_params")
+
+    def normalisation(self):
+        mean = np.zeros(GUESS_FEATURES, dtype=np.float32)
+        scale = np.zeros(GUESS_FEATURES, dtype=np.float32)
+        ts = ctypes.c_float()
+        self._check(self.lib.nls_guess_get_normalisation(self.h, _ptr(mean), _ptr(scale), ctypes.byref(ts)),
+                    "nls_guess_get_normalisation")
+        return mean, scale, ts.value
+
+    def set_normalisation(self, mean, scale, tscale: float):
+        mean = np.ascontiguousarray(mean, dtype=np.float32)
+        scale = np.ascontiguousarray(scale, dtype=np.float32)
+        self._check(self.lib.nls_guess_set_normalisation(self.h, _ptr(mean), _ptr(scale), tscale),
+                    "nls_guess_set_normalisation")
+
+    def gradient(self, X: np.ndarray, T: np.ndarray, bf16: bool = False):
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        T = np.ascontiguousarray(T, dtype=np.float32)
+        g = np.zeros(self.params().shape[0], dtype=np.float32)
+        L = ctypes.c_float()
+        self._check(self.lib.nls_guess_gradient(self.h, X.shape[0], _ptr(X), _ptr(T), 1 if bf16 else 0, _ptr(g),
+                                                ctypes.byref(L)), "nls_guess_gradient")
+        return g, L.value
+
+    def forward(self, X: np.ndarray) -> np.ndarray:
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        Y = np.zeros((X.shape[0], GUESS_OUTPUTS), dtype=np.float32)
+        self._check(self.lib.nls_guess_forward(self.h, X.shape[0], _ptr(X), _ptr(Y)), "nls_guess_forward")
+        return Y
+
+    def train(self, steps: int, batch: int = 256, lr: float = 1e-3, seed: int = 7) -> np.ndarray:
+        losses = np.zeros(steps, dtype=np.float32)
+        self._check(self.lib.nls_guess_train(self.h, steps, batch, lr, seed, _ptr(losses)), "nls_guess_train")
+        return losses
+
+    def split(self, flat: np.ndarray):
+        """[(W, b)] of the three layers from a flat parameter array."""
+        sizes = [GUESS_FEATURES, self.h1, self.h2, GUESS_OUTPUTS]
+        out, o = [], 0
+        for fi, fo in zip(sizes[:-1], sizes[1:]):
+            W = flat[o:o + fo * fi].reshape(fo, fi)
+            o += fo * fi
+            b = flat[o:o + fo]
+            o += fo
+            out.append((W, b))
+        return out
+
+
+def attach_guess(solver: "Solver", net: "GuessNet", mode: int):
+    solver._check(solver.lib.nls_guess_attach(solver.h, net.h if net else None, mode), "nls_guess_attach")
+
+
+def guess_counts(solver: "Solver"):
+    p, a = ctypes.c_int64(), ctypes.c_int64()
+    solver._check(solver.lib.nls_guess_counts(solver.h, ctypes.byref(p), ctypes.byref(a)), "nls_guess_counts")
+    return p.value, a.value
+
+
 def make_solver(p: Problem, coupling: str = "hybrid", precision: str = "fp32", coarse: Optional[bool] = None,
                 device: int = 0, setup: bool = True, **opts) -> Solver:
     """Context for a problem from ``paper_2410_24138_gb300.inputs`` with the given options."""
@@ -331,7 +449,7 @@ def make_solver(p: Problem, coupling: str = "hybrid", precision: str = "fp32", c
     use_coarse = (coupling != "one") if coarse is None else coarse
     s.set_coarse(COARSE_RGDSW if use_coarse else COARSE_NONE)
     prec = PREC_FP32_IR if precision == "fp32" else PREC_FP64
-    kw = dict(coupling=COUPLING[coupling], local_precision=prec, load_steps=p.load_steps)
+    kw = dict(coupling=COUPLING[coupling], local_precision=prec, coarse_precision=prec, load_steps=p.load_steps)
     kw.update(opts)
     s.set_options(**kw)
     if setup == "host":
