@@ -204,7 +204,7 @@ def run_gpu(args):
         s.set_options(coupling=nls.COUPLING["hybrid"], load_steps=p.load_steps,
                       local_precision=nls.PREC_FP32_IR if precision == "fp32" else nls.PREC_FP64,
                       coarse_precision=nls.PREC_FP32_IR if precision == "fp32" else nls.PREC_FP64,
-                      profile_kernels=profile)
+                      profile_kernels=profile, autotune=1)
         t0 = time.perf_counter()
         s.setup()
         return s, time.perf_counter() - t0
@@ -271,7 +271,11 @@ def run_gpu(args):
     peaks, peak_kind = measured_peaks()
     dom_name, (dom_launches, dom_ms) = max(kstats.items(), key=lambda kv: kv[1][1])
     total_prof_ms = sum(v[1] for v in kstats.values())
-    roof = roofline_for(dom_name, dom_launches, dom_ms, sizes, peaks, peak_kind)
+    steps_per_launch = preps[-1].subdomain_newton_steps / max(1, preps[-1].outer_iterations)
+    roof = roofline_for(dom_name, dom_launches, dom_ms, sizes, peaks, peak_kind, steps_per_launch)
+    roof_top = [roofline_for(k, v[0], v[1], sizes, peaks, peak_kind, steps_per_launch)
+                for k, v in sorted(kstats.items(), key=lambda kv: -kv[1][1])[:3]]
+    tuning = chosen.tuning()
 
     if rank == 0:
         cpu = None
@@ -302,6 +306,8 @@ def run_gpu(args):
             "kernels_ms": {k: [v[0], round(v[1], 3), round(100.0 * v[1] / total_prof_ms, 1)] for k, v in
                            sorted(kstats.items(), key=lambda kv: -kv[1][1])[:8]},
             "roofline": roof,
+            "roofline_top3": roof_top,
+            "tuning": tuning,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * n_dofs, "d2h_bytes_per_step": 8 * n_dofs},
             "gpu_launches": int(sum(r.kernel_launches for r in reps)),
             "clocks": clk,
@@ -314,14 +320,35 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
-def roofline_for(name, launches, ms, sizes, peaks, peak_kind):
-    """Achieved algorithmic bandwidth (or ALU rate) of the dominant kernel per launch."""
+# FP32 FMA peak of the GB300 derived from its unit counts and clock: 152 SMs x 128 FP32 lanes
+# x 2 flops per FMA x 2.07 GHz (maximum SM clock).
+SMS, FP32_LANES_PER_SM = 152, 128
+
+
+def fp32_peak_tflops(peaks):
+    mhz = peaks.get("sm_max_mhz", 2070.0)
+    return SMS * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+
+
+def roofline_for(name, launches, ms, sizes, peaks, peak_kind, steps_per_launch=None):
+    """Achieved algorithmic bandwidth (or ALU rate) of a kernel per launch."""
     avg_s = ms * 1e-3 / max(1, launches)
+    if "local_newton" in name and steps_per_launch is not None:
+        # factorizations: one per local Newton step plus the refactorization at the converged
+        # state of every subdomain; one pair of triangular solves per Newton step
+        per_sub_steps = steps_per_launch / sizes.n_sub
+        flops = sizes.lu_flops * (per_sub_steps + 1.0) + sizes.solve_flops * per_sub_steps
+        peak = fp32_peak_tflops(peaks)
+        ach = flops / avg_s / 1e12
+        return {"kernel": name, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": None, "algorithmic_flops_per_launch": flops,
+                "avg_launch_ms": avg_s * 1e3,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock"}
     if "local_apply" in name:
         fb = sizes.factor_bytes
-        # one pass over the factors, the local Jacobian (value + column index), the table gather
-        # of the input vector and the owned scatter of the output
-        alg = (sizes.total_factor_entries * fb + sizes.total_local_nnz * 12 + sizes.total_table_dofs * 12
+        # one pass over the packed solve operands, the local Jacobian (value + column index), the
+        # table gather of the input vector and the owned scatter of the output
+        alg = (sizes.total_solve_entries * fb + sizes.total_local_nnz * 12 + sizes.total_table_dofs * 12
                + sizes.n_dofs * 8)
         peak = peaks["hbm_gbs"]
         return {"kernel": name, "bound": "hbm", "achieved": alg / avg_s / 1e9, "peak": peak, "unit": "GB/s",

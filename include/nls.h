@@ -77,10 +77,23 @@ typedef struct nls_options {
   int32_t gmres_maxit;
   double ir_rtol;             /* iterative refinement stops at ||r - J s|| <= ir_rtol ||r|| */
   int32_t ir_max_sweeps;
-  int32_t threads_per_block;  /* CTA size of the batched local kernels (0 = library choice) */
+  int32_t threads_per_block;  /* CTA size of the batched local Newton kernel, a multiple of 32 in
+                                 [64, 256] and at least 32 + the largest half bandwidth (raised to
+                                 that if smaller); 0 = library choice (or the autotuner's) */
   int32_t verbose;
   int32_t profile_kernels;    /* 1: time every kernel launch with CUDA events on the context's
                                  stream and accumulate per-kernel totals (nls_get_kernel_stats) */
+  int32_t cuda_graphs;        /* 1 (default): each GMRES iteration body (tangent application,
+                                 two Gram-Schmidt passes, norm, copy of the Hessenberg column) is
+                                 captured once per Krylov index into a CUDA graph and replayed;
+                                 0: plain stream launches.  Graphs are not used while
+                                 profile_kernels is set.  Results are identical either way. */
+  int32_t autotune;           /* 1: on the first use, time the batched local Newton kernel with
+                                 128- and 256-thread CTAs and the tangent kernel with CTA sizes
+                                 from 32 + b to 256 on the context's own data, and keep the
+                                 fastest (nls_get_tuning).  The choice changes the order of
+                                 floating-point reductions inside a subdomain only.  0 (default):
+                                 the library's fixed choice or threads_per_block. */
 } nls_options;
 
 /* Per-solve report. */
@@ -171,6 +184,13 @@ typedef struct nls_sizes {
   int64_t total_table_dofs;      /* sum_i dofs touched by Omega_i' */
   int32_t factor_bytes;          /* 4 (FP32 factors) or 8 (FP64 factors) per the current options */
   int32_t pad;
+  int64_t total_solve_entries;   /* sum_i entries of the packed triangular-solve operands that one
+                                    pair of triangular solves reads (diagonal-block inverses and
+                                    couplings, blocks of 32 rows in FP32 and 16 rows in FP64) */
+  double lu_flops;               /* sum_i flops of one no-pivoting band LU of subdomain i:
+                                    sum_k (lim_k + 2 lim_k^2), lim_k = min(b_i, n_i - 1 - k) */
+  double solve_flops;            /* sum_i flops of one forward + backward solve with the packed
+                                    operands: 2 entries read = 2 flops per entry used */
 } nls_sizes;
 
 /* Per-kernel timing collected while nls_options.profile_kernels is set.  `name` is a static
@@ -182,6 +202,17 @@ typedef struct nls_kernel_stat {
 } nls_kernel_stat;
 /* Copy up to `cap` entries (kernels with at least one launch) into out; *n_out receives the count. */
 int nls_get_kernel_stats(const nls_ctx* ctx, int32_t cap, nls_kernel_stat* out, int32_t* n_out);
+
+/* CTA sizes in use for the batched local Newton kernel and the tangent kernel, and whether
+ * they came from the autotuner (1) or the fixed rule (0).  Valid after nls_setup. */
+typedef struct nls_tuning {
+  int32_t newton_threads, apply_threads;
+  int32_t newton_tuned, apply_tuned;
+  double newton_ms[2];        /* measured launch times of the 128- and 256-thread variants (0: not tried) */
+  int32_t graphs_captured;    /* GMRES iteration graphs currently instantiated */
+  int32_t pad;
+} nls_tuning;
+int nls_get_tuning(const nls_ctx* ctx, nls_tuning* out);
 int nls_reset_kernel_stats(nls_ctx* ctx);
 int nls_get_sizes(const nls_ctx* ctx, nls_sizes* out);
 

@@ -1,5 +1,6 @@
 // C ABI entry points (include/nls.h): argument checking, copies of the caller's arrays, and
 // dispatch to the setup (setup.cpp) and the device solver (solver.cu).
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <exception>
@@ -44,6 +45,8 @@ void nls_options_default(nls_options* o) {
   o->ir_rtol = 1e-10;
   o->ir_max_sweeps = 5;
   o->threads_per_block = 0;
+  o->cuda_graphs = 1;
+  o->autotune = 0;
   o->verbose = 0;
 }
 
@@ -188,8 +191,10 @@ int nls_set_options(nls_ctx* ctx, const nls_options* o) {
     return fail(ctx, NLS_E_ARG, "unknown precision");
   if (o->load_steps < 1 || o->gmres_restart < 1 || o->gmres_maxit < 1 || o->inner_maxit < 0 || o->ls_trials < 1)
     return fail(ctx, NLS_E_ARG, "bad iteration limits");
-  if (o->threads_per_block != 0 && (o->threads_per_block < 64 || o->threads_per_block > 512 || o->threads_per_block % 32))
-    return fail(ctx, NLS_E_ARG, "threads_per_block must be 0 or a multiple of 32 in [64, 512]");
+  if (o->threads_per_block != 0 && (o->threads_per_block < 64 || o->threads_per_block > 256 || o->threads_per_block % 32))
+    return fail(ctx, NLS_E_ARG, "threads_per_block must be 0 or a multiple of 32 in [64, 256]");
+  if ((o->cuda_graphs != 0 && o->cuda_graphs != 1) || (o->autotune != 0 && o->autotune != 1))
+    return fail(ctx, NLS_E_ARG, "cuda_graphs and autotune must be 0 or 1");
   ctx->c.opt = *o;
   return NLS_OK;
 }
@@ -278,12 +283,30 @@ int nls_get_sizes(const nls_ctx* ctx, nls_sizes* o) {
   o->total_local_nnz = c.ov.total_nnz;
   o->total_table_dofs = c.ov.total_nt;
   o->factor_bytes = (c.opt.local_precision == NLS_PREC_FP32_IR) ? 4 : 8;
+  o->total_solve_entries = 0;
+  const int64_t bs = o->factor_bytes == 4 ? 32 : 16;
+  o->lu_flops = 0.0;
+  o->solve_flops = 0.0;
+  for (const nls::SubMeta& m : c.ov.meta) {
+    o->total_solve_entries += ((m.n + bs - 1) / bs) * (2 * bs * bs + 2 * (int64_t)m.b * bs);
+    for (int64_t k = 0; k < m.n; ++k) {
+      const double lim = (double)std::min<int64_t>(m.b, m.n - 1 - k);
+      o->lu_flops += lim + 2.0 * lim * lim;
+    }
+    o->solve_flops += 2.0 * (double)((m.n + bs - 1) / bs) * (2 * bs * bs + 2 * (double)m.b * bs);
+  }
   return NLS_OK;
 }
 
 int nls_get_kernel_stats(const nls_ctx* ctx, int32_t cap, nls_kernel_stat* out, int32_t* n_out) {
   if (!ctx || !n_out) return NLS_E_ARG;
   return nls::kernel_stats(ctx->c, cap, out, n_out);
+}
+
+int nls_get_tuning(const nls_ctx* ctx, nls_tuning* out) {
+  if (!ctx || !out) return NLS_E_ARG;
+  if (!ctx->c.is_setup) return NLS_E_ARG;
+  return nls::get_tuning(ctx->c, out);
 }
 
 int nls_local_corrections_noalloc(nls_ctx* ctx, const double* x, double* Fx, int32_t* its, int32_t* status,

@@ -94,6 +94,22 @@ struct Dev {
   bool tangent_ready = false;
   void* guess = nullptr;  // learned-guess attachment (guess.cu)
   double last_load = 1.0;
+  // CTA sizes (0 = fixed rule) and the autotuner's measurements
+  int newton_T = 0, apply_T = 0;
+  bool newton_tuned = false, apply_tuned = false;
+  double newton_ms[2] = {0.0, 0.0};
+  // GMRES iteration graphs, one per Krylov index, valid while `graph_key` matches
+  cudaStream_t cap = nullptr;  // private stream the graphs are captured on
+  std::vector<cudaGraphExec_t> it_exec;
+  std::vector<int64_t> it_launches;
+  std::string graph_key;
+  void reset_graphs() {
+    for (auto& g : it_exec)
+      if (g) cudaGraphExecDestroy(g);
+    it_exec.clear();
+    it_launches.clear();
+    graph_key.clear();
+  }
   // per-launch CUDA-event timing (nls_options.profile_kernels)
   bool prof = false;
   struct EvRec {

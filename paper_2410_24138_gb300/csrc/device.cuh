@@ -369,15 +369,35 @@ __device__ int band_lu_inplace_cj(int n, int b, FT* __restrict__ F, FT* win, FT*
     FT u[CJ];
 #pragma unroll
     for (int c = 0; c < CJ; ++c) u[c] = (lane + 32 * c < lim) ? rowk[b + 1 + lane + 32 * c] : (FT)0;
-    for (int ri = wid; ri < lim; ri += NW) {
-      int slot = s1 + ri;
-      if (slot >= R) slot -= R;
-      FT* rowi = win + slot * W + b - ri;
-      const FT l = rowi[-1] * rpk;
+    // rows in groups of four: all loads of a group are issued before its FMAs and stores, so
+    // the shared-memory latency of four rows overlaps (rows of one step never alias)
+    for (int q0 = wid; q0 < lim; q0 += 4 * NW) {
+      FT lv[4], val[4][CJ];
+      FT* rowp[4];
 #pragma unroll
-      for (int c = 0; c < CJ; ++c) {
-        const int cj = lane + 32 * c;
-        if (cj < lim) rowi[cj] -= l * u[c];
+      for (int g = 0; g < 4; ++g) {
+        const int ri = q0 + g * NW;
+        int slot = s1 + ri;
+        if (slot >= R) slot -= R;
+        rowp[g] = win + slot * W + b - ri;
+        const bool in = ri < lim;
+        lv[g] = in ? rowp[g][-1] : (FT)0;
+#pragma unroll
+        for (int c = 0; c < CJ; ++c) val[g][c] = (in && lane + 32 * c < lim) ? rowp[g][lane + 32 * c] : (FT)0;
+      }
+#pragma unroll
+      for (int g = 0; g < 4; ++g) {
+        const FT l = lv[g] * rpk;
+#pragma unroll
+        for (int c = 0; c < CJ; ++c) val[g][c] -= l * u[c];
+      }
+#pragma unroll
+      for (int g = 0; g < 4; ++g) {
+        if (q0 + g * NW < lim) {
+#pragma unroll
+          for (int c = 0; c < CJ; ++c)
+            if (lane + 32 * c < lim) rowp[g][lane + 32 * c] = val[g][c];
+        }
       }
     }
     // thread 0 updated the new pivot A[k+1][k+1] itself (row 0, column 0 of the update)
@@ -529,22 +549,36 @@ __device__ void band_solve(int n, int b, const FT* __restrict__ F, FT* y) {
 }
 
 // ------------------------------------------------------------------------------------------
-// Explicit inverses of the BS x BS diagonal blocks of the band factors.  Block t (rows
-// t BS .. t BS + bs - 1) stores inv(L_tt) then inv(U_tt), each BS x BS row-major (padded with
-// the identity beyond bs), so that the solve replaces the BS-step dependent shuffle chain of a
+// Packed solve operands.  After a factorization the operands of the two triangular solves are
+// copied, block by block (BS rows), into a layout in which every warp-wide load of the solve
+// reads BS consecutive values:
+//
+//   block t (rows k0 = t BS .. k0 + bs - 1), PB = 2 BS^2 + 2 b BS entries:
+//     [0, BS^2)               inv(L_tt), column-major: entry (r, j) at j BS + r (identity padded)
+//     [BS^2, 2 BS^2)          inv(U_tt), column-major (U's diagonal is stored inverted)
+//     [2 BS^2, + b BS)        CL: entry (j, r) at j b + r = L[k0 + BS + r][k0 + j]
+//     [2 BS^2 + b BS, + b BS) CU: entry (j, r) at j b + r = U[k0 - 1 - r][k0 + j]
+//
+// The explicit diagonal-block inverses replace the BS-step dependent shuffle chain of a
 // diagonal block by one short dot product per row.  One warp per block; `tmp` holds
-// (BS x (BS + 1)) FT per warp that takes part (`nwarps`).
+// BS x (BS + 1) FT per warp that takes part (`nwarps`).
 // ------------------------------------------------------------------------------------------
 template <typename FT>
-__device__ void band_diag_inverses(int n, int b, const FT* __restrict__ F, FT* __restrict__ Dinv, FT* tmp, int nwarps) {
+__host__ __device__ constexpr int64_t packed_block_entries(int b) {
+  return 2 * (int64_t)SolveBlock<FT>::BS * SolveBlock<FT>::BS + 2 * (int64_t)b * SolveBlock<FT>::BS;
+}
+
+template <typename FT>
+__device__ void band_pack_solve(int n, int b, const FT* __restrict__ F, FT* __restrict__ P, FT* tmp, int nwarps) {
   constexpr int BS = SolveBlock<FT>::BS;
   const int W = 2 * b + 1, lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int nblk = (n + BS - 1) / BS;
+  const int64_t PB = packed_block_entries<FT>(b);
   if (wid < nwarps) {
     FT* M = tmp + wid * BS * (BS + 1);
     for (int t = wid; t < nblk; t += nwarps) {
       const int k0 = t * BS, bs = min(BS, n - k0);
-      FT* out = Dinv + (int64_t)t * 2 * BS * BS;
+      FT* out = P + (int64_t)t * PB;
       // lower: M[i][j] = L[k0+i][k0+j] (j < i), unit diagonal
       for (int e = lane; e < BS * BS; e += 32) {
         const int i = e / BS, j = e % BS;
@@ -564,7 +598,7 @@ __device__ void band_diag_inverses(int n, int b, const FT* __restrict__ F, FT* _
           x[i] = acc;
         }
 #pragma unroll
-        for (int i = 0; i < BS; ++i) out[i * BS + lane] = x[i];
+        for (int i = 0; i < BS; ++i) out[lane * BS + i] = x[i];
       }
       __syncwarp();
       // upper: M[i][j] = U[k0+i][k0+j] (j > i), M[i][i] = 1/U_ii (stored reciprocal)
@@ -585,9 +619,18 @@ __device__ void band_diag_inverses(int n, int b, const FT* __restrict__ F, FT* _
           for (int j = i + 1; j < BS; ++j) acc -= M[i * (BS + 1) + j] * x[j];
           x[i] = acc * M[i * (BS + 1) + i];
         }
-        FT* ou = out + BS * BS;
 #pragma unroll
-        for (int i = 0; i < BS; ++i) ou[i * BS + lane] = x[i];
+        for (int i = 0; i < BS; ++i) out[BS * BS + lane * BS + i] = x[i];
+      }
+      // couplings (coalesced writes; the band is read once per factorization)
+      FT* cl = out + 2 * BS * BS;
+      FT* cu = cl + (int64_t)b * BS;
+      for (int e = lane; e < BS * b; e += 32) {
+        const int j = e / b, r = e % b;
+        const int il = k0 + BS + r, dl = j - BS - r + b;
+        cl[e] = (j < bs && il < n && dl >= 0) ? F[(int64_t)il * W + dl] : (FT)0;
+        const int iu = k0 - 1 - r;
+        cu[e] = (j < bs && iu >= 0 && j + 1 + r <= b) ? F[(int64_t)iu * W + (j + 1 + r + b)] : (FT)0;
       }
       __syncwarp();
     }
@@ -595,36 +638,36 @@ __device__ void band_diag_inverses(int n, int b, const FT* __restrict__ F, FT* _
   __syncthreads();
 }
 
-// Triangular solves with the band factors and the explicit diagonal-block inverses: warp 0
-// applies the block inverse (lane l: row l of inv(L_tt) or inv(U_tt) dotted with the block of
-// y), threads 32 .. 32 + b - 1 apply the coupling to the next b rows.  Register prefetch of
-// the next block as in band_solve.  Needs blockDim.x >= 32 + b.
+// Triangular solves with the packed operands, in place on y[0..n) (shared memory): warp 0
+// applies the block inverse (lane r: row r of inv(L_tt) or inv(U_tt) dotted with the block of
+// y), threads 32 .. 32 + b - 1 apply the coupling to the next b rows.  The operands of the next
+// block are loaded into registers while the current one is applied.  Needs blockDim.x >= 32 + b.
 template <typename FT>
-__device__ void band_solve_inv(int n, int b, const FT* __restrict__ F, const FT* __restrict__ Dinv, FT* y) {
+__device__ void band_solve_packed(int n, int b, const FT* __restrict__ P, FT* y) {
   constexpr int BS = SolveBlock<FT>::BS;
-  const int W = 2 * b + 1, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const bool diag = wid == 0 && lane < BS;
   const bool offd = tid >= 32 && tid < 32 + b;
   const int r = tid - 32;
+  const int64_t PB = packed_block_entries<FT>(b);
+  const int nblk = (n + BS - 1) / BS;
   FT cur[BS], nxt[BS];
-#define NLS_LOAD_FWDI(k0_, R_)                                                            \
-  {                                                                                       \
-    const int kb_ = min(BS, n - (k0_));                                                   \
-    if (diag) {                                                                           \
-      const FT* Li_ = Dinv + (int64_t)((k0_) / BS) * 2 * BS * BS + lane * BS;             \
-      _Pragma("unroll") for (int j = 0; j < BS; ++j) R_[j] = Li_[j];                      \
-    } else if (offd) {                                                                    \
-      const int i_ = (k0_) + kb_ + r;                                                     \
-      _Pragma("unroll") for (int j = 0; j < BS; ++j) {                                    \
-        const int d = j + b - kb_ - r;                                                    \
-        R_[j] = (i_ < n && j < kb_ && d >= 0) ? F[(int64_t)i_ * W + d] : (FT)0;           \
-      }                                                                                   \
-    }                                                                                     \
+  // forward: diag lanes read inv(L_tt) (offset 0), coupling threads read CL
+#define NLS_LOAD_PK(t_, R_, dofs_, cofs_)                                                   \
+  {                                                                                         \
+    const FT* Pt_ = P + (int64_t)(t_) * PB;                                                 \
+    if (diag) {                                                                             \
+      _Pragma("unroll") for (int j = 0; j < BS; ++j) R_[j] = Pt_[(dofs_) + j * BS + lane];  \
+    } else if (offd) {                                                                      \
+      _Pragma("unroll") for (int j = 0; j < BS; ++j) R_[j] = Pt_[(cofs_) + j * b + r];      \
+    }                                                                                       \
   }
-  if (n > 0) NLS_LOAD_FWDI(0, cur);
-  for (int k0 = 0; k0 < n; k0 += BS) {
-    const int kb = min(BS, n - k0);
-    if (k0 + BS < n) NLS_LOAD_FWDI(k0 + BS, nxt);
+  const int oL = 0, oU = BS * BS;
+  const int64_t oCL = 2 * BS * BS, oCU = 2 * BS * BS + (int64_t)b * BS;
+  if (n > 0) NLS_LOAD_PK(0, cur, oL, oCL);
+  for (int t = 0; t < nblk; ++t) {
+    const int k0 = t * BS, kb = min(BS, n - k0);
+    if (t + 1 < nblk) NLS_LOAD_PK(t + 1, nxt, oL, oCL);
     if (wid == 0) {  // the whole warp reaches __syncwarp; only lanes < BS hold a block row
       FT a0 = 0, a1 = 0;
       if (diag) {
@@ -639,13 +682,13 @@ __device__ void band_solve_inv(int n, int b, const FT* __restrict__ F, const FT*
     }
     __syncthreads();
     if (offd) {
-      const int i = k0 + kb + r;
+      const int i = k0 + BS + r;
       if (i < n) {
         FT a0 = 0, a1 = 0;
 #pragma unroll
         for (int j = 0; j < BS; j += 2) {
-          if (j < kb) a0 += cur[j] * y[k0 + j];
-          if (j + 1 < kb) a1 += cur[j + 1] * y[k0 + j + 1];
+          a0 += cur[j] * y[k0 + j];
+          a1 += cur[j + 1] * y[k0 + j + 1];
         }
         y[i] -= a0 + a1;
       }
@@ -654,27 +697,12 @@ __device__ void band_solve_inv(int n, int b, const FT* __restrict__ F, const FT*
 #pragma unroll
     for (int j = 0; j < BS; ++j) cur[j] = nxt[j];
   }
-#undef NLS_LOAD_FWDI
-#define NLS_LOAD_BWDI(t_, R_)                                                             \
-  {                                                                                       \
-    const int k0_ = (t_) * BS, kb_ = min(BS, n - k0_);                                     \
-    if (diag) {                                                                           \
-      const FT* Ui_ = Dinv + (int64_t)(t_) * 2 * BS * BS + BS * BS + lane * BS;          \
-      _Pragma("unroll") for (int j = 0; j < BS; ++j) R_[j] = Ui_[j];                      \
-    } else if (offd) {                                                                    \
-      const int i_ = k0_ - 1 - r;                                                         \
-      _Pragma("unroll") for (int j = 0; j < BS; ++j) {                                    \
-        R_[j] = (i_ >= 0 && j < kb_ && j + 1 + r <= b) ? F[(int64_t)i_ * W + (j + 1 + r + b)] : (FT)0; \
-      }                                                                                   \
-    }                                                                                     \
-  }
-  // blocks are aligned to multiples of BS (the last one may be partial), as in the inverses
-  const int nblk = (n + BS - 1) / BS;
-  if (n > 0) NLS_LOAD_BWDI(nblk - 1, cur);
+  // backward: diag lanes read inv(U_tt), coupling threads read CU
+  if (n > 0) NLS_LOAD_PK(nblk - 1, cur, oU, oCU);
   for (int t = nblk - 1; t >= 0; --t) {
-    const int k0 = t * BS, k1 = min(n, k0 + BS), kb = k1 - k0;
-    if (t > 0) NLS_LOAD_BWDI(t - 1, nxt);
-    if (wid == 0) {  // the whole warp reaches __syncwarp; only lanes < BS hold a block row
+    const int k0 = t * BS, kb = min(BS, n - k0);
+    if (t > 0) NLS_LOAD_PK(t - 1, nxt, oU, oCU);
+    if (wid == 0) {
       FT a0 = 0, a1 = 0;
       if (diag) {
 #pragma unroll
@@ -703,7 +731,7 @@ __device__ void band_solve_inv(int n, int b, const FT* __restrict__ F, const FT*
 #pragma unroll
     for (int j = 0; j < BS; ++j) cur[j] = nxt[j];
   }
-#undef NLS_LOAD_BWDI
+#undef NLS_LOAD_PK
 }
 
 }  // namespace dev

@@ -19,8 +19,13 @@ struct SubMeta {
   int32_t ncolor;  // element colours (no two elements of one colour share a node)
   int32_t nrows;   // CSR rows: n (local rows only) or nt (full Neumann rows)
   int64_t tnode_off, elem_off, color_off, rowptr_off, nnz_off, nnz, factor_off, vec_off, epos_off;
-  int64_t dinv_off;  // diagonal-block inverses of the band factors: 2048 * ceil(n / 32) entries
+  int64_t dinv_off;  // packed solve operands of the factors: packed_solve_entries(n, b) entries
 };
+
+// Entries of the packed triangular-solve operands of an n x n band factor with half bandwidth b
+// (per 32-row block: two 32 x 32 diagonal-block inverses and two 32 x b couplings in FP32; the
+// FP64 layout, 16-row blocks, needs at most the same number of entries).
+inline int64_t packed_solve_entries(int64_t n, int64_t b) { return ((n + 31) / 32) * (2048 + 64 * b); }
 
 // A batch of subdomain-local problems: overlapping subdomains (rows = local unknowns) or
 // non-overlapping ones (rows = all table dofs, for the coarse space).
@@ -51,7 +56,7 @@ struct DeviceLocalSet {
   uint8_t* owned = nullptr;
   double* csr_val = nullptr;       // FP64 local Jacobian (rows per meta.nrows)
   void* factor = nullptr;          // band factors, float or double per precision
-  void* dinv = nullptr;            // explicit inverses of the diagonal blocks of the factors
+  void* dinv = nullptr;            // packed triangular-solve operands of the factors
   double* w = nullptr;             // local states, concatenated (total_n)
   int32_t *its = nullptr, *status = nullptr;
   int32_t* order = nullptr;        // processing order (longest first)
@@ -137,6 +142,7 @@ int get_local_states(Context& c, double* w, int is_dev);
 int get_coarse_basis(const Context& c, double* P0);
 int kernel_stats(const Context& c, int32_t cap, nls_kernel_stat* out, int32_t* n_out);
 void reset_kernel_stats(Context& c);
+int get_tuning(const Context& c, nls_tuning* out);
 int local_corrections_noalloc(Context& c, const double* x, double* Fx, int32_t* its, int32_t* status, double load);
 // guess.cu
 int guess_attach(Context& c, nls_guess_net* net, int32_t mode);

@@ -231,7 +231,7 @@ void build_local_set(Context& c, LocalSet& s, int layers, bool neumann_rows, boo
     fa += (int64_t)m.n * (2 * m.b + 1);
     ve += m.n;
     ep += (int64_t)m.ne * ned * ned;
-    di += 2048 * (int64_t)((m.n + 31) / 32);
+    di += packed_solve_entries(m.n, m.b);
     s.max_n = std::max(s.max_n, m.n);
     s.max_nt = std::max(s.max_nt, m.nt);
     s.max_b = std::max(s.max_b, m.b);

@@ -54,7 +54,7 @@ struct LocalArgs {
   const uint8_t* owned;
   double* csr;
   void* factor;
-  void* dinv;
+  void* dinv;  // packed triangular-solve operands (diagonal-block inverses + couplings)
   double* wbuf;
   int32_t *its, *status;
   const int32_t* order;
@@ -256,7 +256,7 @@ __device__ int local_solve(const LocalArgs& A, const SubMeta& m, const int32_t* 
   const int n = m.n;
   for (int a = threadIdx.x; a < n; a += blockDim.x) yv[a] = (FT)rhs[a];
   __syncthreads();
-  dev::band_solve_inv<FT>(n, m.b, F, Dv, yv);
+  dev::band_solve_packed<FT>(n, m.b, Dv, yv);
   for (int a = threadIdx.x; a < n; a += blockDim.x) s[a] = (double)yv[a];
   __syncthreads();
   int sweeps = 0;
@@ -276,7 +276,7 @@ __device__ int local_solve(const LocalArgs& A, const SubMeta& m, const int32_t* 
       if (!(rn > A.ir_rtol * rhs_norm)) break;
       for (int a = threadIdx.x; a < n; a += blockDim.x) yv[a] = (FT)res[a];
       __syncthreads();
-      dev::band_solve_inv<FT>(n, m.b, F, Dv, yv);
+      dev::band_solve_packed<FT>(n, m.b, Dv, yv);
       for (int a = threadIdx.x; a < n; a += blockDim.x) s[a] += (double)yv[a];
       __syncthreads();
       ++sweeps;
@@ -288,8 +288,10 @@ __device__ int local_solve(const LocalArgs& A, const SubMeta& m, const int32_t* 
 // ------------------------------------------------------------------------------------------
 // k_local_newton: the batched local corrections T_i of Eq. 4
 // ------------------------------------------------------------------------------------------
-template <int LAW, typename FT>
-__global__ void __launch_bounds__(512) k_local_newton(LocalArgs A) {
+// MAXT is the largest CTA the instantiation is compiled for: 128-thread CTAs keep three CTAs
+// per SM within the register file, 256-thread CTAs get the whole register budget per thread.
+template <int LAW, typename FT, int MAXT>
+__global__ void __launch_bounds__(MAXT, (MAXT <= 128 ? 3 : 1)) k_local_newton(LocalArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
   const SmemPlan P = smem_plan<FT>(A.max_n, A.max_nt, A.max_b, true);
   double* xt = (double*)(smem + P.xt);
@@ -380,7 +382,7 @@ __global__ void __launch_bounds__(512) k_local_newton(LocalArgs A) {
         status = ST_PIVOT;
         break;
       }
-      dev::band_diag_inverses<FT>(n, m.b, F, Dv, win, inv_warps);
+      dev::band_pack_solve<FT>(n, m.b, F, Dv, win, inv_warps);
       mark(2);
       local_solve<FT>(A, m, rowptr, colidx, csr, F, Dv, r, rn, s, rt, yv, red);
       mark(3);
@@ -419,7 +421,7 @@ __global__ void __launch_bounds__(512) k_local_newton(LocalArgs A) {
       local_jacobian<LAW, JT, FT>(A, m, xt, csr, F);
       mark(5);
       if (dev::band_lu_inplace<FT>(n, m.b, F, win, rp, flag)) status = ST_PIVOT;
-      else dev::band_diag_inverses<FT>(n, m.b, F, Dv, win, inv_warps);
+      else dev::band_pack_solve<FT>(n, m.b, F, Dv, win, inv_warps);
       mark(6);
     }
     for (int a = tid; a < n; a += blockDim.x) {
@@ -600,7 +602,7 @@ __global__ void __launch_bounds__(1024) k_coarse_factor(int N0, int b0, const do
   for (int64_t k = threadIdx.x; k < total; k += blockDim.x) F[k] = (FT)A0[k];
   __syncthreads();
   const int bad = dev::band_lu_inplace<FT>(N0, b0, F, win, rp, flag);
-  if (!bad) dev::band_diag_inverses<FT>(N0, b0, F, Dinv, tmp, 4);
+  if (!bad) dev::band_pack_solve<FT>(N0, b0, F, Dinv, tmp, 4);
   if (threadIdx.x == 0) *status = bad ? ST_PIVOT : ST_OK;
 }
 
@@ -619,7 +621,7 @@ __global__ void __launch_bounds__(256) k_coarse_inverse(int N0, int b0, const do
   for (int col = blockIdx.x; col < N0; col += gridDim.x) {
     for (int a = threadIdx.x; a < N0; a += blockDim.x) y[a] = (a == col) ? (FT)1 : (FT)0;
     __syncthreads();
-    dev::band_solve_inv<FT>(N0, b0, F, Dinv, y);
+    dev::band_solve_packed<FT>(N0, b0, Dinv, y);
     for (int a = threadIdx.x; a < N0; a += blockDim.x) z[a] = (double)y[a];
     __syncthreads();
     if (sizeof(FT) == 4) {
@@ -638,7 +640,7 @@ __global__ void __launch_bounds__(256) k_coarse_inverse(int N0, int b0, const do
         if (!(rn > ir_rtol)) break;
         for (int a = threadIdx.x; a < N0; a += blockDim.x) y[a] = (FT)res[a];
         __syncthreads();
-        dev::band_solve_inv<FT>(N0, b0, F, Dinv, y);
+        dev::band_solve_packed<FT>(N0, b0, Dinv, y);
         for (int a = threadIdx.x; a < N0; a += blockDim.x) z[a] += (double)y[a];
         __syncthreads();
       }
@@ -693,7 +695,7 @@ __global__ void __launch_bounds__(256) k_coarse_solve(int N0, int b0, const doub
     loc += g[a] * g[a];
   }
   const double gn = sqrt(dev::block_sum(loc, red));
-  dev::band_solve_inv<FT>(N0, b0, F, Dinv, y);
+  dev::band_solve_packed<FT>(N0, b0, Dinv, y);
   for (int a = threadIdx.x; a < N0; a += blockDim.x) z[a] = (double)y[a];
   __syncthreads();
   if (sizeof(FT) == 4) {
@@ -712,7 +714,7 @@ __global__ void __launch_bounds__(256) k_coarse_solve(int N0, int b0, const doub
       if (!(rn > ir_rtol * gn)) break;
       for (int a = threadIdx.x; a < N0; a += blockDim.x) y[a] = (FT)res[a];
       __syncthreads();
-      dev::band_solve_inv<FT>(N0, b0, F, Dinv, y);
+      dev::band_solve_packed<FT>(N0, b0, Dinv, y);
       for (int a = threadIdx.x; a < N0; a += blockDim.x) z[a] += (double)y[a];
       __syncthreads();
     }
@@ -899,10 +901,17 @@ inline int grid_for(int64_t n, int threads = 256) {
 
 
 // The triangular solves need warp 0 plus one thread per coupled row (32 + b threads).
+int min_local_threads(const Context& c) { return ((32 + c.ov.max_b + 31) / 32) * 32; }
+
 int local_threads(const Context& c) {
-  const int need = ((32 + c.ov.max_b + 31) / 32) * 32;
-  const int pick = c.opt.threads_per_block ? c.opt.threads_per_block : (c.ndof == 1 ? 128 : 256);
-  return std::max(pick, need);
+  int pick = c.opt.threads_per_block ? c.opt.threads_per_block : (c.ndof == 1 ? 128 : 256);
+  if (!c.opt.threads_per_block && c.dev && c.dev->newton_T) pick = c.dev->newton_T;
+  return std::max(pick, min_local_threads(c));
+}
+
+int apply_threads(const Context& c) {
+  if (c.dev && c.dev->apply_T) return std::max(c.dev->apply_T, min_local_threads(c));
+  return std::max(64, min_local_threads(c));
 }
 
 bool fp32_local(const Context& c) { return c.opt.local_precision == NLS_PREC_FP32_IR; }
@@ -1017,6 +1026,35 @@ size_t local_newton_smem(const LocalSet& s) {
   return smem_plan<FT>(s.max_n, s.max_nt, s.max_b, true).total;
 }
 
+// Persistent grid: as many CTAs as fit on the device at once (registers and shared memory), at
+// most one per subdomain; the work counter hands out the subdomains.
+template <int LAW, typename FT, int MAXT>
+void launch_newton_t(Dev& D, int count, int T, size_t sm, const LocalArgs& A) {
+  int occ = 0;
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_local_newton<LAW, FT, MAXT>, T, sm));
+  const int grid = std::min(count, D.nsm * std::max(1, occ));
+  LAUNCH(D, (k_local_newton<LAW, FT, MAXT>), grid, T, sm, A);
+}
+
+template <int LAW, typename FT>
+void launch_newton_law(Dev& D, int count, int T, size_t sm, const LocalArgs& A) {
+  if (T <= 128) launch_newton_t<LAW, FT, 128>(D, count, T, sm, A);
+  else launch_newton_t<LAW, FT, 256>(D, count, T, sm, A);
+}
+
+void dispatch_local_newton(Context& c, const LocalSet& s, const LocalArgs& A, int T) {
+  Dev& D = *c.dev;
+  const bool f32 = fp32_local(c);
+  const size_t sm = f32 ? local_newton_smem<float>(s) : local_newton_smem<double>(s);
+  if (c.law == NLS_LAW_DIFFUSION) {
+    if (f32) launch_newton_law<NLS_LAW_DIFFUSION, float>(D, s.count, T, sm, A);
+    else launch_newton_law<NLS_LAW_DIFFUSION, double>(D, s.count, T, sm, A);
+  } else {
+    if (f32) launch_newton_law<NLS_LAW_NEOHOOKE, float>(D, s.count, T, sm, A);
+    else launch_newton_law<NLS_LAW_NEOHOOKE, double>(D, s.count, T, sm, A);
+  }
+}
+
 void launch_local_newton(Context& c, const double* x, double* out, double load, const double* guess, bool want_tangent,
                          int32_t* accepted = nullptr) {
   Dev& D = *c.dev;
@@ -1029,18 +1067,7 @@ void launch_local_newton(Context& c, const double* x, double* out, double load, 
   A.want_tangent = want_tangent ? 1 : 0;
   A.phase = D.prof ? D.phase : nullptr;
   CK(cudaMemsetAsync(D.ov.queue, 0, sizeof(int32_t), D.s));
-  const int T = local_threads(c);
-  const bool f32 = fp32_local(c);
-  const size_t sm = f32 ? local_newton_smem<float>(c.ov) : local_newton_smem<double>(c.ov);
-  int per_sm = (int)std::max<size_t>(1, std::min<size_t>(2048 / T, D.smem_optin / std::max<size_t>(sm + 1024, 1)));
-  int grid = std::min(c.ov.count, D.nsm * per_sm);
-  if (c.law == NLS_LAW_DIFFUSION) {
-    if (f32) LAUNCH(D, (k_local_newton<NLS_LAW_DIFFUSION, float>), grid, T, sm, A);
-    else LAUNCH(D, (k_local_newton<NLS_LAW_DIFFUSION, double>), grid, T, sm, A);
-  } else {
-    if (f32) LAUNCH(D, (k_local_newton<NLS_LAW_NEOHOOKE, float>), grid, T, sm, A);
-    else LAUNCH(D, (k_local_newton<NLS_LAW_NEOHOOKE, double>), grid, T, sm, A);
-  }
+  dispatch_local_newton(c, c.ov, A, local_threads(c));
 }
 
 void launch_local_apply(Context& c, const double* v, const double* add, double* out) {
@@ -1051,7 +1078,7 @@ void launch_local_apply(Context& c, const double* v, const double* add, double* 
   A.out = out;
   // the solves need warp 0 plus one thread per coupled row (32 + b); small CTAs let more
   // subdomains be in flight on every SM, which is what hides the latency of the solves
-  const int T = std::max(64, (32 + c.ov.max_b + 31) / 32 * 32);
+  const int T = apply_threads(c);
   if (fp32_local(c)) {
     const size_t sm = smem_plan<float>(c.ov.max_n, c.ov.max_nt, c.ov.max_b, false).total;
     LAUNCH(D, k_local_apply<float>, c.ov.count, T, sm, A);
@@ -1059,6 +1086,74 @@ void launch_local_apply(Context& c, const double* v, const double* add, double* 
     const size_t sm = smem_plan<double>(c.ov.max_n, c.ov.max_nt, c.ov.max_b, false).total;
     LAUNCH(D, k_local_apply<double>, c.ov.count, T, sm, A);
   }
+}
+
+// ---- autotuner (nls_options.autotune) -------------------------------------------------------
+// Candidates are timed with CUDA events on the context's own data and the fastest is kept for
+// the life of the context.  Every candidate computes the same quantities (only the order of
+// the reductions inside a subdomain differs), so the timed launches double as warm-up.
+template <typename F>
+float time_on_stream(Dev& D, F&& f) {
+  cudaEvent_t a, b;
+  CK(cudaEventCreate(&a));
+  CK(cudaEventCreate(&b));
+  CK(cudaEventRecord(a, D.s));
+  f();
+  CK(cudaEventRecord(b, D.s));
+  CK(cudaEventSynchronize(b));
+  float ms = 0.f;
+  CK(cudaEventElapsedTime(&ms, a, b));
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return ms;
+}
+
+void tune_local_newton(Context& c, const double* x, double* out, double load, const double* guess, int32_t* accepted) {
+  Dev& D = *c.dev;
+  if (D.newton_tuned || !c.opt.autotune || c.opt.threads_per_block) return;
+  const int need = min_local_threads(c);
+  const int cand[2] = {128, 256};
+  // warm-up with the fixed choice (first touch of the factor storage and the caches)
+  launch_local_newton(c, x, out, load, guess, true, accepted);
+  double best = INFINITY;
+  int bestT = 0;
+  for (int i = 0; i < 2; ++i) {
+    if (cand[i] < need) continue;
+    D.newton_T = cand[i];
+    const float ms = time_on_stream(D, [&] { launch_local_newton(c, x, out, load, guess, true, accepted); });
+    D.newton_ms[i] = ms;
+    if (ms < best) {
+      best = ms;
+      bestT = cand[i];
+    }
+  }
+  D.newton_T = bestT;
+  D.newton_tuned = true;
+}
+
+void tune_local_apply(Context& c, const double* v, double* out) {
+  Dev& D = *c.dev;
+  if (D.apply_tuned || !c.opt.autotune) return;
+  const int need = std::max(64, min_local_threads(c));
+  std::vector<int> cand;
+  for (int T : {need, need + 32, need + 64, 128, 192, 256})
+    if (T >= need && T <= 256 && std::find(cand.begin(), cand.end(), T) == cand.end()) cand.push_back(T);
+  D.apply_T = need;
+  launch_local_apply(c, v, nullptr, out);  // warm-up
+  double best = INFINITY;
+  int bestT = need;
+  for (int T : cand) {
+    D.apply_T = T;
+    float ms = INFINITY;
+    for (int rep = 0; rep < 2; ++rep)
+      ms = std::min(ms, time_on_stream(D, [&] { launch_local_apply(c, v, nullptr, out); }));
+    if (ms < best) {
+      best = ms;
+      bestT = T;
+    }
+  }
+  D.apply_T = bestT;
+  D.apply_tuned = true;
 }
 
 // ---- coarse ---------------------------------------------------------------------------------
@@ -1292,10 +1387,14 @@ int device_setup(Context& c) {
                                ", coarse " + std::to_string(c.cs.b0) + "); the band factorisation supports 128");
     need(local_newton_smem<float>(c.ov), "local Newton (FP32 factors)");
     if (!fp32_local(c)) need(local_newton_smem<double>(c.ov), "local Newton (FP64 factors)");
-    set_smem(k_local_newton<NLS_LAW_DIFFUSION, float>, lim);
-    set_smem(k_local_newton<NLS_LAW_DIFFUSION, double>, lim);
-    set_smem(k_local_newton<NLS_LAW_NEOHOOKE, float>, lim);
-    set_smem(k_local_newton<NLS_LAW_NEOHOOKE, double>, lim);
+    set_smem(k_local_newton<NLS_LAW_DIFFUSION, float, 128>, lim);
+    set_smem(k_local_newton<NLS_LAW_DIFFUSION, double, 128>, lim);
+    set_smem(k_local_newton<NLS_LAW_NEOHOOKE, float, 128>, lim);
+    set_smem(k_local_newton<NLS_LAW_NEOHOOKE, double, 128>, lim);
+    set_smem(k_local_newton<NLS_LAW_DIFFUSION, float, 256>, lim);
+    set_smem(k_local_newton<NLS_LAW_DIFFUSION, double, 256>, lim);
+    set_smem(k_local_newton<NLS_LAW_NEOHOOKE, float, 256>, lim);
+    set_smem(k_local_newton<NLS_LAW_NEOHOOKE, double, 256>, lim);
     set_smem(k_local_apply<float>, lim);
     set_smem(k_local_apply<double>, lim);
     set_smem(k_harmonic<NLS_LAW_DIFFUSION>, lim);
@@ -1319,7 +1418,7 @@ int device_setup(Context& c) {
       D.a0_ptr = D.upload(cs.a0_ptr);
       D.a0_src = D.upload(cs.a0_src);
       D.A0 = D.alloc<double>((size_t)cs.N0 * (2 * cs.b0 + 1));
-      const size_t ndinv = 2048 * (size_t)((cs.N0 + 31) / 32);
+      const size_t ndinv = (size_t)packed_solve_entries(cs.N0, cs.b0);
       if (fp32_coarse(c)) {
         D.A0f = D.alloc<float>((size_t)cs.N0 * (2 * cs.b0 + 1));
         D.A0dinv = D.alloc<float>(ndinv);
@@ -1391,6 +1490,8 @@ void device_free(Context& c) {
   cudaSetDevice(c.device);
   if (D.s) cudaStreamSynchronize(D.s);
   guess_free(c);
+  D.reset_graphs();
+  if (D.cap) cudaStreamDestroy(D.cap);
   for (void* p : D.allocs)
     if (p) cudaFree(p);
   if (D.h_scal) cudaFreeHost(D.h_scal);
@@ -1437,6 +1538,7 @@ FxInfo evaluate_Fx(Context& c, const double* u, double load, double* t_inner, do
   auto t1 = std::chrono::steady_clock::now();
   int32_t* accepted = nullptr;
   const double* proposal = guess_propose(c, point, load, &accepted);
+  tune_local_newton(c, point, D.Fx, load, proposal, accepted);
   launch_local_newton(c, point, D.Fx, load, proposal, true, accepted);
   guess_after_local(c, point, load, proposal != nullptr);
   std::vector<int32_t> its(c.ov.count), st(c.ov.count);
@@ -1509,11 +1611,59 @@ struct GmresResult {
 
 // GMRES(m), zero initial guess, classical Gram-Schmidt with one re-orthogonalisation
 // (device multi-dots), Givens rotations on the host.  Solution into D.gx.
+// Replays (capturing on first use) the graph of GMRES iteration body `j`.  The graphs hold
+// device pointers and kernel arguments, so they are keyed by everything those depend on: the
+// options, the coarse-solve form (explicit inverse or band factors) and the tangent CTA size.
+template <typename F>
+void run_iteration_graph(Context& c, int j, F&& body) {
+  Dev& D = *c.dev;
+  std::string key((const char*)&c.opt, sizeof(c.opt));
+  key += D.ainv_valid ? 'i' : 'b';
+  key += std::to_string(apply_threads(c));
+  if (key != D.graph_key || (int)D.it_exec.size() != D.m) {
+    D.reset_graphs();
+    D.graph_key = key;
+    D.it_exec.assign(D.m, nullptr);
+    D.it_launches.assign(D.m, 0);
+  }
+  if (!D.it_exec[j]) {
+    if (!D.cap) CK(cudaStreamCreateWithFlags(&D.cap, cudaStreamNonBlocking));
+    const cudaStream_t saved = D.s;
+    const int64_t l0 = D.launches;
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(D.cap, cudaStreamCaptureModeThreadLocal));
+    D.s = D.cap;
+    try {
+      body();
+    } catch (...) {
+      cudaStreamEndCapture(D.cap, &g);
+      if (g) cudaGraphDestroy(g);
+      D.s = saved;
+      D.launches = l0;
+      throw;
+    }
+    const cudaError_t e = cudaStreamEndCapture(D.cap, &g);
+    D.s = saved;
+    CK(e);
+    cudaGraphExec_t ex = nullptr;
+    const cudaError_t ei = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    CK(ei);
+    D.it_exec[j] = ex;
+    D.it_launches[j] = D.launches - l0;
+    D.launches = l0;
+  }
+  CK(cudaGraphLaunch(D.it_exec[j], D.s));
+  D.launches += D.it_launches[j];
+}
+
 GmresResult gmres(Context& c, const double* b) {
   Dev& D = *c.dev;
   const int64_t N = c.N;
   const int m = D.m;
   GmresResult R;
+  tune_local_apply(c, b, D.t1);
+  const bool graphs = c.opt.cuda_graphs && !D.prof;
   CK(cudaMemsetAsync(D.gx, 0, sizeof(double) * N, D.s));
   const double bn = norm2(D, N, b);
   if (bn == 0.0) {
@@ -1536,18 +1686,23 @@ GmresResult gmres(Context& c, const double* b) {
     while (j < m && R.its < c.opt.gmres_maxit) {
       double* vj = D.V + (size_t)j * N;
       double* w = D.V + (size_t)(j + 1) * N;
-      tangent(c, vj, w);
-      // CGS2
-      for (int pass = 0; pass < 2; ++pass) {
-        LAUNCH(D, k_multidot_partial, kVecBlocks, kVecThreads, 0, N, j + 1, D.V, N, w, D.partial);
-        LAUNCH(D, k_partial_final, std::min(j + 1, 64), 256, 0, j + 1, D.partial, D.scal + pass * (kMaxGmresVecs / 2));
-        LAUNCH(D, k_multiaxpy, grid_for(N), 256, 0, N, j + 1, D.V, N, D.scal + pass * (kMaxGmresVecs / 2), -1.0, w);
-      }
-      LAUNCH(D, k_multidot_partial, kVecBlocks, kVecThreads, 0, N, 1, w, (int64_t)0, w, D.partial);
-      LAUNCH(D, k_partial_final, 1, 256, 0, 1, D.partial, D.scal + kMaxGmresVecs);
-      LAUNCH(D, k_sqrt_inplace, 1, 1, 0, D.scal + kMaxGmresVecs);
-      CK(cudaMemcpyAsync(D.h_scal, D.scal, sizeof(double) * (kMaxGmresVecs + 1), cudaMemcpyDeviceToHost, D.s));
-      LAUNCH(D, k_scale_inv, grid_for(N), 256, 0, N, w, D.scal + kMaxGmresVecs, w);
+      auto body = [&]() {
+        tangent(c, vj, w);
+        // CGS2
+        for (int pass = 0; pass < 2; ++pass) {
+          LAUNCH(D, k_multidot_partial, kVecBlocks, kVecThreads, 0, N, j + 1, D.V, N, w, D.partial);
+          LAUNCH(D, k_partial_final, std::min(j + 1, 64), 256, 0, j + 1, D.partial,
+                 D.scal + pass * (kMaxGmresVecs / 2));
+          LAUNCH(D, k_multiaxpy, grid_for(N), 256, 0, N, j + 1, D.V, N, D.scal + pass * (kMaxGmresVecs / 2), -1.0, w);
+        }
+        LAUNCH(D, k_multidot_partial, kVecBlocks, kVecThreads, 0, N, 1, w, (int64_t)0, w, D.partial);
+        LAUNCH(D, k_partial_final, 1, 256, 0, 1, D.partial, D.scal + kMaxGmresVecs);
+        LAUNCH(D, k_sqrt_inplace, 1, 1, 0, D.scal + kMaxGmresVecs);
+        CK(cudaMemcpyAsync(D.h_scal, D.scal, sizeof(double) * (kMaxGmresVecs + 1), cudaMemcpyDeviceToHost, D.s));
+        LAUNCH(D, k_scale_inv, grid_for(N), 256, 0, N, w, D.scal + kMaxGmresVecs, w);
+      };
+      if (graphs) run_iteration_graph(c, j, body);
+      else body();
       sync(D);
       for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = D.h_scal[i] + D.h_scal[kMaxGmresVecs / 2 + i];
       const double hn = D.h_scal[kMaxGmresVecs];
@@ -1914,20 +2069,24 @@ int local_corrections_noalloc(Context& c, const double* x, double* Fx, int32_t* 
     // the work counter must start at zero; the rest of the area is written before it is read
     CK(cudaMemsetAsync(A.queue, 0, sizeof(int32_t), D.s));
     LAUNCH(D, k_mask, grid_for(c.N), 256, 0, c.N, D.free_dof, Fx);
-    const int T = local_threads(c);
-    const size_t sm = f32 ? local_newton_smem<float>(s) : local_newton_smem<double>(s);
-    const int per_sm = (int)std::max<size_t>(1, std::min<size_t>(2048 / T, D.smem_optin / (sm + 1024)));
-    const int grid = std::min(s.count, D.nsm * per_sm);
-    if (c.law == NLS_LAW_DIFFUSION) {
-      if (f32) LAUNCH(D, (k_local_newton<NLS_LAW_DIFFUSION, float>), grid, T, sm, A);
-      else LAUNCH(D, (k_local_newton<NLS_LAW_DIFFUSION, double>), grid, T, sm, A);
-    } else {
-      if (f32) LAUNCH(D, (k_local_newton<NLS_LAW_NEOHOOKE, float>), grid, T, sm, A);
-      else LAUNCH(D, (k_local_newton<NLS_LAW_NEOHOOKE, double>), grid, T, sm, A);
-    }
+    dispatch_local_newton(c, s, A, local_threads(c));
   } catch (const std::exception& ex) {
     c.last_error = ex.what();
     return NLS_E_CUDA;
+  }
+  return NLS_OK;
+}
+
+int get_tuning(const Context& c, nls_tuning* out) {
+  std::memset(out, 0, sizeof(*out));
+  out->newton_threads = local_threads(c);
+  out->apply_threads = c.dev ? apply_threads(c) : std::max(64, min_local_threads(c));
+  if (c.dev) {
+    out->newton_tuned = c.dev->newton_tuned ? 1 : 0;
+    out->apply_tuned = c.dev->apply_tuned ? 1 : 0;
+    out->newton_ms[0] = c.dev->newton_ms[0];
+    out->newton_ms[1] = c.dev->newton_ms[1];
+    for (auto g : c.dev->it_exec) out->graphs_captured += g ? 1 : 0;
   }
   return NLS_OK;
 }

@@ -33,7 +33,7 @@ class Options(ctypes.Structure):
                 ("gmres_rtol", ctypes.c_double), ("gmres_restart", ctypes.c_int32), ("gmres_maxit", ctypes.c_int32),
                 ("ir_rtol", ctypes.c_double), ("ir_max_sweeps", ctypes.c_int32),
                 ("threads_per_block", ctypes.c_int32), ("verbose", ctypes.c_int32),
-                ("profile_kernels", ctypes.c_int32)]
+                ("profile_kernels", ctypes.c_int32), ("cuda_graphs", ctypes.c_int32), ("autotune", ctypes.c_int32)]
 
 
 class Report(ctypes.Structure):
@@ -57,7 +57,20 @@ class Sizes(ctypes.Structure):
                 ("max_half_band", ctypes.c_int32), ("coarse_half_band", ctypes.c_int32),
                 ("device_bytes", ctypes.c_int64), ("total_factor_entries", ctypes.c_int64),
                 ("total_local_nnz", ctypes.c_int64), ("total_table_dofs", ctypes.c_int64),
-                ("factor_bytes", ctypes.c_int32), ("pad", ctypes.c_int32)]
+                ("factor_bytes", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("total_solve_entries", ctypes.c_int64), ("lu_flops", ctypes.c_double),
+                ("solve_flops", ctypes.c_double)]
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("newton_threads", ctypes.c_int32), ("apply_threads", ctypes.c_int32),
+                ("newton_tuned", ctypes.c_int32), ("apply_tuned", ctypes.c_int32),
+                ("newton_ms", ctypes.c_double * 2), ("graphs_captured", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {"newton_threads": self.newton_threads, "apply_threads": self.apply_threads,
+                "newton_tuned": bool(self.newton_tuned), "apply_tuned": bool(self.apply_tuned),
+                "newton_ms": list(self.newton_ms), "graphs_captured": self.graphs_captured}
 
 
 class KernelStat(ctypes.Structure):
@@ -75,7 +88,7 @@ EXPORTS = ["nls_options_default", "nls_create", "nls_destroy", "nls_strerror", "
            "nls_reset_kernel_stats", "nls_local_corrections_noalloc", "nls_guess_create", "nls_guess_destroy",
            "nls_guess_attach", "nls_guess_train", "nls_guess_pairs", "nls_guess_get_params", "nls_guess_set_params",
            "nls_guess_get_normalisation", "nls_guess_set_normalisation", "nls_guess_gradient", "nls_guess_forward",
-           "nls_guess_counts"]
+           "nls_guess_counts", "nls_get_tuning"]
 
 _LIB = None
 _P = ctypes.c_void_p
@@ -123,6 +136,7 @@ def load() -> ctypes.CDLL:
         "nls_apply_tangent": (ctypes.c_int, [_P, _P, _P, ctypes.c_int]),
         "nls_get_local_states": (ctypes.c_int, [_P, _P, ctypes.c_int]),
         "nls_get_kernel_stats": (ctypes.c_int, [_P, i32, ctypes.POINTER(KernelStat), ctypes.POINTER(i32)]),
+        "nls_get_tuning": (ctypes.c_int, [_P, ctypes.POINTER(Tuning)]),
         "nls_reset_kernel_stats": (ctypes.c_int, [_P]),
         "nls_local_corrections_noalloc": (ctypes.c_int, [_P, _P, _P, _P, _P, dbl]),
         "nls_guess_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, i32, i32, ctypes.c_uint64, i64]),
@@ -322,6 +336,12 @@ class Solver:
         n = ctypes.c_int32()
         self._check(self.lib.nls_get_kernel_stats(self.h, cap, arr, ctypes.byref(n)), "nls_get_kernel_stats")
         return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].total_ms)) for i in range(n.value)}
+
+    def tuning(self) -> dict:
+        """CTA sizes in use (autotuned or fixed) and the number of captured GMRES iteration graphs."""
+        t = Tuning()
+        self._check(self.lib.nls_get_tuning(self.h, ctypes.byref(t)), "nls_get_tuning")
+        return t.as_dict()
 
     def reset_kernel_stats(self):
         self._check(self.lib.nls_reset_kernel_stats(self.h), "nls_reset_kernel_stats")
