@@ -115,10 +115,14 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
+            # the timed region starts once the sampler is producing lines
+            t0 = time.time()
+            while not self.lines and time.time() - t0 < 3.0:
+                time.sleep(0.01)
         except OSError:
             self.proc = None
 
@@ -291,7 +295,9 @@ def run_gpu(args):
             "config": {"workload": desc, "coupling": "hybrid", "precision": "FP32 local and coarse band factors + FP64 iterative refinement; FP64 residuals, GMRES, coarse matrix",
                        "l2": "512 MB buffer written between steps; working set > L2",
                        "parallelism": "replicas" if world > 1 else "single GPU", "setup_s": setup_s,
-                       "n_dofs": n_dofs, "n_sub": sizes.n_sub, "coarse_dofs": sizes.n_coarse_dofs},
+                       "n_dofs": n_dofs, "n_sub": sizes.n_sub, "coarse_dofs": sizes.n_coarse_dofs,
+                       "max_local_dofs": sizes.max_local_dofs, "max_half_band": sizes.max_half_band,
+                       "coarse_half_band": sizes.coarse_half_band},
             "time_to_solution_s": {"chosen": statistics.median(times) * 1e-3,
                                    "plain_fp64": statistics.median(p_times) * 1e-3},
             "subdomain_newton_steps_per_s": {"chosen": value / world, "plain_fp64": plain_rate},
@@ -364,7 +370,7 @@ def roofline_for(name, launches, ms, sizes, peaks, peak_kind, steps_per_launch=N
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3"])

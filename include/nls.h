@@ -257,8 +257,14 @@ int nls_get_local_states(nls_ctx* ctx, double* w_out, int is_device);
  * bilinearly interpolated correction.  Layers: 391 -> h1 -> h2 -> 1024, tanh-form GELU.
  * Training: BF16 operands on the tensor cores with FP32 accumulation, FP32 master weights,
  * Adam, loss 1/(2B) sum ||y - t||^2 on normalised inputs and targets.  Inference: FP32.
- * A guess is used only where its local residual is smaller than that of R_i x (the start the
- * method uses otherwise), so convergence to tolerance does not depend on the network.
+ * Before the test, `sweeps` damped Jacobi steps w <- w - omega r(w) / d(w) on the local
+ * problem remove the pointwise (high-frequency) part of the network's error, which otherwise
+ * dominates the residual: d_a(w) = (1 + w_a^2) sum_{e owns a} k_e |grad phi_a|^2 |e|, the
+ * diagonal of the Jacobian's leading term (defaults: 6 sweeps, omega = 0.8, the damping that
+ * minimises the smoothing factor of Jacobi on the five-point stencil P1 yields here).
+ * A guess is used only where its (smoothed) local residual is smaller than that of R_i x (the
+ * start the method uses otherwise); the local stopping test stays relative to the residual at
+ * R_i x, so convergence to tolerance does not depend on the network.
  * The network lives on one device; every array below is a host pointer. */
 typedef struct nls_guess_net nls_guess_net;
 #define NLS_GUESS_FEATURES 391
@@ -293,6 +299,9 @@ int nls_guess_gradient(nls_guess_net* net, int32_t B, const float* X, const floa
 int nls_guess_forward(nls_guess_net* net, int32_t B, const float* X, float* Y);
 /* Guesses proposed and accepted by the local solves since the last call (then reset). */
 int nls_guess_counts(nls_ctx* ctx, int64_t* proposed, int64_t* accepted);
+/* Smoothing of proposed starts (see above): sweeps in [0, 64], omega in (0, 1].  Needs an
+ * attached network; attaching resets the defaults. */
+int nls_guess_set_smoothing(nls_ctx* ctx, int32_t sweeps, double omega);
 
 /* ---- allocation-free variant (the paper has no counterpart) ----------------------------
  * Local corrections F_1(x) = sum_i P~_i T_i(x) of the context's overlapping subdomains -- the

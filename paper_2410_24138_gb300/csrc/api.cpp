@@ -320,6 +320,11 @@ int nls_guess_attach(nls_ctx* ctx, nls_guess_net* net, int32_t mode) {
   return nls::guess_attach(ctx->c, net, mode);
 }
 
+int nls_guess_set_smoothing(nls_ctx* ctx, int32_t sweeps, double omega) {
+  if (!ctx) return NLS_E_ARG;
+  return nls::guess_set_smoothing(ctx->c, sweeps, omega);
+}
+
 int nls_guess_counts(nls_ctx* ctx, int64_t* proposed, int64_t* accepted) {
   if (!ctx) return NLS_E_ARG;
   return nls::guess_counts(ctx->c, proposed, accepted);

@@ -21,10 +21,14 @@ struct CudaFailure : std::runtime_error {
     if (e_ != cudaSuccess) throw ::nls::CudaFailure(std::string(#call) + ": " + cudaGetErrorString(e_)); \
   } while (0)
 
-#define LAUNCH(D, kernel, grid, block, smem, ...)                          \
+#define LAUNCH(D, kernel, grid, block, smem, ...) LAUNCH_NAMED(D, #kernel, kernel, grid, block, smem, __VA_ARGS__)
+
+// The same with the profiling name given as a static string (for kernels launched through a
+// template whose stringified name would show the template parameters' names).
+#define LAUNCH_NAMED(D, name, kernel, grid, block, smem, ...)             \
   do {                                                                     \
     const bool prof_ = (D).prof;                                           \
-    if (prof_) (D).prof_begin(#kernel);                                    \
+    if (prof_) (D).prof_begin(name);                                       \
     kernel<<<(grid), (block), (smem), (D).s>>>(__VA_ARGS__);               \
     if (prof_) (D).prof_end();                                             \
     (D).launches += 1;                                                     \

@@ -315,15 +315,24 @@ __device__ inline void stage_row_async(int row, int n, int W, const FT* F, FT* d
 
 constexpr int kLuPrefetch = 8;
 
-// Thread mapping of one elimination step: warp w updates rows k+1+ri with ri = w, w + NW, ...;
-// lane l updates columns k+1+cj with cj = l, l + 32, ... (CJ slots, b <= 32 CJ).  Each thread
-// loads its pivot-row values once per step and its multiplier once per row, so the inner
-// work is one shared load, one FMA and one shared store per matrix entry.
-template <typename FT, int CJ>
-__device__ int band_lu_inplace_cj(int n, int b, FT* __restrict__ F, FT* win, FT* rp, int* flag) {
-  constexpr int PD = kLuPrefetch;
+// Thread mapping of one elimination step (2D tiling): the CTA is TY x 8 threads, thread
+// (ty, tx) updates rows k+1+ri with ri = ty, ty + TY, ... and columns k+1+cj with
+// cj = tx, tx + 8, ..., tx + 8 (QM - 1) (b <= 8 QM).  Every thread loads its QM pivot-row
+// values once per step and one multiplier per row, so the per-row overhead is shared by QM
+// entries and at most 7 column slots per row are idle.  Every thread forms 1 / pivot itself
+// after the step's barrier (no single-thread step on the critical path); thread 0 records it
+// in rp (per ring slot) for the write-back of the L part and flags a bad pivot.
+template <typename FT>
+__device__ inline FT recip(FT p) {
+  if constexpr (sizeof(FT) == 4) return __frcp_rn(p);
+  else return (FT)1 / p;
+}
+
+template <typename FT, int QM>
+__device__ int band_lu_inplace_q(int n, int b, FT* __restrict__ F, FT* win, FT* rp, int* flag) {
+  constexpr int PD = kLuPrefetch, TX = 8;
   const int W = 2 * b + 1, R = b + 2 + PD;
-  const int tid = threadIdx.x, T = blockDim.x, lane = tid & 31, wid = tid >> 5, NW = T >> 5;
+  const int tid = threadIdx.x, T = blockDim.x, tx = tid % TX, ty = tid / TX, TY = T / TX;
   if (tid == 0) *flag = 0;
   // stage rows 0 .. b + PD (one copy group per row and thread)
   for (int i = 0; i <= b + PD; ++i) {
@@ -333,16 +342,15 @@ __device__ int band_lu_inplace_cj(int n, int b, FT* __restrict__ F, FT* win, FT*
   }
   cp_async_wait<PD>();
   __syncthreads();
-  if (tid == 0) {
-    const FT p = win[b];
-    if (!(p != (FT)0) || !isfinite((double)p)) *flag = 1;
-    rp[0] = (FT)1 / p;
-  }
-  __syncthreads();
   int sk = 0, s1 = 1;  // ring slots of rows k and k + 1 (R >= b + 2 >= 2)
   for (int k = 0; k < n; ++k) {
     const FT* rowk = win + sk * W;
-    const FT rpk = rp[sk];
+    const FT piv = rowk[b];
+    const FT rpk = recip<FT>(piv);
+    if (tid == 0) {
+      if (!(piv != (FT)0) || !isfinite((double)piv)) *flag = 1;
+      rp[sk] = rpk;
+    }
     const int lim = min(b, n - 1 - k);
     // row k is final: write it back in place (scaled L part, reciprocal pivot, U part)
     for (int d = tid; d < W; d += T) {
@@ -364,47 +372,20 @@ __device__ int band_lu_inplace_cj(int n, int b, FT* __restrict__ F, FT* win, FT*
         for (int d = tid; d < W; d += T) cp_async_elem<FT>(win + ss * W + d, F + (int64_t)rs * W + d);
       cp_async_commit();
     }
-    // rank-1 update of rows k+1..k+lim, columns k+1..k+lim: warp w takes rows w, w+NW, ...,
-    // lane l takes columns l, l+32, ...; one shared load, FMA and store per entry
-    FT u[CJ];
+    // rank-1 update of rows k+1..k+lim, columns k+1..k+lim
+    FT u[QM];
 #pragma unroll
-    for (int c = 0; c < CJ; ++c) u[c] = (lane + 32 * c < lim) ? rowk[b + 1 + lane + 32 * c] : (FT)0;
-    // rows in groups of four: all loads of a group are issued before its FMAs and stores, so
-    // the shared-memory latency of four rows overlaps (rows of one step never alias)
-    for (int q0 = wid; q0 < lim; q0 += 4 * NW) {
-      FT lv[4], val[4][CJ];
-      FT* rowp[4];
+    for (int q = 0; q < QM; ++q) u[q] = (tx + TX * q < lim) ? rowk[b + 1 + tx + TX * q] : (FT)0;
+    for (int ri = ty; ri < lim; ri += TY) {
+      int slot = s1 + ri;
+      if (slot >= R) slot -= R;
+      FT* rowi = win + slot * W + b - ri;
+      const FT l = rowi[-1] * rpk;
 #pragma unroll
-      for (int g = 0; g < 4; ++g) {
-        const int ri = q0 + g * NW;
-        int slot = s1 + ri;
-        if (slot >= R) slot -= R;
-        rowp[g] = win + slot * W + b - ri;
-        const bool in = ri < lim;
-        lv[g] = in ? rowp[g][-1] : (FT)0;
-#pragma unroll
-        for (int c = 0; c < CJ; ++c) val[g][c] = (in && lane + 32 * c < lim) ? rowp[g][lane + 32 * c] : (FT)0;
+      for (int q = 0; q < QM; ++q) {
+        const int cj = tx + TX * q;
+        if (cj < lim) rowi[cj] -= l * u[q];
       }
-#pragma unroll
-      for (int g = 0; g < 4; ++g) {
-        const FT l = lv[g] * rpk;
-#pragma unroll
-        for (int c = 0; c < CJ; ++c) val[g][c] -= l * u[c];
-      }
-#pragma unroll
-      for (int g = 0; g < 4; ++g) {
-        if (q0 + g * NW < lim) {
-#pragma unroll
-          for (int c = 0; c < CJ; ++c)
-            if (lane + 32 * c < lim) rowp[g][lane + 32 * c] = val[g][c];
-        }
-      }
-    }
-    // thread 0 updated the new pivot A[k+1][k+1] itself (row 0, column 0 of the update)
-    if (tid == 0 && k + 1 < n) {
-      const FT nv = win[s1 * W + b];
-      if (!(nv != (FT)0) || !isfinite((double)nv)) *flag = 1;
-      rp[s1] = (FT)1 / nv;
     }
     // rows up to k + b + 1 must have landed before step k + 1
     cp_async_wait<PD>();
@@ -417,14 +398,20 @@ __device__ int band_lu_inplace_cj(int n, int b, FT* __restrict__ F, FT* win, FT*
   return *flag;
 }
 
-// Dispatch on the number of column slots per lane (half bandwidth up to 128).
+// Rows of the shared-memory window of the band LU (each 2b + 1 entries): the b + 2 rows an
+// elimination step touches plus the rows staged ahead.
+__host__ __device__ constexpr int band_lu_window_rows(int b) { return b + 2 + kLuPrefetch; }
+
+// Dispatch on the number of column slots per thread (half bandwidth up to 128).  blockDim.x
+// must be a multiple of 8.
 template <typename FT>
 __device__ int band_lu_inplace(int n, int b, FT* __restrict__ F, FT* win, FT* rp, int* flag) {
   if (n <= 0) return 0;
-  if (b <= 32) return band_lu_inplace_cj<FT, 1>(n, b, F, win, rp, flag);
-  if (b <= 64) return band_lu_inplace_cj<FT, 2>(n, b, F, win, rp, flag);
-  if (b <= 96) return band_lu_inplace_cj<FT, 3>(n, b, F, win, rp, flag);
-  return band_lu_inplace_cj<FT, 4>(n, b, F, win, rp, flag);
+  if (b <= 32) return band_lu_inplace_q<FT, 4>(n, b, F, win, rp, flag);
+  if (b <= 48) return band_lu_inplace_q<FT, 6>(n, b, F, win, rp, flag);
+  if (b <= 64) return band_lu_inplace_q<FT, 8>(n, b, F, win, rp, flag);
+  if (b <= 96) return band_lu_inplace_q<FT, 12>(n, b, F, win, rp, flag);
+  return band_lu_inplace_q<FT, 16>(n, b, F, win, rp, flag);
 }
 
 // ------------------------------------------------------------------------------------------

@@ -83,6 +83,9 @@ struct GuessCtx {
   double* guess = nullptr; // proposed local states (total local unknowns)
   int32_t* accepted = nullptr;
   double* fcell_dev = nullptr;
+  double* diag = nullptr;  // per local unknown: sum_e k_e |grad phi_a|^2 |e| (Jacobi smoothing)
+  int sweeps = 6;
+  double omega = 0.8;
   int64_t proposed_total = 0, accepted_total = 0;
   std::vector<void*> allocs;
   template <typename T>
@@ -566,6 +569,7 @@ void build_geometry(Context& c, GuessCtx& G) {
       fel(nsub);
   std::vector<float> sw((size_t)nsub * 4 * kSide), box(2 * (size_t)nsub);
   std::vector<float2> st(s.total_n);
+  std::vector<double> diag(s.total_n, 0.0);
   std::vector<int4> cidx((size_t)nsub * kNO);
   std::vector<float2> cw((size_t)nsub * kNO);
   for (int sb = 0; sb < nsub; ++sb) {
@@ -617,7 +621,18 @@ void build_geometry(Context& c, GuessCtx& G) {
       const int ci = std::min((i0 + i1) / 2, nn - 1), cj = std::min((j0 + j1) / 2, nn - 1);
       fel[sb] = 2 * (cj * nn + ci);
     }
+    // leading-term Jacobian diagonal of the local unknowns (the element's k, |grad phi_a|^2, area)
+    for (int e = 0; e < m.ne; ++e) {
+      const int64_t ge = s.elem_gid[m.elem_off + e];
+      const double* g = &c.geom[ge * c.geom_stride];
+      const double ke = c.k_elem.empty() ? 1.0 : c.k_elem[ge];
+      for (int a = 0; a < 3; ++a) {
+        const int t = s.lconn[(m.elem_off + e) * 3 + a];
+        if (t < m.n) diag[m.vec_off + t] += ke * g[6] * (g[2 * a] * g[2 * a] + g[2 * a + 1] * g[2 * a + 1]);
+      }
+    }
     for (int a = 0; a < m.n; ++a) {
+      if (!(diag[m.vec_off + a] > 0.0)) throw std::runtime_error("learned guess: zero Jacobi diagonal");
       const int32_t v = s.tnode_gid[m.tnode_off + a];
       st[m.vec_off + a] = make_float2((float)((gi[v] - i0) / (double)(i1 - i0)), (float)((gj[v] - j0) / (double)(j1 - j0)));
     }
@@ -644,6 +659,7 @@ void build_geometry(Context& c, GuessCtx& G) {
   G.st = G.upload(D, st);
   G.cidx = G.upload(D, cidx);
   G.cw = G.upload(D, cw);
+  G.diag = G.upload(D, diag);
   G.raw = G.alloc<float>((size_t)nsub * kNF);
   G.xin = G.alloc<float>((size_t)nsub * kNF);
   G.side = G.alloc<double>((size_t)nsub * 4 * kSide);
@@ -683,11 +699,11 @@ GeoArgs geo_args(Context& c, GuessCtx& G, const double* x, double load) {
 // ------------------------------------------------------------------------------------------
 // hooks used by the solver
 // ------------------------------------------------------------------------------------------
-const double* guess_propose(Context& c, const double* x, double load, int32_t** accepted) {
+GuessProposal guess_propose(Context& c, const double* x, double load) {
   Dev& D = *c.dev;
   GuessCtx* G = (GuessCtx*)D.guess;
-  *accepted = nullptr;
-  if (!G || !(G->mode & NLS_GUESS_USE) || !G->net) return nullptr;
+  GuessProposal out;
+  if (!G || !(G->mode & NLS_GUESS_USE) || !G->net) return out;
   GuessNet& N = *G->net;
   N.ensure_batch(G->nsub);
   GeoArgs a = geo_args(c, *G, x, load);
@@ -697,9 +713,28 @@ const double* guess_propose(Context& c, const double* x, double load, int32_t** 
   D.launches += 6;
   LAUNCH(D, k_guess_decode, G->nsub, 128, 0, a, G->nsub, N.Y, N.tscale, G->guess);
   CK(cudaMemsetAsync(G->accepted, 0, sizeof(int32_t) * G->nsub, D.s));
-  *accepted = G->accepted;
   G->proposed_total += G->nsub;
-  return G->guess;
+  out.x = G->guess;
+  out.accepted = G->accepted;
+  out.diag = G->diag;
+  out.sweeps = G->sweeps;
+  out.omega = G->omega;
+  return out;
+}
+
+int guess_set_smoothing(Context& c, int32_t sweeps, double omega) {
+  GuessCtx* G = c.dev ? (GuessCtx*)c.dev->guess : nullptr;
+  if (!G) {
+    c.last_error = "nls_guess_set_smoothing needs an attached network";
+    return NLS_E_ARG;
+  }
+  if (sweeps < 0 || sweeps > 64 || !(omega > 0.0 && omega <= 1.0)) {
+    c.last_error = "smoothing needs sweeps in [0, 64] and omega in (0, 1]";
+    return NLS_E_ARG;
+  }
+  G->sweeps = sweeps;
+  G->omega = omega;
+  return NLS_OK;
 }
 
 void guess_after_local(Context& c, const double* x, double load, bool proposed) {

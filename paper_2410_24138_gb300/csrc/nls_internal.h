@@ -147,7 +147,16 @@ int local_corrections_noalloc(Context& c, const double* x, double* Fx, int32_t* 
 // guess.cu
 int guess_attach(Context& c, nls_guess_net* net, int32_t mode);
 int guess_counts(Context& c, int64_t* proposed, int64_t* accepted);
-const double* guess_propose(Context& c, const double* x, double load, int32_t** accepted);
+// Proposed local starts of one batched local Newton launch (x null: no proposal).
+struct GuessProposal {
+  const double* x = nullptr;     // concatenated local states
+  int32_t* accepted = nullptr;   // per subdomain: 1 if the start was taken
+  const double* diag = nullptr;  // per local unknown: sum_e k_e |grad phi_a|^2 |e|
+  int sweeps = 0;
+  double omega = 0.8;
+};
+GuessProposal guess_propose(Context& c, const double* x, double load);
+int guess_set_smoothing(Context& c, int32_t sweeps, double omega);
 void guess_after_local(Context& c, const double* x, double load, bool proposed);
 void guess_free(Context& c);
 

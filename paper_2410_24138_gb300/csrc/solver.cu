@@ -67,6 +67,9 @@ struct LocalArgs {
   const double* x;        // evaluation point (global)
   double* out;            // F_x: owned entries receive x - w
   const double* guess;    // optional start states (concatenated local vectors)
+  const double* guess_diag;  // Jacobi diagonal (leading term) of the smoothing of the start
+  int guess_sweeps;
+  double guess_omega;
   int want_tangent;
   int32_t* accepted;          // per subdomain: 1 where the proposed start was taken
   unsigned long long* phase;  // optional per-phase clock counters (profiling), see kPhaseNames
@@ -100,12 +103,12 @@ __host__ __device__ inline SmemPlan smem_plan(int max_n, int max_nt, int max_b, 
   p.red = o; o += sizeof(double) * 40;
   p.yv = o; o += align_up(sizeof(FT) * max_n, 16);
   {
-    const size_t lu = (size_t)(max_b + 2 + dev::kLuPrefetch) * (2 * max_b + 1);
+    const size_t lu = (size_t)dev::band_lu_window_rows(max_b) * (2 * max_b + 1);
     const size_t inv = 2 * (size_t)dev::SolveBlock<FT>::BS * (dev::SolveBlock<FT>::BS + 1);
     p.win = o;
     o += with_window ? align_up(sizeof(FT) * (lu > inv ? lu : inv), 16) : 0;
   }
-  p.rp = o; o += with_window ? align_up(sizeof(FT) * (max_b + 2 + dev::kLuPrefetch), 16) : 0;
+  p.rp = o; o += with_window ? align_up(sizeof(FT) * dev::band_lu_window_rows(max_b), 16) : 0;
   p.flag = o; o += 16;
   p.total = o;
   return p;
@@ -351,7 +354,16 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 128 ? 3 : 1)) k_local_newton(Lo
         xt[a] = A.guess[m.vec_off + a];
       }
       __syncthreads();
-      const bool okg = local_residual<LAW>(A, m, xt, rt);
+      bool okg = local_residual<LAW>(A, m, xt, rt);
+      // damped Jacobi on the local problem removes the pointwise part of the proposal's error
+      for (int sw = 0; sw < A.guess_sweeps && okg; ++sw) {
+        for (int a = tid; a < n; a += blockDim.x) {
+          const double q = (LAW == NLS_LAW_DIFFUSION) ? 1.0 + xt[a] * xt[a] : 1.0;
+          xt[a] -= A.guess_omega * rt[a] / (A.guess_diag[m.vec_off + a] * q);
+        }
+        __syncthreads();
+        okg = local_residual<LAW>(A, m, xt, rt);
+      }
       double lg = 0.0;
       for (int a = tid; a < n; a += blockDim.x) lg += rt[a] * rt[a];
       double rng = sqrt(dev::block_sum(lg, red));
@@ -593,7 +605,7 @@ template <typename FT>
 __global__ void __launch_bounds__(1024) k_coarse_factor(int N0, int b0, const double* A0, FT* F, FT* Dinv, int* status) {
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int BS = dev::SolveBlock<FT>::BS;
-  const size_t R = (size_t)b0 + 2 + dev::kLuPrefetch;
+  const size_t R = (size_t)dev::band_lu_window_rows(b0);
   FT* win = (FT*)smem;
   FT* rp = win + R * (2 * b0 + 1);
   FT* tmp = rp + R;
@@ -602,7 +614,9 @@ __global__ void __launch_bounds__(1024) k_coarse_factor(int N0, int b0, const do
   for (int64_t k = threadIdx.x; k < total; k += blockDim.x) F[k] = (FT)A0[k];
   __syncthreads();
   const int bad = dev::band_lu_inplace<FT>(N0, b0, F, win, rp, flag);
-  if (!bad) dev::band_pack_solve<FT>(N0, b0, F, Dinv, tmp, 4);
+  // the LU window is free again: it holds the packing scratch of up to every warp
+  const int pw = min((int)(blockDim.x >> 5), (int)((R * (2 * b0 + 1)) / (BS * (BS + 1))));
+  if (!bad) dev::band_pack_solve<FT>(N0, b0, F, Dinv, pw >= 4 ? win : tmp, pw >= 4 ? pw : 4);
   if (threadIdx.x == 0) *status = bad ? ST_PIVOT : ST_OK;
 }
 
@@ -1028,12 +1042,21 @@ size_t local_newton_smem(const LocalSet& s) {
 
 // Persistent grid: as many CTAs as fit on the device at once (registers and shared memory), at
 // most one per subdomain; the work counter hands out the subdomains.
+const char* newton_kernel_name(int law, bool f32, int maxt) {
+  static const char* names[8] = {
+      "k_local_newton<diffusion, double, 128>", "k_local_newton<diffusion, float, 128>",
+      "k_local_newton<diffusion, double, 256>", "k_local_newton<diffusion, float, 256>",
+      "k_local_newton<neohooke, double, 128>",  "k_local_newton<neohooke, float, 128>",
+      "k_local_newton<neohooke, double, 256>",  "k_local_newton<neohooke, float, 256>"};
+  return names[(law == NLS_LAW_DIFFUSION ? 0 : 4) + (maxt > 128 ? 2 : 0) + (f32 ? 1 : 0)];
+}
+
 template <int LAW, typename FT, int MAXT>
 void launch_newton_t(Dev& D, int count, int T, size_t sm, const LocalArgs& A) {
   int occ = 0;
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_local_newton<LAW, FT, MAXT>, T, sm));
   const int grid = std::min(count, D.nsm * std::max(1, occ));
-  LAUNCH(D, (k_local_newton<LAW, FT, MAXT>), grid, T, sm, A);
+  LAUNCH_NAMED(D, newton_kernel_name(LAW, sizeof(FT) == 4, MAXT), (k_local_newton<LAW, FT, MAXT>), grid, T, sm, A);
 }
 
 template <int LAW, typename FT>
@@ -1055,15 +1078,18 @@ void dispatch_local_newton(Context& c, const LocalSet& s, const LocalArgs& A, in
   }
 }
 
-void launch_local_newton(Context& c, const double* x, double* out, double load, const double* guess, bool want_tangent,
-                         int32_t* accepted = nullptr) {
+void launch_local_newton(Context& c, const double* x, double* out, double load, const GuessProposal& g,
+                         bool want_tangent) {
   Dev& D = *c.dev;
   LocalArgs A = make_args(c, c.ov, D.ov);
   A.x = x;
   A.out = out;
   A.load = load;
-  A.guess = guess;
-  A.accepted = accepted;
+  A.guess = g.x;
+  A.accepted = g.accepted;
+  A.guess_diag = g.diag;
+  A.guess_sweeps = g.x ? g.sweeps : 0;
+  A.guess_omega = g.omega;
   A.want_tangent = want_tangent ? 1 : 0;
   A.phase = D.prof ? D.phase : nullptr;
   CK(cudaMemsetAsync(D.ov.queue, 0, sizeof(int32_t), D.s));
@@ -1108,19 +1134,19 @@ float time_on_stream(Dev& D, F&& f) {
   return ms;
 }
 
-void tune_local_newton(Context& c, const double* x, double* out, double load, const double* guess, int32_t* accepted) {
+void tune_local_newton(Context& c, const double* x, double* out, double load, const GuessProposal& guess) {
   Dev& D = *c.dev;
   if (D.newton_tuned || !c.opt.autotune || c.opt.threads_per_block) return;
   const int need = min_local_threads(c);
   const int cand[2] = {128, 256};
   // warm-up with the fixed choice (first touch of the factor storage and the caches)
-  launch_local_newton(c, x, out, load, guess, true, accepted);
+  launch_local_newton(c, x, out, load, guess, true);
   double best = INFINITY;
   int bestT = 0;
   for (int i = 0; i < 2; ++i) {
     if (cand[i] < need) continue;
     D.newton_T = cand[i];
-    const float ms = time_on_stream(D, [&] { launch_local_newton(c, x, out, load, guess, true, accepted); });
+    const float ms = time_on_stream(D, [&] { launch_local_newton(c, x, out, load, guess, true); });
     D.newton_ms[i] = ms;
     if (ms < best) {
       best = ms;
@@ -1172,7 +1198,7 @@ LocalArgs coarse_args(Context& c) {
 size_t coarse_factor_smem(const Context& c, bool f32) {
   const size_t fs = f32 ? sizeof(float) : sizeof(double);
   const size_t BS = f32 ? dev::SolveBlock<float>::BS : dev::SolveBlock<double>::BS;
-  const size_t R = (size_t)c.cs.b0 + 2 + dev::kLuPrefetch;
+  const size_t R = (size_t)dev::band_lu_window_rows(c.cs.b0);
   return fs * (R * (2 * c.cs.b0 + 1) + R + 4 * BS * (BS + 1)) + 16;
 }
 
@@ -1536,11 +1562,10 @@ FxInfo evaluate_Fx(Context& c, const double* u, double load, double* t_inner, do
   }
   sync(D);
   auto t1 = std::chrono::steady_clock::now();
-  int32_t* accepted = nullptr;
-  const double* proposal = guess_propose(c, point, load, &accepted);
-  tune_local_newton(c, point, D.Fx, load, proposal, accepted);
-  launch_local_newton(c, point, D.Fx, load, proposal, true, accepted);
-  guess_after_local(c, point, load, proposal != nullptr);
+  const GuessProposal proposal = guess_propose(c, point, load);
+  tune_local_newton(c, point, D.Fx, load, proposal);
+  launch_local_newton(c, point, D.Fx, load, proposal, true);
+  guess_after_local(c, point, load, proposal.x != nullptr);
   std::vector<int32_t> its(c.ov.count), st(c.ov.count);
   CK(cudaMemcpyAsync(its.data(), D.ov.its, sizeof(int32_t) * its.size(), cudaMemcpyDeviceToHost, D.s));
   CK(cudaMemcpyAsync(st.data(), D.ov.status, sizeof(int32_t) * st.size(), cudaMemcpyDeviceToHost, D.s));

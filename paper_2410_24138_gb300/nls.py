@@ -88,7 +88,7 @@ EXPORTS = ["nls_options_default", "nls_create", "nls_destroy", "nls_strerror", "
            "nls_reset_kernel_stats", "nls_local_corrections_noalloc", "nls_guess_create", "nls_guess_destroy",
            "nls_guess_attach", "nls_guess_train", "nls_guess_pairs", "nls_guess_get_params", "nls_guess_set_params",
            "nls_guess_get_normalisation", "nls_guess_set_normalisation", "nls_guess_gradient", "nls_guess_forward",
-           "nls_guess_counts", "nls_get_tuning"]
+           "nls_guess_counts", "nls_get_tuning", "nls_guess_set_smoothing"]
 
 _LIB = None
 _P = ctypes.c_void_p
@@ -151,6 +151,7 @@ def load() -> ctypes.CDLL:
         "nls_guess_gradient": (ctypes.c_int, [_P, i32, _P, _P, i32, _P, ctypes.POINTER(ctypes.c_float)]),
         "nls_guess_forward": (ctypes.c_int, [_P, i32, _P, _P]),
         "nls_guess_counts": (ctypes.c_int, [_P, ctypes.POINTER(i64), ctypes.POINTER(i64)]),
+        "nls_guess_set_smoothing": (ctypes.c_int, [_P, i32, ctypes.c_double]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -453,6 +454,10 @@ class GuessNet:
 
 def attach_guess(solver: "Solver", net: "GuessNet", mode: int):
     solver._check(solver.lib.nls_guess_attach(solver.h, net.h if net else None, mode), "nls_guess_attach")
+
+
+def set_guess_smoothing(solver: "Solver", sweeps: int, omega: float = 0.8):
+    solver._check(solver.lib.nls_guess_set_smoothing(solver.h, sweeps, omega), "nls_guess_set_smoothing")
 
 
 def guess_counts(solver: "Solver"):

@@ -57,13 +57,17 @@ def test_inference_matches_reference(nls):
     assert np.linalg.norm(Y - Yr) <= 1e-5 * np.linalg.norm(Yr)
 
 
-def _small_c4(seed, n=96, per=3):
-    """The log-normal-coefficient diffusion family at 96x96 cells on 3x3 brick subdomains."""
-    return I.diffusion_c4(seed, n=n, per_side=per)
+def _c4_family(seed, n=128, per=4, fscale=1.0):
+    """The log-normal-coefficient diffusion family (Eq. 1 with k(x), f) at n x n cells on per x per
+    brick subdomains (about 32 x 32 cells each, as in the 512 x 512 workload), f scaled by fscale."""
+    g = I.gaussian_random_field(n, seed, ell=1.0 / 16.0, sigma=1.0)
+    f = fscale * (0.5 + 1.5 * I.uniform01(I.splitmix64(seed ^ 0x5DEECE66D), 1)[0])
+    return I.diffusion_problem(n, I.brick_partition(n, per, per, I.PARTITION_SEED), per * per, 2,
+                               k_cell=np.exp(g), f_cell=np.full(n * n, f))
 
 
 def test_garbage_network_does_not_change_the_solution(nls):
-    p = _small_c4(1001)
+    p = _c4_family(1001, n=96, per=3)
     ref = nls.make_solver(p, coupling="hybrid")
     u_ref, rep_ref = ref.solve()
     s = nls.make_solver(p, coupling="hybrid")
@@ -80,30 +84,47 @@ def test_garbage_network_does_not_change_the_solution(nls):
     assert np.linalg.norm(u - u_ref) <= 1e-6 * np.linalg.norm(u_ref)
 
 
-def test_harvest_train_and_gain(nls):
-    net = nls.GuessNet(h1=128, h2=128, seed=11, capacity=4000)
-    for seed in range(1, 13):
-        s = nls.make_solver(_small_c4(seed), coupling="hybrid")
+def _train(nls, seeds, fscale):
+    net = nls.GuessNet(h1=256, h2=256, seed=11, capacity=20000)
+    for seed in seeds:
+        s = nls.make_solver(_c4_family(seed, fscale=fscale), coupling="hybrid")
         nls.attach_guess(s, net, nls.GUESS_HARVEST)
         _, rep = s.solve()
         assert rep.status == 0
         s.close()
-    assert net.pairs() > 100
-    losses = net.train(steps=600, batch=64, lr=2e-3, seed=5)
+    losses = net.train(steps=2000, batch=128, lr=1e-3, seed=5)
     assert np.all(np.isfinite(losses))
-    assert losses[-50:].mean() < 0.5 * losses[:50].mean()
-    steps_plain, steps_guess, acc = 0, 0, 0
-    for seed in (1001, 1002, 1003):
-        p = _small_c4(seed)
+    assert losses[-50:].mean() < 0.1 * losses[:50].mean()
+    return net
+
+
+def _steps(nls, net, seeds, fscale):
+    plain, guess, acc = 0, 0, 0
+    for seed in seeds:
+        p = _c4_family(seed, fscale=fscale)
         a = nls.make_solver(p, coupling="hybrid")
-        _, ra = a.solve()
+        ua, ra = a.solve()
         b = nls.make_solver(p, coupling="hybrid")
         nls.attach_guess(b, net, nls.GUESS_USE)
         ub, rb = b.solve()
-        _, accepted = nls.guess_counts(b)
-        acc += accepted
+        acc += nls.guess_counts(b)[1]
         assert rb.status == 0 and rb.final_residual < 1e-8
-        steps_plain += ra.subdomain_newton_steps
-        steps_guess += rb.subdomain_newton_steps
+        assert np.linalg.norm(ub - ua) <= 1e-6 * np.linalg.norm(ua)
+        plain += ra.subdomain_newton_steps
+        guess += rb.subdomain_newton_steps
+    return plain, guess, acc
+
+
+def test_trained_guess_gains_local_newton_steps(nls):
+    """Harvest -> train -> use on held-out coefficient fields.  With f in [0.5, 2] the local
+    problems are nearly linear (u ~ 1e-2, so (1 + u^2) ~ 1) and local Newton needs one or two
+    steps from any start; scaling f by 50 makes them strongly nonlinear (u ~ 0.5), the regime
+    where a starting point can save steps.  Both are checked: no loss in the first, a strict
+    gain in the second, the converged solutions unchanged within the FP32-path bound."""
+    net = _train(nls, range(1, 25), 50.0)
+    plain, guess, acc = _steps(nls, net, (1001, 1002, 1003), 50.0)
     assert acc > 0
-    assert steps_guess <= steps_plain
+    assert guess < plain
+    net1 = _train(nls, range(1, 25), 1.0)
+    plain1, guess1, _ = _steps(nls, net1, (1001, 1002), 1.0)
+    assert guess1 <= plain1
