@@ -311,7 +311,8 @@ int nls_guess_set_smoothing(nls_ctx* ctx, int32_t sweeps, double omega);
  * corrections: code being recorded into a CUDA graph (no cudaMalloc during stream capture),
  * applications whose own memory manager owns the GPU, and loops that must not risk the
  * implicit synchronisation of cudaMalloc / cudaFree.  The kernel's scratch (local Jacobians,
- * band factors, local states, work counter) lives in a 32 MiB device array compiled into the
+ * band factors, packed solve operands, local states, work vectors, work counter) lives in a
+ * 32 MiB device array compiled into the
  * library, which every GPU that loads the library keeps until the process exits.
  *   x   [n_dofs] device input (the point, Dirichlet entries holding the Dirichlet values);
  *   Fx  [n_dofs] device output; every entry is written (Dirichlet entries with 0);

@@ -627,8 +627,10 @@ __device__ void band_pack_solve(int n, int b, const FT* __restrict__ F, FT* __re
 
 // Triangular solves with the packed operands, in place on y[0..n) (shared memory): warp 0
 // applies the block inverse (lane r: row r of inv(L_tt) or inv(U_tt) dotted with the block of
-// y), threads 32 .. 32 + b - 1 apply the coupling to the next b rows.  The operands of the next
-// block are loaded into registers while the current one is applied.  Needs blockDim.x >= 32 + b.
+// y), threads 32 .. 32 + b - 1 apply the coupling to the next b rows.  Each block's operands
+// are loaded at the top of its step (BS coalesced loads per thread, issued back to back); the
+// latency is hidden by the other CTAs on the SM rather than by a register double buffer, which
+// keeps the solve at BS operand registers per thread.  Needs blockDim.x >= 32 + b.
 template <typename FT>
 __device__ void band_solve_packed(int n, int b, const FT* __restrict__ P, FT* y) {
   constexpr int BS = SolveBlock<FT>::BS;
@@ -638,23 +640,19 @@ __device__ void band_solve_packed(int n, int b, const FT* __restrict__ P, FT* y)
   const int r = tid - 32;
   const int64_t PB = packed_block_entries<FT>(b);
   const int nblk = (n + BS - 1) / BS;
-  FT cur[BS], nxt[BS];
-  // forward: diag lanes read inv(L_tt) (offset 0), coupling threads read CL
-#define NLS_LOAD_PK(t_, R_, dofs_, cofs_)                                                   \
-  {                                                                                         \
-    const FT* Pt_ = P + (int64_t)(t_) * PB;                                                 \
-    if (diag) {                                                                             \
-      _Pragma("unroll") for (int j = 0; j < BS; ++j) R_[j] = Pt_[(dofs_) + j * BS + lane];  \
-    } else if (offd) {                                                                      \
-      _Pragma("unroll") for (int j = 0; j < BS; ++j) R_[j] = Pt_[(cofs_) + j * b + r];      \
-    }                                                                                       \
-  }
-  const int oL = 0, oU = BS * BS;
-  const int64_t oCL = 2 * BS * BS, oCU = 2 * BS * BS + (int64_t)b * BS;
-  if (n > 0) NLS_LOAD_PK(0, cur, oL, oCL);
+  const int64_t oL = 0, oU = BS * BS, oCL = 2 * BS * BS, oCU = 2 * BS * BS + (int64_t)b * BS;
+  FT cur[BS];
+  // forward: diag lanes read inv(L_tt), coupling threads read CL
   for (int t = 0; t < nblk; ++t) {
     const int k0 = t * BS, kb = min(BS, n - k0);
-    if (t + 1 < nblk) NLS_LOAD_PK(t + 1, nxt, oL, oCL);
+    const FT* Pt = P + (int64_t)t * PB;
+    if (diag) {
+#pragma unroll
+      for (int j = 0; j < BS; ++j) cur[j] = Pt[oL + j * BS + lane];
+    } else if (offd) {
+#pragma unroll
+      for (int j = 0; j < BS; ++j) cur[j] = Pt[oCL + j * b + r];
+    }
     if (wid == 0) {  // the whole warp reaches __syncwarp; only lanes < BS hold a block row
       FT a0 = 0, a1 = 0;
       if (diag) {
@@ -681,14 +679,18 @@ __device__ void band_solve_packed(int n, int b, const FT* __restrict__ P, FT* y)
       }
     }
     __syncthreads();
-#pragma unroll
-    for (int j = 0; j < BS; ++j) cur[j] = nxt[j];
   }
   // backward: diag lanes read inv(U_tt), coupling threads read CU
-  if (n > 0) NLS_LOAD_PK(nblk - 1, cur, oU, oCU);
   for (int t = nblk - 1; t >= 0; --t) {
     const int k0 = t * BS, kb = min(BS, n - k0);
-    if (t > 0) NLS_LOAD_PK(t - 1, nxt, oU, oCU);
+    const FT* Pt = P + (int64_t)t * PB;
+    if (diag) {
+#pragma unroll
+      for (int j = 0; j < BS; ++j) cur[j] = Pt[oU + j * BS + lane];
+    } else if (offd) {
+#pragma unroll
+      for (int j = 0; j < BS; ++j) cur[j] = Pt[oCU + j * b + r];
+    }
     if (wid == 0) {
       FT a0 = 0, a1 = 0;
       if (diag) {
@@ -715,10 +717,7 @@ __device__ void band_solve_packed(int n, int b, const FT* __restrict__ P, FT* y)
       }
     }
     __syncthreads();
-#pragma unroll
-    for (int j = 0; j < BS; ++j) cur[j] = nxt[j];
   }
-#undef NLS_LOAD_PK
 }
 
 }  // namespace dev

@@ -56,6 +56,8 @@ struct LocalArgs {
   void* factor;
   void* dinv;  // packed triangular-solve operands (diagonal-block inverses + couplings)
   double* wbuf;
+  double* work;        // three per-subdomain FP64 vectors (vec_off), `work_stride` apart
+  int64_t work_stride;
   int32_t *its, *status;
   const int32_t* order;
   int32_t* queue;
@@ -110,6 +112,48 @@ __host__ __device__ inline SmemPlan smem_plan(int max_n, int max_nt, int max_b, 
   }
   p.rp = o; o += with_window ? align_up(sizeof(FT) * dev::band_lu_window_rows(max_b), 16) : 0;
   p.flag = o; o += 16;
+  p.total = o;
+  return p;
+}
+
+// Shared memory of the batched local kernels.  Only what the inner loops hit per entry stays in
+// shared memory -- the table state (gathered by every element), the residual being assembled,
+// the band-LU window and the solve vector (which lives in the window once the factors are
+// packed); the current residual, the Newton step and the refinement residual are per-subdomain
+// vectors in global memory (read and written O(n) times per phase, coalesced).
+struct LocalPlan {
+  size_t xt, racc, red, win, rp, flag, total;
+};
+
+template <typename FT>
+__host__ __device__ inline LocalPlan newton_plan(int max_n, int max_nt, int max_b) {
+  LocalPlan p;
+  size_t o = 0;
+  p.xt = o; o += sizeof(double) * max_nt;
+  p.racc = o; o += sizeof(double) * max_n;
+  p.red = o; o += sizeof(double) * 40;
+  {
+    const size_t lu = (size_t)dev::band_lu_window_rows(max_b) * (2 * max_b + 1);
+    const size_t inv = 4 * (size_t)dev::SolveBlock<FT>::BS * (dev::SolveBlock<FT>::BS + 1);
+    size_t w = lu > inv ? lu : inv;
+    w = w > (size_t)max_n ? w : (size_t)max_n;
+    p.win = o; o += align_up(sizeof(FT) * w, 16);
+  }
+  p.rp = o; o += align_up(sizeof(FT) * dev::band_lu_window_rows(max_b), 16);
+  p.flag = o; o += 16;
+  p.total = o;
+  return p;
+}
+
+template <typename FT>
+__host__ __device__ inline LocalPlan apply_plan(int max_n, int max_nt) {
+  LocalPlan p;
+  size_t o = 0;
+  p.xt = o; o += sizeof(double) * max_nt;
+  p.racc = 0;
+  p.red = o; o += sizeof(double) * 40;
+  p.win = o; o += align_up(sizeof(FT) * max_n, 16);
+  p.rp = p.flag = o;
   p.total = o;
   return p;
 }
@@ -254,7 +298,7 @@ __device__ void local_jacobian(const LocalArgs& A, const SubMeta& m, const doubl
 // (columns < n) when the factors are FP32.  `res` is an n-vector of scratch.
 template <typename FT>
 __device__ int local_solve(const LocalArgs& A, const SubMeta& m, const int32_t* rowptr, const int32_t* colidx,
-                           const double* csr, const FT* F, const FT* Dv, const double* rhs, double rhs_norm, double* s,
+                           const double* csr, const FT* Dv, const double* rhs, double rhs_norm, double* s,
                            double* res, FT* yv, double* red) {
   const int n = m.n;
   for (int a = threadIdx.x; a < n; a += blockDim.x) yv[a] = (FT)rhs[a];
@@ -294,24 +338,21 @@ __device__ int local_solve(const LocalArgs& A, const SubMeta& m, const int32_t* 
 // MAXT is the largest CTA the instantiation is compiled for: 128-thread CTAs keep three CTAs
 // per SM within the register file, 256-thread CTAs get the whole register budget per thread.
 template <int LAW, typename FT, int MAXT>
-__global__ void __launch_bounds__(MAXT, (MAXT <= 128 ? 3 : 1)) k_local_newton(LocalArgs A) {
+__global__ void __launch_bounds__(MAXT, (MAXT <= 128 ? 4 : 1)) k_local_newton(LocalArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const SmemPlan P = smem_plan<FT>(A.max_n, A.max_nt, A.max_b, true);
+  const LocalPlan P = newton_plan<FT>(A.max_n, A.max_nt, A.max_b);
   double* xt = (double*)(smem + P.xt);
-  double* r = (double*)(smem + P.r);
-  double* rt = (double*)(smem + P.rt);
-  double* s = (double*)(smem + P.s);
+  double* racc = (double*)(smem + P.racc);  // residual being assembled
   double* red = (double*)(smem + P.red);
-  FT* yv = (FT*)(smem + P.yv);
   FT* win = (FT*)(smem + P.win);
+  FT* yv = win;  // the solve vector lives in the LU window once the factors are packed
   FT* rp = (FT*)(smem + P.rp);
   int* flag = (int*)(smem + P.flag);
   __shared__ int s_item;
   using JT = typename std::conditional<LAW == NLS_LAW_DIFFUSION, double, FT>::type;
   const int tid = threadIdx.x, nd = A.ndof;
   constexpr int BSI = dev::SolveBlock<FT>::BS;
-  const int inv_warps = min((int)(blockDim.x >> 5),
-                            (int)((P.rp - P.win) / (sizeof(FT) * BSI * (BSI + 1))));
+  const int inv_warps = min((int)(blockDim.x >> 5), (int)((P.rp - P.win) / (sizeof(FT) * BSI * (BSI + 1))));
   long long tp = clock64();
   // thread 0 charges the cycles since the last mark to phase `id` (profiling only)
   auto mark = [&](int id) {
@@ -336,12 +377,18 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 128 ? 3 : 1)) k_local_newton(Lo
     FT* F = (FT*)A.factor + m.factor_off;
     FT* Dv = (FT*)A.dinv + m.dinv_off;
     double* wb = A.wbuf + m.vec_off;
+    double* r = A.work + m.vec_off;                            // current residual
+    double* s = A.work + A.work_stride + m.vec_off;            // Newton step
+    double* res = A.work + 2 * A.work_stride + m.vec_off;      // refinement residual
     for (int t = tid; t < m.nt; t += blockDim.x)
       xt[t] = A.x[(int64_t)A.tnode_gid[m.tnode_off + t / nd] * nd + t % nd];
     __syncthreads();
-    bool ok = local_residual<LAW>(A, m, xt, r);
+    bool ok = local_residual<LAW>(A, m, xt, racc);
     double loc = 0.0;
-    for (int a = tid; a < n; a += blockDim.x) loc += r[a] * r[a];
+    for (int a = tid; a < n; a += blockDim.x) {
+      r[a] = racc[a];
+      loc += racc[a] * racc[a];
+    }
     double rn = sqrt(dev::block_sum(loc, red));
     if (!ok) rn = INFINITY;
     // the stopping test is relative to the residual of the method's own start R_i x, with or
@@ -354,30 +401,28 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 128 ? 3 : 1)) k_local_newton(Lo
         xt[a] = A.guess[m.vec_off + a];
       }
       __syncthreads();
-      bool okg = local_residual<LAW>(A, m, xt, rt);
+      bool okg = local_residual<LAW>(A, m, xt, racc);
       // damped Jacobi on the local problem removes the pointwise part of the proposal's error
       for (int sw = 0; sw < A.guess_sweeps && okg; ++sw) {
         for (int a = tid; a < n; a += blockDim.x) {
           const double q = (LAW == NLS_LAW_DIFFUSION) ? 1.0 + xt[a] * xt[a] : 1.0;
-          xt[a] -= A.guess_omega * rt[a] / (A.guess_diag[m.vec_off + a] * q);
+          xt[a] -= A.guess_omega * racc[a] / (A.guess_diag[m.vec_off + a] * q);
         }
         __syncthreads();
-        okg = local_residual<LAW>(A, m, xt, rt);
+        okg = local_residual<LAW>(A, m, xt, racc);
       }
       double lg = 0.0;
-      for (int a = tid; a < n; a += blockDim.x) lg += rt[a] * rt[a];
+      for (int a = tid; a < n; a += blockDim.x) lg += racc[a] * racc[a];
       double rng = sqrt(dev::block_sum(lg, red));
       if (!okg) rng = INFINITY;
       const bool take = isfinite(rng) && rng < rn;
       if (take) {
-        double* tmp = r;
-        r = rt;
-        rt = tmp;
+        for (int a = tid; a < n; a += blockDim.x) r[a] = racc[a];
         rn = rng;
       } else {
         for (int a = tid; a < n; a += blockDim.x) xt[a] = wb[a];
-        __syncthreads();
       }
+      __syncthreads();
       if (tid == 0 && A.accepted) A.accepted[sub] = take ? 1 : 0;
     }
     int its = 0, status = ST_OK;
@@ -396,7 +441,7 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 128 ? 3 : 1)) k_local_newton(Lo
       }
       dev::band_pack_solve<FT>(n, m.b, F, Dv, win, inv_warps);
       mark(2);
-      local_solve<FT>(A, m, rowptr, colidx, csr, F, Dv, r, rn, s, rt, yv, red);
+      local_solve<FT>(A, m, rowptr, colidx, csr, Dv, r, rn, s, res, yv, red);
       mark(3);
       for (int a = tid; a < n; a += blockDim.x) wb[a] = xt[a];
       __syncthreads();
@@ -405,9 +450,9 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 128 ? 3 : 1)) k_local_newton(Lo
       for (int trial = 0; trial < A.ls_trials; ++trial) {
         for (int a = tid; a < n; a += blockDim.x) xt[a] = wb[a] - alpha * s[a];
         __syncthreads();
-        const bool tok = local_residual<LAW>(A, m, xt, rt);
+        const bool tok = local_residual<LAW>(A, m, xt, racc);
         double l2 = 0.0;
-        for (int a = tid; a < n; a += blockDim.x) l2 += rt[a] * rt[a];
+        for (int a = tid; a < n; a += blockDim.x) l2 += racc[a] * racc[a];
         rtn = sqrt(dev::block_sum(l2, red));
         if (!tok) rtn = INFINITY;
         if (isfinite(rtn) && rtn <= (1.0 - A.armijo * alpha) * rn) {
@@ -424,9 +469,8 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 128 ? 3 : 1)) k_local_newton(Lo
         status = ST_LS;
         break;
       }
-      double* tmp = r;
-      r = rt;
-      rt = tmp;
+      for (int a = tid; a < n; a += blockDim.x) r[a] = racc[a];
+      __syncthreads();
       rn = rtn;
     }
     if (A.want_tangent && status != ST_NONFINITE && status != ST_PIVOT) {
@@ -449,9 +493,6 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 128 ? 3 : 1)) k_local_newton(Lo
     }
     __syncthreads();
     mark(7);
-    // restore the ping-pong buffers for the next subdomain
-    r = (double*)(smem + P.r);
-    rt = (double*)(smem + P.rt);
   }
 }
 
@@ -461,21 +502,20 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 128 ? 3 : 1)) k_local_newton(Lo
 template <typename FT>
 __global__ void __launch_bounds__(512) k_local_apply(LocalArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const SmemPlan P = smem_plan<FT>(A.max_n, A.max_nt, A.max_b, false);
+  const LocalPlan P = apply_plan<FT>(A.max_n, A.max_nt);
   double* yt = (double*)(smem + P.xt);
-  double* q = (double*)(smem + P.r);
-  double* res = (double*)(smem + P.rt);
-  double* z = (double*)(smem + P.s);
   double* red = (double*)(smem + P.red);
-  FT* yv = (FT*)(smem + P.yv);
+  FT* yv = (FT*)(smem + P.win);
   const int sub = blockIdx.x, tid = threadIdx.x, nd = A.ndof;
   const SubMeta m = A.meta[sub];
   const int n = m.n;
   const int32_t* rowptr = A.rowptr + m.rowptr_off;
   const int32_t* colidx = A.colidx + m.nnz_off;
   const double* csr = A.csr + m.nnz_off;
-  const FT* F = (const FT*)A.factor + m.factor_off;
   const FT* Dv = (const FT*)A.dinv + m.dinv_off;
+  double* q = A.work + m.vec_off;
+  double* z = A.work + A.work_stride + m.vec_off;
+  double* res = A.work + 2 * A.work_stride + m.vec_off;
   for (int t = tid; t < m.nt; t += blockDim.x) yt[t] = A.v[(int64_t)A.tnode_gid[m.tnode_off + t / nd] * nd + t % nd];
   __syncthreads();
   double loc = 0.0;
@@ -486,7 +526,7 @@ __global__ void __launch_bounds__(512) k_local_apply(LocalArgs A) {
     loc += acc * acc;
   }
   const double qn = sqrt(dev::block_sum(loc, red));
-  local_solve<FT>(A, m, rowptr, colidx, csr, F, Dv, q, qn, z, res, yv, red);
+  local_solve<FT>(A, m, rowptr, colidx, csr, Dv, q, qn, z, res, yv, red);
   for (int a = tid; a < n; a += blockDim.x)
     if (A.owned[m.vec_off + a]) {
       const int64_t g = (int64_t)A.tnode_gid[m.tnode_off + a / nd] * nd + a % nd;
@@ -948,6 +988,8 @@ LocalArgs make_args(const Context& c, const LocalSet& hs, const DeviceLocalSet& 
   A.factor = ds.factor;
   A.dinv = ds.dinv;
   A.wbuf = ds.w;
+  A.work = ds.work;
+  A.work_stride = hs.total_n;
   A.its = ds.its;
   A.status = ds.status;
   A.order = ds.order;
@@ -1037,7 +1079,7 @@ void global_jacobian(Context& c, const double* x) {
 // ---- batched local kernels ---------------------------------------------------------------------
 template <typename FT>
 size_t local_newton_smem(const LocalSet& s) {
-  return smem_plan<FT>(s.max_n, s.max_nt, s.max_b, true).total;
+  return newton_plan<FT>(s.max_n, s.max_nt, s.max_b).total;
 }
 
 // Persistent grid: as many CTAs as fit on the device at once (registers and shared memory), at
@@ -1106,10 +1148,10 @@ void launch_local_apply(Context& c, const double* v, const double* add, double* 
   // subdomains be in flight on every SM, which is what hides the latency of the solves
   const int T = apply_threads(c);
   if (fp32_local(c)) {
-    const size_t sm = smem_plan<float>(c.ov.max_n, c.ov.max_nt, c.ov.max_b, false).total;
+    const size_t sm = apply_plan<float>(c.ov.max_n, c.ov.max_nt).total;
     LAUNCH(D, k_local_apply<float>, c.ov.count, T, sm, A);
   } else {
-    const size_t sm = smem_plan<double>(c.ov.max_n, c.ov.max_nt, c.ov.max_b, false).total;
+    const size_t sm = apply_plan<double>(c.ov.max_n, c.ov.max_nt).total;
     LAUNCH(D, k_local_apply<double>, c.ov.count, T, sm, A);
   }
 }
@@ -1339,6 +1381,7 @@ void upload_set(Dev& D, const LocalSet& h, DeviceLocalSet& d, bool fp32_factor, 
     if (with_dinv) d.dinv = D.alloc<double>(h.total_dinv);
   }
   d.w = D.alloc<double>(h.total_n);
+  d.work = D.alloc<double>(3 * (size_t)h.total_n);
   d.its = D.alloc<int32_t>(h.count);
   d.status = D.alloc<int32_t>(h.count);
   // longest first: cost ~ n b^2
@@ -2050,7 +2093,8 @@ int local_corrections_noalloc(Context& c, const double* x, double* Fx, int32_t* 
   Dev& D = *c.dev;
   const LocalSet& s = c.ov;
   const bool f32 = fp32_local(c);
-  // scratch plan: CSR values, band factors, local states, its, status, work counter
+  // scratch plan: CSR values, band factors, packed solve operands, local states, work vectors,
+  // its, status, work counter
   const size_t fbytes = f32 ? sizeof(float) : sizeof(double);
   size_t off = 0;
   const size_t o_csr = off;
@@ -2061,6 +2105,8 @@ int local_corrections_noalloc(Context& c, const double* x, double* Fx, int32_t* 
   off = align_up(off + fbytes * (size_t)s.total_dinv, 256);
   const size_t o_w = off;
   off = align_up(off + sizeof(double) * (size_t)s.total_n, 256);
+  const size_t o_work = off;
+  off = align_up(off + 3 * sizeof(double) * (size_t)s.total_n, 256);
   const size_t o_its = off;
   off = align_up(off + sizeof(int32_t) * (size_t)s.count, 256);
   const size_t o_st = off;
@@ -2083,6 +2129,8 @@ int local_corrections_noalloc(Context& c, const double* x, double* Fx, int32_t* 
     A.factor = sc + o_fac;
     A.dinv = sc + o_dinv;
     A.wbuf = (double*)(sc + o_w);
+    A.work = (double*)(sc + o_work);
+    A.work_stride = s.total_n;
     A.its = its_out ? its_out : (int32_t*)(sc + o_its);
     A.status = status_out ? status_out : (int32_t*)(sc + o_st);
     A.queue = (int32_t*)(sc + o_q);

@@ -9,7 +9,7 @@ Tolerances (derived in the design notes):
   1e-9 relative.  The FP32-factor path refines to the same FP64 residual -> same bound.
 * the tangent (Eqs. 6, 12): FP64 factors 1e-9; FP32 factors refined to 1e-10 -> 1e-7.
 * converged solutions: 1e-8 (FP64 path) and 1e-6 (FP32 + refinement) relative l2, the
-  bounds the benchmark spec's target states; both sides are driven to ||F|| < 1e-12 first so that
+  bounds the workload statement sets; both sides are driven to ||F|| < 1e-12 first so that
   the bound measures the method, not the stopping test.
 """
 import numpy as np
