@@ -88,12 +88,20 @@ typedef struct nls_options {
                                  captured once per Krylov index into a CUDA graph and replayed;
                                  0: plain stream launches.  Graphs are not used while
                                  profile_kernels is set.  Results are identical either way. */
+  int32_t coarse_reuse;       /* 1 (default): the coarse Newton iteration of Eq. 9 starts every
+                                 outer step after the first of an nls_solve with the
+                                 factorization (and explicit inverse) of the previous tangent
+                                 phase's A_0 -- chord steps -- and forms A_0 at
+                                 the current point only when a step contracts ||P_0^T F|| by less
+                                 than half or fails the line search; 0: a fresh A_0 every coarse
+                                 step.  The stopping test (inner_rtol, inner_atol) is the same. */
   int32_t autotune;           /* 1: on the first use, time the batched local Newton kernel with
-                                 128- and 256-thread CTAs and the tangent kernel with CTA sizes
-                                 from 32 + b to 256 on the context's own data, and keep the
+                                 128- and 256-thread CTAs, the tangent kernel with CTA sizes
+                                 from 32 + b to 256 and the coarse band factorization with 256,
+                                 512 and 1024 threads on the context's own data, and keep the
                                  fastest (nls_get_tuning).  The choice changes the order of
-                                 floating-point reductions inside a subdomain only.  0 (default):
-                                 the library's fixed choice or threads_per_block. */
+                                 floating-point reductions only.  0 (default): the library's
+                                 fixed choice or threads_per_block. */
 } nls_options;
 
 /* Per-solve report. */
@@ -151,6 +159,10 @@ int nls_set_partition(nls_ctx* ctx, int32_t n_sub, const int32_t* elem_to_sub, i
 /* Coarse space NLS_COARSE_NONE or NLS_COARSE_RGDSW. */
 int nls_set_coarse(nls_ctx* ctx, int kind);
 
+/* Copy the options (validated; NLS_E_ARG on a bad value).  After nls_setup the factor
+ * precisions can no longer change (the factor storage is sized for them); any other change
+ * takes effect at the next call and drops the reused coarse factorization and the captured
+ * GMRES graphs. */
 int nls_set_options(nls_ctx* ctx, const nls_options* opt);
 int nls_get_options(const nls_ctx* ctx, nls_options* opt);
 
@@ -203,14 +215,15 @@ typedef struct nls_kernel_stat {
 /* Copy up to `cap` entries (kernels with at least one launch) into out; *n_out receives the count. */
 int nls_get_kernel_stats(const nls_ctx* ctx, int32_t cap, nls_kernel_stat* out, int32_t* n_out);
 
-/* CTA sizes in use for the batched local Newton kernel and the tangent kernel, and whether
- * they came from the autotuner (1) or the fixed rule (0).  Valid after nls_setup. */
+/* CTA sizes in use for the batched local Newton kernel, the tangent kernel and the coarse
+ * factorization, and whether they came from the autotuner (1) or the fixed rule (0).  Valid
+ * after nls_setup. */
 typedef struct nls_tuning {
   int32_t newton_threads, apply_threads;
   int32_t newton_tuned, apply_tuned;
   double newton_ms[2];        /* measured launch times of the 128- and 256-thread variants (0: not tried) */
   int32_t graphs_captured;    /* GMRES iteration graphs currently instantiated */
-  int32_t pad;
+  int32_t coarse_threads;     /* CTA size of the coarse band factorization (autotuned when enabled) */
 } nls_tuning;
 int nls_get_tuning(const nls_ctx* ctx, nls_tuning* out);
 int nls_reset_kernel_stats(nls_ctx* ctx);

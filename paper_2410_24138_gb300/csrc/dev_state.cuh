@@ -92,6 +92,7 @@ struct Dev {
   double* ainv = nullptr;               // explicit A_0^-1 (transposed) for the tangent phase
   double* gpart = nullptr;              // GEMV chunk partials
   bool ainv_valid = false;
+  bool coarse_fact_valid = false;  // the coarse band factors hold A_0 at some earlier point
   int clock_khz = 1;
   double* h_scal = nullptr;  // pinned
   int m = 0;                 // GMRES restart length allocated
@@ -99,8 +100,8 @@ struct Dev {
   void* guess = nullptr;  // learned-guess attachment (guess.cu)
   double last_load = 1.0;
   // CTA sizes (0 = fixed rule) and the autotuner's measurements
-  int newton_T = 0, apply_T = 0;
-  bool newton_tuned = false, apply_tuned = false;
+  int newton_T = 0, apply_T = 0, coarse_T = 1024;
+  bool newton_tuned = false, apply_tuned = false, coarse_tuned = false;
   double newton_ms[2] = {0.0, 0.0};
   // GMRES iteration graphs, one per Krylov index, valid while `graph_key` matches
   cudaStream_t cap = nullptr;  // private stream the graphs are captured on

@@ -627,13 +627,15 @@ __device__ void band_pack_solve(int n, int b, const FT* __restrict__ F, FT* __re
 
 // Triangular solves with the packed operands, in place on y[0..n) (shared memory): warp 0
 // applies the block inverse (lane r: row r of inv(L_tt) or inv(U_tt) dotted with the block of
-// y), threads 32 .. 32 + b - 1 apply the coupling to the next b rows.  Each block's operands
-// are loaded at the top of its step (BS coalesced loads per thread, issued back to back); the
-// latency is hidden by the other CTAs on the SM rather than by a register double buffer, which
-// keeps the solve at BS operand registers per thread.  Needs blockDim.x >= 32 + b.
-template <typename FT>
+// y), threads 32 .. 32 + b - 1 apply the coupling to the next b rows.  With PF the operands of
+// the next block are loaded into registers while the current one is applied (2 BS operand
+// registers per thread: for kernels with few CTAs per SM, where nothing else hides the load
+// latency); without PF each block's operands are loaded at the top of its step (BS registers,
+// for kernels that keep enough CTAs resident).  Needs blockDim.x >= 32 + b.
+template <typename FT, bool PF>
 __device__ void band_solve_packed(int n, int b, const FT* __restrict__ P, FT* y) {
   constexpr int BS = SolveBlock<FT>::BS;
+  constexpr int NB = PF ? 2 : 1;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const bool diag = wid == 0 && lane < BS;
   const bool offd = tid >= 32 && tid < 32 + b;
@@ -641,18 +643,27 @@ __device__ void band_solve_packed(int n, int b, const FT* __restrict__ P, FT* y)
   const int64_t PB = packed_block_entries<FT>(b);
   const int nblk = (n + BS - 1) / BS;
   const int64_t oL = 0, oU = BS * BS, oCL = 2 * BS * BS, oCU = 2 * BS * BS + (int64_t)b * BS;
-  FT cur[BS];
-  // forward: diag lanes read inv(L_tt), coupling threads read CL
-  for (int t = 0; t < nblk; ++t) {
-    const int k0 = t * BS, kb = min(BS, n - k0);
+  FT buf[NB][BS];
+  auto load = [&](int t, int which, int64_t od, int64_t oc) {
     const FT* Pt = P + (int64_t)t * PB;
     if (diag) {
 #pragma unroll
-      for (int j = 0; j < BS; ++j) cur[j] = Pt[oL + j * BS + lane];
+      for (int j = 0; j < BS; ++j) buf[which][j] = Pt[od + j * BS + lane];
     } else if (offd) {
 #pragma unroll
-      for (int j = 0; j < BS; ++j) cur[j] = Pt[oCL + j * b + r];
+      for (int j = 0; j < BS; ++j) buf[which][j] = Pt[oc + j * b + r];
     }
+  };
+  // forward: diag lanes read inv(L_tt), coupling threads read CL
+  if (PF && nblk > 0) load(0, 0, oL, oCL);
+  for (int t = 0; t < nblk; ++t) {
+    const int k0 = t * BS, kb = min(BS, n - k0);
+    if (PF) {
+      if (t + 1 < nblk) load(t + 1, NB - 1, oL, oCL);
+    } else {
+      load(t, 0, oL, oCL);
+    }
+    const FT* cur = buf[0];
     if (wid == 0) {  // the whole warp reaches __syncwarp; only lanes < BS hold a block row
       FT a0 = 0, a1 = 0;
       if (diag) {
@@ -679,18 +690,21 @@ __device__ void band_solve_packed(int n, int b, const FT* __restrict__ P, FT* y)
       }
     }
     __syncthreads();
+    if (PF) {
+#pragma unroll
+      for (int j = 0; j < BS; ++j) buf[0][j] = buf[NB - 1][j];
+    }
   }
   // backward: diag lanes read inv(U_tt), coupling threads read CU
+  if (PF && nblk > 0) load(nblk - 1, 0, oU, oCU);
   for (int t = nblk - 1; t >= 0; --t) {
     const int k0 = t * BS, kb = min(BS, n - k0);
-    const FT* Pt = P + (int64_t)t * PB;
-    if (diag) {
-#pragma unroll
-      for (int j = 0; j < BS; ++j) cur[j] = Pt[oU + j * BS + lane];
-    } else if (offd) {
-#pragma unroll
-      for (int j = 0; j < BS; ++j) cur[j] = Pt[oCU + j * b + r];
+    if (PF) {
+      if (t > 0) load(t - 1, NB - 1, oU, oCU);
+    } else {
+      load(t, 0, oU, oCU);
     }
+    const FT* cur = buf[0];
     if (wid == 0) {
       FT a0 = 0, a1 = 0;
       if (diag) {
@@ -717,6 +731,10 @@ __device__ void band_solve_packed(int n, int b, const FT* __restrict__ P, FT* y)
       }
     }
     __syncthreads();
+    if (PF) {
+#pragma unroll
+      for (int j = 0; j < BS; ++j) buf[0][j] = buf[NB - 1][j];
+    }
   }
 }
 

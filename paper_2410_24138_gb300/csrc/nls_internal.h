@@ -144,6 +144,7 @@ int get_coarse_basis(const Context& c, double* P0);
 int kernel_stats(const Context& c, int32_t cap, nls_kernel_stat* out, int32_t* n_out);
 void reset_kernel_stats(Context& c);
 int get_tuning(const Context& c, nls_tuning* out);
+void options_changed(Context& c);  // drops state that depends on the options (reused coarse factors, graphs)
 int local_corrections_noalloc(Context& c, const double* x, double* Fx, int32_t* its, int32_t* status, double load);
 // guess.cu
 int guess_attach(Context& c, nls_guess_net* net, int32_t mode);

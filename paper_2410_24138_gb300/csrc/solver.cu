@@ -296,14 +296,14 @@ __device__ void local_jacobian(const LocalArgs& A, const SubMeta& m, const doubl
 
 // s = J^-1 rhs with the band factors, then FP64 iterative refinement against the CSR matrix
 // (columns < n) when the factors are FP32.  `res` is an n-vector of scratch.
-template <typename FT>
+template <typename FT, bool PF>
 __device__ int local_solve(const LocalArgs& A, const SubMeta& m, const int32_t* rowptr, const int32_t* colidx,
                            const double* csr, const FT* Dv, const double* rhs, double rhs_norm, double* s,
                            double* res, FT* yv, double* red) {
   const int n = m.n;
   for (int a = threadIdx.x; a < n; a += blockDim.x) yv[a] = (FT)rhs[a];
   __syncthreads();
-  dev::band_solve_packed<FT>(n, m.b, Dv, yv);
+  dev::band_solve_packed<FT, PF>(n, m.b, Dv, yv);
   for (int a = threadIdx.x; a < n; a += blockDim.x) s[a] = (double)yv[a];
   __syncthreads();
   int sweeps = 0;
@@ -323,7 +323,7 @@ __device__ int local_solve(const LocalArgs& A, const SubMeta& m, const int32_t* 
       if (!(rn > A.ir_rtol * rhs_norm)) break;
       for (int a = threadIdx.x; a < n; a += blockDim.x) yv[a] = (FT)res[a];
       __syncthreads();
-      dev::band_solve_packed<FT>(n, m.b, Dv, yv);
+      dev::band_solve_packed<FT, PF>(n, m.b, Dv, yv);
       for (int a = threadIdx.x; a < n; a += blockDim.x) s[a] += (double)yv[a];
       __syncthreads();
       ++sweeps;
@@ -441,7 +441,7 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 128 ? 4 : 1)) k_local_newton(Lo
       }
       dev::band_pack_solve<FT>(n, m.b, F, Dv, win, inv_warps);
       mark(2);
-      local_solve<FT>(A, m, rowptr, colidx, csr, Dv, r, rn, s, res, yv, red);
+      local_solve<FT, false>(A, m, rowptr, colidx, csr, Dv, r, rn, s, res, yv, red);
       mark(3);
       for (int a = tid; a < n; a += blockDim.x) wb[a] = xt[a];
       __syncthreads();
@@ -526,7 +526,7 @@ __global__ void __launch_bounds__(512) k_local_apply(LocalArgs A) {
     loc += acc * acc;
   }
   const double qn = sqrt(dev::block_sum(loc, red));
-  local_solve<FT>(A, m, rowptr, colidx, csr, Dv, q, qn, z, res, yv, red);
+  local_solve<FT, true>(A, m, rowptr, colidx, csr, Dv, q, qn, z, res, yv, red);
   for (int a = tid; a < n; a += blockDim.x)
     if (A.owned[m.vec_off + a]) {
       const int64_t g = (int64_t)A.tnode_gid[m.tnode_off + a / nd] * nd + a % nd;
@@ -538,7 +538,7 @@ __global__ void __launch_bounds__(512) k_local_apply(LocalArgs A) {
 // coarse space: harmonic extension (setup) and Galerkin blocks
 // ------------------------------------------------------------------------------------------
 template <int LAW>
-__global__ void __launch_bounds__(512) k_harmonic(LocalArgs A) {
+__global__ void __launch_bounds__(256) k_harmonic(LocalArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
   const SmemPlan P = smem_plan<double>(A.max_n, A.max_nt, A.max_b, true);
   double* xt = (double*)(smem + P.xt);
@@ -586,7 +586,7 @@ __global__ void __launch_bounds__(512) k_harmonic(LocalArgs A) {
 }
 
 template <int LAW, typename JT>
-__global__ void __launch_bounds__(1024) k_galerkin(LocalArgs A) {
+__global__ void __launch_bounds__(256) k_galerkin(LocalArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
   const SmemPlan P = smem_plan<double>(A.max_n, A.max_nt, A.max_b, false);
   double* xt = (double*)(smem + P.xt);
@@ -675,7 +675,7 @@ __global__ void __launch_bounds__(256) k_coarse_inverse(int N0, int b0, const do
   for (int col = blockIdx.x; col < N0; col += gridDim.x) {
     for (int a = threadIdx.x; a < N0; a += blockDim.x) y[a] = (a == col) ? (FT)1 : (FT)0;
     __syncthreads();
-    dev::band_solve_packed<FT>(N0, b0, Dinv, y);
+    dev::band_solve_packed<FT, false>(N0, b0, Dinv, y);
     for (int a = threadIdx.x; a < N0; a += blockDim.x) z[a] = (double)y[a];
     __syncthreads();
     if (sizeof(FT) == 4) {
@@ -694,7 +694,7 @@ __global__ void __launch_bounds__(256) k_coarse_inverse(int N0, int b0, const do
         if (!(rn > ir_rtol)) break;
         for (int a = threadIdx.x; a < N0; a += blockDim.x) y[a] = (FT)res[a];
         __syncthreads();
-        dev::band_solve_packed<FT>(N0, b0, Dinv, y);
+        dev::band_solve_packed<FT, false>(N0, b0, Dinv, y);
         for (int a = threadIdx.x; a < N0; a += blockDim.x) z[a] += (double)y[a];
         __syncthreads();
       }
@@ -749,7 +749,7 @@ __global__ void __launch_bounds__(256) k_coarse_solve(int N0, int b0, const doub
     loc += g[a] * g[a];
   }
   const double gn = sqrt(dev::block_sum(loc, red));
-  dev::band_solve_packed<FT>(N0, b0, Dinv, y);
+  dev::band_solve_packed<FT, true>(N0, b0, Dinv, y);
   for (int a = threadIdx.x; a < N0; a += blockDim.x) z[a] = (double)y[a];
   __syncthreads();
   if (sizeof(FT) == 4) {
@@ -768,7 +768,7 @@ __global__ void __launch_bounds__(256) k_coarse_solve(int N0, int b0, const doub
       if (!(rn > ir_rtol * gn)) break;
       for (int a = threadIdx.x; a < N0; a += blockDim.x) y[a] = (FT)res[a];
       __syncthreads();
-      dev::band_solve_packed<FT>(N0, b0, Dinv, y);
+      dev::band_solve_packed<FT, true>(N0, b0, Dinv, y);
       for (int a = threadIdx.x; a < N0; a += blockDim.x) z[a] += (double)y[a];
       __syncthreads();
     }
@@ -1258,11 +1258,30 @@ bool coarse_matrix(Context& c, const double* x) {
   LAUNCH(D, k_a0_gather, grid_for(ne), 256, 0, ne, D.a0_ptr, D.a0_src, D.blk, D.A0);
   const bool f32 = fp32_coarse(c);
   const size_t fsm = coarse_factor_smem(c, f32);
-  if (f32)
-    LAUNCH(D, k_coarse_factor<float>, 1, 1024, fsm, c.cs.N0, c.cs.b0, D.A0, (float*)D.A0f, (float*)D.A0dinv, D.cstatus);
-  else
-    LAUNCH(D, k_coarse_factor<double>, 1, 1024, fsm, c.cs.N0, c.cs.b0, D.A0, (double*)D.A0f, (double*)D.A0dinv,
-           D.cstatus);
+  auto factor = [&](int T) {
+    if (f32)
+      LAUNCH(D, k_coarse_factor<float>, 1, T, fsm, c.cs.N0, c.cs.b0, D.A0, (float*)D.A0f, (float*)D.A0dinv,
+             D.cstatus);
+    else
+      LAUNCH(D, k_coarse_factor<double>, 1, T, fsm, c.cs.N0, c.cs.b0, D.A0, (double*)D.A0f, (double*)D.A0dinv,
+             D.cstatus);
+  };
+  if (c.opt.autotune && !D.coarse_tuned) {
+    // the factorization reads A_0 and overwrites its own outputs: every candidate is a full,
+    // valid factorization; the fastest CTA size is kept
+    double best = INFINITY;
+    int bestT = 1024;
+    for (int T : {256, 512, 1024}) {
+      const float ms = time_on_stream(D, [&] { factor(T); });
+      if (ms < best) {
+        best = ms;
+        bestT = T;
+      }
+    }
+    D.coarse_T = bestT;
+    D.coarse_tuned = true;
+  }
+  factor(D.coarse_T);
   int32_t st = 0;
   CK(cudaMemcpyAsync(&st, D.cstatus, sizeof(int32_t), cudaMemcpyDeviceToHost, D.s));
   sync(D);
@@ -1317,14 +1336,24 @@ CoarseResult coarse_newton(Context& c, const double* u, double load) {
     return R;
   }
   const double tol = std::max(c.opt.inner_atol, c.opt.inner_rtol * gn);
+  // With coarse_reuse the iteration starts from the factorization of the previous tangent
+  // phase's A_0 (chord steps, solved with its explicit inverse) and forms A_0 at the current
+  // point only when a step contracts ||g|| by less than half or fails the line search; the
+  // stopping test is the same either way.
+  bool refresh = !(c.opt.coarse_reuse && D.coarse_fact_valid);
   while (gn > tol) {
     if (R.its >= c.opt.inner_maxit) {
       R.status = ST_MAXIT;
       break;
     }
-    if (!coarse_matrix(c, D.u0)) {
-      R.status = ST_PIVOT;
-      break;
+    const bool chord = !refresh;
+    if (!chord) {
+      D.ainv_valid = false;  // the explicit inverse belongs to an older A_0
+      D.coarse_fact_valid = coarse_matrix(c, D.u0);
+      if (!D.coarse_fact_valid) {
+        R.status = ST_PIVOT;
+        break;
+      }
     }
     coarse_solve(c, D.g, D.dc);
     double alpha = 1.0, gtn = INFINITY;
@@ -1341,11 +1370,16 @@ CoarseResult coarse_newton(Context& c, const double* u, double load) {
       }
       alpha *= 0.5;
     }
+    if (!accepted && chord) {
+      refresh = true;  // retry the step with A_0 at the current point
+      continue;
+    }
     R.its += 1;
     if (!accepted) {
       R.status = ST_LS;
       break;
     }
+    refresh = !c.opt.coarse_reuse || gtn > 0.5 * gn;
     std::swap(D.c, D.ct);
     std::swap(D.u0, D.x);
     std::swap(D.g, D.gt);
@@ -1593,7 +1627,6 @@ FxInfo evaluate_Fx(Context& c, const double* u, double load, double* t_inner, do
   Dev& D = *c.dev;
   FxInfo info;
   const int cp = c.opt.coupling;
-  D.ainv_valid = false;
   CK(cudaMemsetAsync(D.Fx, 0, sizeof(double) * c.N, D.s));
   auto t0 = std::chrono::steady_clock::now();
   const double* point = u;
@@ -1626,7 +1659,9 @@ FxInfo evaluate_Fx(Context& c, const double* u, double load, double* t_inner, do
     // F_x += P0 T_0(u); the coarse part of the tangent at u_0 = u - P0 T_0(u)
     LAUNCH(D, k_p0_apply, grid_for(c.N), 256, 0, c.N, D.p0_rowptr, D.p0_col, D.p0_val, D.c, 1.0, D.Fx, 1.0, D.Fx);
     global_jacobian(c, D.u0);
-    if (!coarse_matrix(c, D.u0)) info.pivot_failure = true;
+    D.ainv_valid = false;
+    D.coarse_fact_valid = coarse_matrix(c, D.u0);
+    if (!D.coarse_fact_valid) info.pivot_failure = true;
     // the tangent's coarse solves (one per GMRES iteration) reuse A_0(u_0): form its inverse
     else if (D.ainv) {
       const int N0 = c.cs.N0;
@@ -1688,6 +1723,10 @@ void run_iteration_graph(Context& c, int j, F&& body) {
   std::string key((const char*)&c.opt, sizeof(c.opt));
   key += D.ainv_valid ? 'i' : 'b';
   key += std::to_string(apply_threads(c));
+  // scratch vectors the tangent writes (some are swapped by the coarse Newton iteration)
+  for (const void* p : {(const void*)D.t1, (const void*)D.t2, (const void*)D.w0, (const void*)D.gt,
+                        (const void*)D.dc, (const void*)D.gpart, (const void*)D.cres, (const void*)D.cy})
+    key += std::to_string((uintptr_t)p) + ",";
   if (key != D.graph_key || (int)D.it_exec.size() != D.m) {
     D.reset_graphs();
     D.graph_key = key;
@@ -1834,6 +1873,10 @@ int solve(Context& c, double* u_user, int u_dev, nls_report* rep) {
   try {
     CK(cudaSetDevice(c.device));
     D.prof = c.opt.profile_kernels != 0;
+    // a solve depends on its inputs only: the coarse factorization is reused across the outer
+    // iterations of this call, never from an earlier one
+    D.coarse_fact_valid = false;
+    D.ainv_valid = false;
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
@@ -2150,6 +2193,13 @@ int local_corrections_noalloc(Context& c, const double* x, double* Fx, int32_t* 
   return NLS_OK;
 }
 
+void options_changed(Context& c) {
+  if (!c.dev) return;
+  c.dev->coarse_fact_valid = false;
+  c.dev->ainv_valid = false;
+  c.dev->reset_graphs();
+}
+
 int get_tuning(const Context& c, nls_tuning* out) {
   std::memset(out, 0, sizeof(*out));
   out->newton_threads = local_threads(c);
@@ -2160,6 +2210,7 @@ int get_tuning(const Context& c, nls_tuning* out) {
     out->newton_ms[0] = c.dev->newton_ms[0];
     out->newton_ms[1] = c.dev->newton_ms[1];
     for (auto g : c.dev->it_exec) out->graphs_captured += g ? 1 : 0;
+    out->coarse_threads = c.dev->coarse_T;
   }
   return NLS_OK;
 }

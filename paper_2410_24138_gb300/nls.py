@@ -33,7 +33,8 @@ class Options(ctypes.Structure):
                 ("gmres_rtol", ctypes.c_double), ("gmres_restart", ctypes.c_int32), ("gmres_maxit", ctypes.c_int32),
                 ("ir_rtol", ctypes.c_double), ("ir_max_sweeps", ctypes.c_int32),
                 ("threads_per_block", ctypes.c_int32), ("verbose", ctypes.c_int32),
-                ("profile_kernels", ctypes.c_int32), ("cuda_graphs", ctypes.c_int32), ("autotune", ctypes.c_int32)]
+                ("profile_kernels", ctypes.c_int32), ("cuda_graphs", ctypes.c_int32),
+                ("coarse_reuse", ctypes.c_int32), ("autotune", ctypes.c_int32)]
 
 
 class Report(ctypes.Structure):
@@ -65,12 +66,14 @@ class Sizes(ctypes.Structure):
 class Tuning(ctypes.Structure):
     _fields_ = [("newton_threads", ctypes.c_int32), ("apply_threads", ctypes.c_int32),
                 ("newton_tuned", ctypes.c_int32), ("apply_tuned", ctypes.c_int32),
-                ("newton_ms", ctypes.c_double * 2), ("graphs_captured", ctypes.c_int32), ("pad", ctypes.c_int32)]
+                ("newton_ms", ctypes.c_double * 2), ("graphs_captured", ctypes.c_int32),
+                ("coarse_threads", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {"newton_threads": self.newton_threads, "apply_threads": self.apply_threads,
                 "newton_tuned": bool(self.newton_tuned), "apply_tuned": bool(self.apply_tuned),
-                "newton_ms": list(self.newton_ms), "graphs_captured": self.graphs_captured}
+                "newton_ms": list(self.newton_ms), "graphs_captured": self.graphs_captured,
+                "coarse_threads": self.coarse_threads}
 
 
 class KernelStat(ctypes.Structure):
