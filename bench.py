@@ -43,6 +43,8 @@ def workload(name: str):
         return I.diffusion_c1(), "diffusion 64x64 P1, 4x4 subdomains, overlap 1"
     if name == "c3":
         return I.neohooke_c3(), "Neo-Hooke 512x512 Q1 (0.5M dofs), 256 uneven subdomains, overlap 2, 5 load steps"
+    if name == "c4":
+        return I.diffusion_c4(1), "log-normal diffusion 512x512 P1 (263k dofs), 256 uneven subdomains, overlap 2"
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -159,6 +161,94 @@ class ClockSampler:
 # ----------------------------------------------------------------------------------------------
 # GPU arm
 # ----------------------------------------------------------------------------------------------
+def run_c4(args):
+    """Learned-guess workload (log-normal diffusion, 512 x 512 P1, 256 bricks, overlap 2): harvest
+    (features, converged local state) pairs from the method's own solves over training fields,
+    train the network on the GPU (BF16 tensor-core GEMMs, FP32 master weights, Adam), then time
+    held-out solves with and without the guess on the same context (coefficients swapped with
+    nls_set_coefficients).  The timed region is the solves only; training is reported apart."""
+    import torch
+    from paper_2410_24138_gb300 import build, nls, inputs as I
+    build.build()
+    n, per = 512, 16
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream().cuda_stream
+    base = I.diffusion_c4(1, n=n, per_side=per)
+    s = nls.Solver(device=0, stream=stream)
+    s.set_problem(base)
+    s.set_coarse(nls.COARSE_RGDSW)
+    s.set_options(coupling=nls.COUPLING["hybrid"], local_precision=nls.PREC_FP32_IR,
+                  coarse_precision=nls.PREC_FP32_IR, autotune=1)
+    t0 = time.perf_counter()
+    s.setup()
+    setup_s = time.perf_counter() - t0
+    sizes = s.sizes()
+    net = nls.GuessNet(h1=512, h2=512, seed=11, capacity=args.c4_pairs + 4096)
+    nls.attach_guess(s, net, nls.GUESS_HARVEST)
+    t0 = time.perf_counter()
+    seed, harvest_solves = 1, 0
+    while net.pairs() < args.c4_pairs:
+        s.set_coefficients(*I.c4_elem_coefficients(seed, n))
+        u, rep = s.solve()
+        seed += 1
+        harvest_solves += 1
+    harvest_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    losses = net.train(steps=args.c4_train_steps, batch=256, lr=1e-3, seed=5)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    flush_buf = torch.zeros(64 * 1024 * 1024, dtype=torch.float64, device="cuda")
+    res = {"plain": [], "guess": []}
+    accepted = proposed = 0
+    test_seeds = list(range(1001, 1001 + args.steps))
+    for mode in ("plain", "guess"):
+        nls.attach_guess(s, net if mode == "guess" else None, nls.GUESS_USE)
+        if mode == "guess":
+            nls.set_guess_smoothing(s, args.c4_sweeps, 0.8)
+        for i, sd in enumerate([1001, 1002, 1003] + test_seeds):  # the first three warm up
+            s.set_coefficients(*I.c4_elem_coefficients(sd, n))
+            flush_buf.add_(1.0)
+            u = torch.zeros(sizes.n_dofs, dtype=torch.float64, device="cuda")
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            u, rep = s.solve(u)
+            e1.record()
+            e1.synchronize()
+            if mode == "guess":
+                p_, a_ = nls.guess_counts(s)
+            if i >= 3:
+                res[mode].append((e0.elapsed_time(e1), rep.subdomain_newton_steps, rep.outer_iterations,
+                                  rep.final_residual))
+                if mode == "guess":
+                    proposed += p_
+                    accepted += a_
+    ms_plain = sum(r[0] for r in res["plain"])
+    ms_guess = sum(r[0] for r in res["guess"])
+    st_plain = sum(r[1] for r in res["plain"])
+    st_guess = sum(r[1] for r in res["guess"])
+    line = {
+        "metric": METRIC, "value": st_guess / (ms_guess * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": 3, "ms_per_step": ms_guess / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64+f32 (bf16 network training)", "data": "synthetic",
+        "config": {"workload": "log-normal diffusion 512x512 P1 (263k dofs), 256 uneven subdomains, overlap 2; "
+                               "learned initial guess", "coupling": "hybrid",
+                   "l2": "512 MB buffer written between steps", "setup_s": setup_s,
+                   "n_dofs": sizes.n_dofs, "n_sub": sizes.n_sub, "coarse_dofs": sizes.n_coarse_dofs},
+        "guess": {"pairs": net.pairs(), "harvest_solves": harvest_solves, "harvest_s": harvest_s,
+                  "train_steps": args.c4_train_steps, "train_s": train_s,
+                  "loss_first50": float(losses[:50].mean()), "loss_last50": float(losses[-50:].mean()),
+                  "proposed": proposed, "accepted": accepted, "smoothing_sweeps": args.c4_sweeps},
+        "held_out": {"solves": args.steps,
+                     "time_to_solution_ms": {"plain": ms_plain / args.steps, "guess": ms_guess / args.steps},
+                     "subdomain_newton_steps": {"plain": st_plain, "guess": st_guess},
+                     "outer_iterations": {"plain": [r[2] for r in res["plain"]], "guess": [r[2] for r in res["guess"]]},
+                     "max_final_residual": max(r[3] for r in res["plain"] + res["guess"])},
+        "tuning": s.tuning(),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -373,7 +463,10 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3"])
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4"])
+    ap.add_argument("--c4-pairs", type=int, default=50000)
+    ap.add_argument("--c4-train-steps", type=int, default=4000)
+    ap.add_argument("--c4-sweeps", type=int, default=6)
     ap.add_argument("--ref-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -381,6 +474,8 @@ def main():
         raise SystemExit("at least 3 warm-up steps are required")
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "c4":
+        run_c4(args)
     else:
         run_gpu(args)
 

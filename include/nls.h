@@ -156,6 +156,14 @@ int nls_set_material(nls_ctx* ctx, int law, const double* params, const double* 
  * `overlap` >= 1 layers of node-sharing elements (Section 2: element-based overlap). */
 int nls_set_partition(nls_ctx* ctx, int32_t n_sub, const int32_t* elem_to_sub, int32_t overlap);
 
+/* New per-element coefficients k and f of Eq. 1 (NULL = 1) for a diffusion problem, before or
+ * after nls_setup.  After setup only what depends on them is redone -- the external load, the
+ * energy-minimising extension of the coarse basis (it uses K = DF(u^(0))) and the learned
+ * guess's Jacobi diagonal -- not the index maps, so many coefficient fields can be solved on one
+ * mesh and partition (training the learned guess, parameter sweeps).  NLS_E_ARG on a
+ * non-finite value or a non-positive k. */
+int nls_set_coefficients(nls_ctx* ctx, const double* k_elem, const double* f_elem);
+
 /* Coarse space NLS_COARSE_NONE or NLS_COARSE_RGDSW. */
 int nls_set_coarse(nls_ctx* ctx, int kind);
 

@@ -157,6 +157,29 @@ int nls_set_material(nls_ctx* ctx, int law, const double* params, const double* 
   return NLS_OK;
 }
 
+int nls_set_coefficients(nls_ctx* ctx, const double* k_elem, const double* f_elem) {
+  if (!ctx || !ctx->c.have_material) return fail(ctx, NLS_E_ARG, "set the material first");
+  Context& c = ctx->c;
+  if (c.law != NLS_LAW_DIFFUSION) return fail(ctx, NLS_E_ARG, "k_elem / f_elem apply to the diffusion law only");
+  for (const double* a : {k_elem, f_elem})
+    if (a)
+      for (int64_t e = 0; e < c.n_elems; ++e)
+        if (!std::isfinite(a[e])) return fail(ctx, NLS_E_ARG, "non-finite coefficient");
+  if (k_elem)
+    for (int64_t e = 0; e < c.n_elems; ++e)
+      if (!(k_elem[e] > 0.0)) return fail(ctx, NLS_E_ARG, "k must be positive");
+  c.k_elem.clear();
+  c.f_elem.clear();
+  if (k_elem) c.k_elem.assign(k_elem, k_elem + c.n_elems);
+  if (f_elem) c.f_elem.assign(f_elem, f_elem + c.n_elems);
+  if (!c.is_setup) return NLS_OK;
+  nls::build_fext(c);
+  if (!c.dev) return NLS_OK;  // host-only setup
+  const int st = nls::device_set_coefficients(c);
+  if (st != NLS_OK) return fail(ctx, st, c.last_error.c_str());
+  return NLS_OK;
+}
+
 int nls_set_partition(nls_ctx* ctx, int32_t n_sub, const int32_t* elem_to_sub, int32_t overlap) {
   if (!ctx || !ctx->c.have_mesh) return fail(ctx, NLS_E_ARG, "set the mesh first");
   if (n_sub <= 0 || !elem_to_sub) return fail(ctx, NLS_E_ARG, "bad partition");

@@ -315,6 +315,19 @@ __device__ inline void stage_row_async(int row, int n, int W, const FT* F, FT* d
 
 constexpr int kLuPrefetch = 8;
 
+// Rows of the shared-memory window of the band LU: the b + 2 rows an elimination step touches
+// plus the rows staged ahead.
+__host__ __device__ constexpr int band_lu_window_rows(int b) { return b + 2 + kLuPrefetch; }
+
+// Row stride of the window (>= 2b + 1 entries).  One warp of the 2D-tiled update touches 4
+// consecutive rows x 8 consecutive columns, at addresses (stride - 1) apart from row to row;
+// with (stride - 1) = 8 or 24 (mod 32) the four rows land on disjoint groups of 8 banks.
+__host__ __device__ constexpr int band_lu_window_stride(int b) {
+  int w = 2 * b + 1;
+  while (((w - 1) & 31) != 8 && ((w - 1) & 31) != 24) ++w;
+  return w;
+}
+
 // Thread mapping of one elimination step (2D tiling): the CTA is TY x 8 threads, thread
 // (ty, tx) updates rows k+1+ri with ri = ty, ty + TY, ... and columns k+1+cj with
 // cj = tx, tx + 8, ..., tx + 8 (QM - 1) (b <= 8 QM).  Every thread loads its QM pivot-row
@@ -331,20 +344,20 @@ __device__ inline FT recip(FT p) {
 template <typename FT, int QM>
 __device__ int band_lu_inplace_q(int n, int b, FT* __restrict__ F, FT* win, FT* rp, int* flag) {
   constexpr int PD = kLuPrefetch, TX = 8;
-  const int W = 2 * b + 1, R = b + 2 + PD;
+  const int W = 2 * b + 1, WS = band_lu_window_stride(b), R = b + 2 + PD;
   const int tid = threadIdx.x, T = blockDim.x, tx = tid % TX, ty = tid / TX, TY = T / TX;
   if (tid == 0) *flag = 0;
   // stage rows 0 .. b + PD (one copy group per row and thread)
   for (int i = 0; i <= b + PD; ++i) {
     if (i < n)
-      for (int d = tid; d < W; d += T) cp_async_elem<FT>(win + i * W + d, F + (int64_t)i * W + d);
+      for (int d = tid; d < W; d += T) cp_async_elem<FT>(win + i * WS + d, F + (int64_t)i * W + d);
     cp_async_commit();
   }
   cp_async_wait<PD>();
   __syncthreads();
   int sk = 0, s1 = 1;  // ring slots of rows k and k + 1 (R >= b + 2 >= 2)
   for (int k = 0; k < n; ++k) {
-    const FT* rowk = win + sk * W;
+    const FT* rowk = win + sk * WS;
     const FT piv = rowk[b];
     const FT rpk = recip<FT>(piv);
     if (tid == 0) {
@@ -369,7 +382,7 @@ __device__ int band_lu_inplace_q(int n, int b, FT* __restrict__ F, FT* win, FT* 
       const int rs = k + b + 1 + PD;
       const int ss = (sk == 0) ? R - 1 : sk - 1;
       if (rs < n)
-        for (int d = tid; d < W; d += T) cp_async_elem<FT>(win + ss * W + d, F + (int64_t)rs * W + d);
+        for (int d = tid; d < W; d += T) cp_async_elem<FT>(win + ss * WS + d, F + (int64_t)rs * W + d);
       cp_async_commit();
     }
     // rank-1 update of rows k+1..k+lim, columns k+1..k+lim
@@ -379,7 +392,7 @@ __device__ int band_lu_inplace_q(int n, int b, FT* __restrict__ F, FT* win, FT* 
     for (int ri = ty; ri < lim; ri += TY) {
       int slot = s1 + ri;
       if (slot >= R) slot -= R;
-      FT* rowi = win + slot * W + b - ri;
+      FT* rowi = win + slot * WS + b - ri;
       const FT l = rowi[-1] * rpk;
 #pragma unroll
       for (int q = 0; q < QM; ++q) {
@@ -398,9 +411,6 @@ __device__ int band_lu_inplace_q(int n, int b, FT* __restrict__ F, FT* win, FT* 
   return *flag;
 }
 
-// Rows of the shared-memory window of the band LU (each 2b + 1 entries): the b + 2 rows an
-// elimination step touches plus the rows staged ahead.
-__host__ __device__ constexpr int band_lu_window_rows(int b) { return b + 2 + kLuPrefetch; }
 
 // Dispatch on the number of column slots per thread (half bandwidth up to 128).  blockDim.x
 // must be a multiple of 8.

@@ -539,6 +539,28 @@ float net_gradient(GuessNet& N, cudaStream_t s, int B, bool bf16) {
 // ------------------------------------------------------------------------------------------
 // host geometry of the attachment (structured P1 meshes)
 // ------------------------------------------------------------------------------------------
+// Leading-term Jacobian diagonal of every local unknown: sum over the subdomain's elements of
+// k_e |grad phi_a|^2 |e| (the smoothing of proposed starts divides by it times (1 + w_a^2)).
+std::vector<double> jacobi_diagonal(const Context& c) {
+  const LocalSet& s = c.ov;
+  std::vector<double> diag(s.total_n, 0.0);
+  for (int sb = 0; sb < s.count; ++sb) {
+    const SubMeta& m = s.meta[sb];
+    for (int e = 0; e < m.ne; ++e) {
+      const int64_t ge = s.elem_gid[m.elem_off + e];
+      const double* g = &c.geom[ge * c.geom_stride];
+      const double ke = c.k_elem.empty() ? 1.0 : c.k_elem[ge];
+      for (int a = 0; a < 3; ++a) {
+        const int t = s.lconn[(m.elem_off + e) * 3 + a];
+        if (t < m.n) diag[m.vec_off + t] += ke * g[6] * (g[2 * a] * g[2 * a] + g[2 * a + 1] * g[2 * a + 1]);
+      }
+    }
+    for (int a = 0; a < m.n; ++a)
+      if (!(diag[m.vec_off + a] > 0.0)) throw std::runtime_error("learned guess: zero Jacobi diagonal");
+  }
+  return diag;
+}
+
 void build_geometry(Context& c, GuessCtx& G) {
   if (c.elem_type != NLS_P1_TRI || c.ndof != 1)
     throw std::runtime_error("the learned guess supports the P1 diffusion problem on structured meshes");
@@ -569,7 +591,7 @@ void build_geometry(Context& c, GuessCtx& G) {
       fel(nsub);
   std::vector<float> sw((size_t)nsub * 4 * kSide), box(2 * (size_t)nsub);
   std::vector<float2> st(s.total_n);
-  std::vector<double> diag(s.total_n, 0.0);
+  const std::vector<double> diag = jacobi_diagonal(c);
   std::vector<int4> cidx((size_t)nsub * kNO);
   std::vector<float2> cw((size_t)nsub * kNO);
   for (int sb = 0; sb < nsub; ++sb) {
@@ -621,18 +643,7 @@ void build_geometry(Context& c, GuessCtx& G) {
       const int ci = std::min((i0 + i1) / 2, nn - 1), cj = std::min((j0 + j1) / 2, nn - 1);
       fel[sb] = 2 * (cj * nn + ci);
     }
-    // leading-term Jacobian diagonal of the local unknowns (the element's k, |grad phi_a|^2, area)
-    for (int e = 0; e < m.ne; ++e) {
-      const int64_t ge = s.elem_gid[m.elem_off + e];
-      const double* g = &c.geom[ge * c.geom_stride];
-      const double ke = c.k_elem.empty() ? 1.0 : c.k_elem[ge];
-      for (int a = 0; a < 3; ++a) {
-        const int t = s.lconn[(m.elem_off + e) * 3 + a];
-        if (t < m.n) diag[m.vec_off + t] += ke * g[6] * (g[2 * a] * g[2 * a] + g[2 * a + 1] * g[2 * a + 1]);
-      }
-    }
     for (int a = 0; a < m.n; ++a) {
-      if (!(diag[m.vec_off + a] > 0.0)) throw std::runtime_error("learned guess: zero Jacobi diagonal");
       const int32_t v = s.tnode_gid[m.tnode_off + a];
       st[m.vec_off + a] = make_float2((float)((gi[v] - i0) / (double)(i1 - i0)), (float)((gj[v] - j0) / (double)(j1 - j0)));
     }
@@ -755,6 +766,19 @@ void guess_after_local(Context& c, const double* x, double load, bool proposed) 
     LAUNCH(D, k_guess_harvest, G->nsub, 128, 0, a, G->nsub, D.ov.w, N.dX, N.dT, N.npairs);
     N.npairs += G->nsub;
   }
+}
+
+// New k / f on an attached context: the per-element f copy and the Jacobi diagonal follow.
+void guess_coefficients_changed(Context& c) {
+  GuessCtx* G = (c.dev && c.dev->guess) ? (GuessCtx*)c.dev->guess : nullptr;
+  if (!G) return;
+  Dev& D = *c.dev;
+  const std::vector<double> diag = jacobi_diagonal(c);
+  CK(cudaMemcpyAsync(G->diag, diag.data(), sizeof(double) * diag.size(), cudaMemcpyHostToDevice, D.s));
+  std::vector<double> fcell(c.n_elems, 1.0);
+  if (!c.f_elem.empty()) fcell = c.f_elem;
+  CK(cudaMemcpyAsync(G->fcell_dev, fcell.data(), sizeof(double) * fcell.size(), cudaMemcpyHostToDevice, D.s));
+  CK(cudaStreamSynchronize(D.s));
 }
 
 void guess_free(Context& c) {

@@ -131,6 +131,9 @@ struct Context {
 
 // setup.cpp
 int build_setup(Context& c);
+void build_fext(Context& c);
+int device_set_coefficients(Context& c);  // after nls_setup: new k / f on the device, coarse basis rebuilt
+void guess_coefficients_changed(Context& c);
 void build_local_set(Context& c, LocalSet& s, int layers, bool neumann_rows, bool keep_overlap_lists);
 // solver.cu
 int device_setup(Context& c);

@@ -367,26 +367,9 @@ void build_global(Context& c) {
       }
     }
   }
-  // external load at load factor 1
-  c.fext.assign(c.N, 0.0);
-  if (c.law == NLS_LAW_DIFFUSION) {
-    for (int64_t e = 0; e < c.n_elems; ++e) {
-      double f = c.f_elem.empty() ? 1.0 : c.f_elem[e];
-      double a3 = c.geom[e * 8 + 6] / 3.0;
-      for (int a = 0; a < 3; ++a) c.fext[c.conn[e * 3 + a]] += f * a3;
-    }
-  }
-  for (size_t k = 0; k < c.tr_edges.size() / 2; ++k) {
-    int32_t n0 = c.tr_edges[2 * k], n1 = c.tr_edges[2 * k + 1];
-    double L = std::hypot(c.xy[2 * n1] - c.xy[2 * n0], c.xy[2 * n1 + 1] - c.xy[2 * n0 + 1]);
-    for (int d = 0; d < 2; ++d) {
-      c.fext[2 * n0 + d] += 0.5 * L * c.tr_vals[2 * k + d];
-      c.fext[2 * n1 + d] += 0.5 * L * c.tr_vals[2 * k + d];
-    }
-  }
-  for (int64_t g = 0; g < c.N; ++g)
-    if (!c.free_dof[g]) c.fext[g] = 0.0;
+  build_fext(c);
 }
+
 
 // ---- RGDSW interface classification and interface values -----------------------------------
 
@@ -690,6 +673,29 @@ int build_setup(Context& c) {
     build_coarse(c);
   }
   return NLS_OK;
+}
+
+// External load at load factor 1: the source f of Eq. 1 (midpoint-rule lumping per triangle)
+// and the traction of Eq. 2 (two-point rule per edge); zero on Dirichlet dofs.
+void build_fext(Context& c) {
+  c.fext.assign(c.N, 0.0);
+  if (c.law == NLS_LAW_DIFFUSION) {
+    for (int64_t e = 0; e < c.n_elems; ++e) {
+      double f = c.f_elem.empty() ? 1.0 : c.f_elem[e];
+      double a3 = c.geom[e * 8 + 6] / 3.0;
+      for (int a = 0; a < 3; ++a) c.fext[c.conn[e * 3 + a]] += f * a3;
+    }
+  }
+  for (size_t k = 0; k < c.tr_edges.size() / 2; ++k) {
+    int32_t n0 = c.tr_edges[2 * k], n1 = c.tr_edges[2 * k + 1];
+    double L = std::hypot(c.xy[2 * n1] - c.xy[2 * n0], c.xy[2 * n1 + 1] - c.xy[2 * n0 + 1]);
+    for (int d = 0; d < 2; ++d) {
+      c.fext[2 * n0 + d] += 0.5 * L * c.tr_vals[2 * k + d];
+      c.fext[2 * n1 + d] += 0.5 * L * c.tr_vals[2 * k + d];
+    }
+  }
+  for (int64_t g = 0; g < c.N; ++g)
+    if (!c.free_dof[g]) c.fext[g] = 0.0;
 }
 
 }  // namespace nls

@@ -105,7 +105,7 @@ __host__ __device__ inline SmemPlan smem_plan(int max_n, int max_nt, int max_b, 
   p.red = o; o += sizeof(double) * 40;
   p.yv = o; o += align_up(sizeof(FT) * max_n, 16);
   {
-    const size_t lu = (size_t)dev::band_lu_window_rows(max_b) * (2 * max_b + 1);
+    const size_t lu = (size_t)dev::band_lu_window_rows(max_b) * dev::band_lu_window_stride(max_b);
     const size_t inv = 2 * (size_t)dev::SolveBlock<FT>::BS * (dev::SolveBlock<FT>::BS + 1);
     p.win = o;
     o += with_window ? align_up(sizeof(FT) * (lu > inv ? lu : inv), 16) : 0;
@@ -133,7 +133,7 @@ __host__ __device__ inline LocalPlan newton_plan(int max_n, int max_nt, int max_
   p.racc = o; o += sizeof(double) * max_n;
   p.red = o; o += sizeof(double) * 40;
   {
-    const size_t lu = (size_t)dev::band_lu_window_rows(max_b) * (2 * max_b + 1);
+    const size_t lu = (size_t)dev::band_lu_window_rows(max_b) * dev::band_lu_window_stride(max_b);
     const size_t inv = 4 * (size_t)dev::SolveBlock<FT>::BS * (dev::SolveBlock<FT>::BS + 1);
     size_t w = lu > inv ? lu : inv;
     w = w > (size_t)max_n ? w : (size_t)max_n;
@@ -647,7 +647,7 @@ __global__ void __launch_bounds__(1024) k_coarse_factor(int N0, int b0, const do
   constexpr int BS = dev::SolveBlock<FT>::BS;
   const size_t R = (size_t)dev::band_lu_window_rows(b0);
   FT* win = (FT*)smem;
-  FT* rp = win + R * (2 * b0 + 1);
+  FT* rp = win + R * dev::band_lu_window_stride(b0);
   FT* tmp = rp + R;
   int* flag = (int*)(tmp + 4 * BS * (BS + 1));
   const int64_t total = (int64_t)N0 * (2 * b0 + 1);
@@ -655,7 +655,7 @@ __global__ void __launch_bounds__(1024) k_coarse_factor(int N0, int b0, const do
   __syncthreads();
   const int bad = dev::band_lu_inplace<FT>(N0, b0, F, win, rp, flag);
   // the LU window is free again: it holds the packing scratch of up to every warp
-  const int pw = min((int)(blockDim.x >> 5), (int)((R * (2 * b0 + 1)) / (BS * (BS + 1))));
+  const int pw = min((int)(blockDim.x >> 5), (int)((R * dev::band_lu_window_stride(b0)) / (BS * (BS + 1))));
   if (!bad) dev::band_pack_solve<FT>(N0, b0, F, Dinv, pw >= 4 ? win : tmp, pw >= 4 ? pw : 4);
   if (threadIdx.x == 0) *status = bad ? ST_PIVOT : ST_OK;
 }
@@ -1241,7 +1241,7 @@ size_t coarse_factor_smem(const Context& c, bool f32) {
   const size_t fs = f32 ? sizeof(float) : sizeof(double);
   const size_t BS = f32 ? dev::SolveBlock<float>::BS : dev::SolveBlock<double>::BS;
   const size_t R = (size_t)dev::band_lu_window_rows(c.cs.b0);
-  return fs * (R * (2 * c.cs.b0 + 1) + R + 4 * BS * (BS + 1)) + 16;
+  return fs * (R * dev::band_lu_window_stride(c.cs.b0) + R + 4 * BS * (BS + 1)) + 16;
 }
 
 // A_0(x) = P_0^T DF(x) P_0 -> band -> factor.  Returns false on a bad pivot.
@@ -1431,6 +1431,38 @@ void upload_set(Dev& D, const LocalSet& h, DeviceLocalSet& d, bool fp32_factor, 
 
 }  // namespace
 
+// Energy-minimising extension of the interface values of the coarse basis (RGDSW, Section 2)
+// with K = DF(u^(0)), u^(0) = Dirichlet data and zero elsewhere, then the values of P_0 and
+// P_0^T.  The factors of the non-overlapping problems are needed for the extension only.
+void coarse_extension(Context& c) {
+  Dev& D = *c.dev;
+  Coarse& cs = c.cs;
+  const int64_t N = c.N;
+  const size_t lim = D.smem_optin;
+  auto need = [&](size_t b, const char* what) {
+    if (b > lim) throw std::runtime_error(std::string(what) + " needs more shared memory than the device offers");
+  };
+  if (!D.nov.factor) D.nov.factor = D.alloc<double>(c.nov.total_factor);
+  CK(cudaMemcpyAsync(D.phi, cs.phi_host.data(), sizeof(double) * cs.phi_host.size(), cudaMemcpyHostToDevice, D.s));
+  CK(cudaMemcpyAsync(D.x, D.ubc, sizeof(double) * N, cudaMemcpyDeviceToDevice, D.s));
+  LocalArgs A = coarse_args(c);
+  A.x = D.x;
+  const size_t sm = smem_plan<double>(c.nov.max_n, c.nov.max_nt, c.nov.max_b, true).total;
+  need(sm, "coarse harmonic extension");
+  if (c.law == NLS_LAW_DIFFUSION) LAUNCH(D, k_harmonic<NLS_LAW_DIFFUSION>, c.nov.count, 256, sm, A);
+  else LAUNCH(D, k_harmonic<NLS_LAW_NEOHOOKE>, c.nov.count, 256, sm, A);
+  std::vector<int32_t> st(c.nov.count);
+  CK(cudaMemcpyAsync(st.data(), D.nov.status, sizeof(int32_t) * st.size(), cudaMemcpyDeviceToHost, D.s));
+  sync(D);
+  for (int32_t s : st)
+    if (s != ST_OK) throw std::runtime_error("coarse harmonic extension hit a zero pivot");
+  const int64_t np = (int64_t)cs.p0_col.size();
+  LAUNCH(D, k_gather_values, grid_for(np), 256, 0, np, D.p0_src, D.phi, D.p0_val);
+  LAUNCH(D, k_gather_values32, grid_for(np), 256, 0, np, D.p0t_src, D.p0_val, D.p0t_val);
+  D.release(D.nov.factor);
+  D.nov.factor = nullptr;
+}
+
 int device_setup(Context& c) {
   try {
     CK(cudaSetDevice(c.device));
@@ -1552,25 +1584,7 @@ int device_setup(Context& c) {
       D.g = D.alloc<double>(cs.N0);
       D.gt = D.alloc<double>(cs.N0);
       D.cres = D.alloc<double>(cs.N0);
-      // energy-minimising extension with K = DF(u^(0)), u^(0) = Dirichlet data, zero elsewhere
-      CK(cudaMemcpyAsync(D.x, D.ubc, sizeof(double) * N, cudaMemcpyDeviceToDevice, D.s));
-      LocalArgs A = coarse_args(c);
-      A.x = D.x;
-      const size_t sm = smem_plan<double>(c.nov.max_n, c.nov.max_nt, c.nov.max_b, true).total;
-      need(sm, "coarse harmonic extension");
-      if (c.law == NLS_LAW_DIFFUSION) LAUNCH(D, k_harmonic<NLS_LAW_DIFFUSION>, c.nov.count, 256, sm, A);
-      else LAUNCH(D, k_harmonic<NLS_LAW_NEOHOOKE>, c.nov.count, 256, sm, A);
-      std::vector<int32_t> st(c.nov.count);
-      CK(cudaMemcpyAsync(st.data(), D.nov.status, sizeof(int32_t) * st.size(), cudaMemcpyDeviceToHost, D.s));
-      sync(D);
-      for (int32_t s : st)
-        if (s != ST_OK) throw std::runtime_error("coarse harmonic extension hit a zero pivot");
-      const int64_t np = (int64_t)cs.p0_col.size();
-      LAUNCH(D, k_gather_values, grid_for(np), 256, 0, np, D.p0_src, D.phi, D.p0_val);
-      LAUNCH(D, k_gather_values32, grid_for(np), 256, 0, np, D.p0t_src, D.p0_val, D.p0t_val);
-      // the non-overlapping factors are only needed for the extension
-      D.release(D.nov.factor);
-      D.nov.factor = nullptr;
+      coarse_extension(c);
     }
     sync(D);
     c.device_bytes = D.bytes;
@@ -1580,6 +1594,30 @@ int device_setup(Context& c) {
   } catch (const std::bad_alloc&) {
     c.last_error = "host allocation failed";
     return NLS_E_NOMEM;
+  } catch (const std::exception& ex) {
+    c.last_error = ex.what();
+    return NLS_E_ARG;
+  }
+  return NLS_OK;
+}
+
+int device_set_coefficients(Context& c) {
+  try {
+    Dev& D = *c.dev;
+    CK(cudaSetDevice(c.device));
+    std::vector<double> k = c.k_elem;
+    if (k.empty()) k.assign(c.n_elems, 1.0);
+    CK(cudaMemcpyAsync(D.kcoef, k.data(), sizeof(double) * k.size(), cudaMemcpyHostToDevice, D.s));
+    CK(cudaMemcpyAsync(D.fext, c.fext.data(), sizeof(double) * c.fext.size(), cudaMemcpyHostToDevice, D.s));
+    if (c.coarse_kind == NLS_COARSE_RGDSW) coarse_extension(c);
+    D.coarse_fact_valid = false;
+    D.ainv_valid = false;
+    D.tangent_ready = false;
+    guess_coefficients_changed(c);
+    sync(D);
+  } catch (const CudaFailure& ex) {
+    c.last_error = ex.what();
+    return NLS_E_CUDA;
   } catch (const std::exception& ex) {
     c.last_error = ex.what();
     return NLS_E_ARG;

@@ -268,13 +268,26 @@ def neohooke_c3(n: int = 512, per_side: int = 16, seed: int = PARTITION_SEED,
                             traction_max, load_steps, name=f"neohooke_c3_{n}x{n}_Q1_{per_side * per_side}_bricks")
 
 
-def diffusion_c4(field_seed: int, n: int = 512, per_side: int = 16, seed: int = PARTITION_SEED) -> Problem:
+def c4_cell_coefficients(field_seed: int, n: int = 512):
+    """Per-cell k (log-normal field, correlation length 1/16, sigma 1) and f (one constant per
+    instance, uniform in [0.5, 2]) of the learned-guess workload."""
     g = gaussian_random_field(n, field_seed, ell=1.0 / 16.0, sigma=1.0)
-    k = np.exp(g)
     f = 0.5 + 1.5 * uniform01(splitmix64(field_seed ^ 0x5DEECE66D), 1)[0]
+    return np.exp(g), np.full(n * n, f)
+
+
+def c4_elem_coefficients(field_seed: int, n: int = 512):
+    """The same per element (both triangles of a cell share the cell's values)."""
+    k, f = c4_cell_coefficients(field_seed, n)
+    rep = elems_per_cell(P1_TRI)
+    return np.repeat(k, rep), np.repeat(f, rep)
+
+
+def diffusion_c4(field_seed: int, n: int = 512, per_side: int = 16, seed: int = PARTITION_SEED) -> Problem:
+    k, f = c4_cell_coefficients(field_seed, n)
     return diffusion_problem(n, brick_partition(n, per_side, per_side, seed), per_side * per_side, 2,
                              name=f"diffusion_c4_{n}x{n}_P1_lognormal_k_seed{field_seed}",
-                             k_cell=k, f_cell=np.full(n * n, f))
+                             k_cell=k, f_cell=f)
 
 
 def neohooke_c5(n: int = 2048, per_side: int = 64, seed: int = PARTITION_SEED) -> Problem:

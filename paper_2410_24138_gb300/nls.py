@@ -91,7 +91,7 @@ EXPORTS = ["nls_options_default", "nls_create", "nls_destroy", "nls_strerror", "
            "nls_reset_kernel_stats", "nls_local_corrections_noalloc", "nls_guess_create", "nls_guess_destroy",
            "nls_guess_attach", "nls_guess_train", "nls_guess_pairs", "nls_guess_get_params", "nls_guess_set_params",
            "nls_guess_get_normalisation", "nls_guess_set_normalisation", "nls_guess_gradient", "nls_guess_forward",
-           "nls_guess_counts", "nls_get_tuning", "nls_guess_set_smoothing"]
+           "nls_guess_counts", "nls_get_tuning", "nls_guess_set_smoothing", "nls_set_coefficients"]
 
 _LIB = None
 _P = ctypes.c_void_p
@@ -155,6 +155,7 @@ def load() -> ctypes.CDLL:
         "nls_guess_forward": (ctypes.c_int, [_P, i32, _P, _P]),
         "nls_guess_counts": (ctypes.c_int, [_P, ctypes.POINTER(i64), ctypes.POINTER(i64)]),
         "nls_guess_set_smoothing": (ctypes.c_int, [_P, i32, ctypes.c_double]),
+        "nls_set_coefficients": (ctypes.c_int, [_P, _P, _P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -340,6 +341,12 @@ class Solver:
         n = ctypes.c_int32()
         self._check(self.lib.nls_get_kernel_stats(self.h, cap, arr, ctypes.byref(n)), "nls_get_kernel_stats")
         return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].total_ms)) for i in range(n.value)}
+
+    def set_coefficients(self, k_elem=None, f_elem=None):
+        """New per-element k and f (diffusion), keeping the maps of the current setup."""
+        k = None if k_elem is None else np.ascontiguousarray(k_elem, dtype=np.float64)
+        f = None if f_elem is None else np.ascontiguousarray(f_elem, dtype=np.float64)
+        self._check(self.lib.nls_set_coefficients(self.h, _ptr(k), _ptr(f)), "nls_set_coefficients")
 
     def tuning(self) -> dict:
         """CTA sizes in use (autotuned or fixed) and the number of captured GMRES iteration graphs."""

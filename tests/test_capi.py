@@ -60,6 +60,23 @@ def test_argument_errors(nls):
         nls.make_solver(bad, coupling="one", setup="host")
 
 
+def test_set_coefficients_validation(nls):
+    p = I.diffusion_c1()
+    s = nls.make_solver(p, coupling="one", setup="host")
+    ne = p.conn.shape[0]
+    s.set_coefficients(np.full(ne, 2.0), np.full(ne, 0.5))  # host-only context: accepted
+    with pytest.raises(nls.NLSError):
+        s.set_coefficients(np.full(ne, -1.0), None)
+    bad = np.full(ne, 1.0)
+    bad[3] = np.nan
+    with pytest.raises(nls.NLSError):
+        s.set_coefficients(None, bad)
+    q = I.neohooke_problem(8, I.brick_partition(8, 2, 2, 5), 4, 1, 1.0)
+    t = nls.make_solver(q, coupling="one", setup="host")
+    with pytest.raises(nls.NLSError):
+        t.set_coefficients(np.full(q.conn.shape[0], 1.0), None)
+
+
 CASES = {
     "c1_boxes_overlap1": lambda: I.diffusion_c1(),
     "bricks_overlap2": lambda: I.diffusion_problem(48, I.brick_partition(48, 4, 4, 7), 16, 2),

@@ -9,6 +9,8 @@ autotuner of the CTA sizes.
   with the fixed choice within the FP32-factor bound of the solution parity tests (1e-6
   relative), and the choice must be one of the candidates.
 * Each path converges to the oracle's solution of F(u) = 0 (Eq. 3) on the same problem.
+* Swapping the coefficients k, f of Eq. 1 on a set-up context (nls_set_coefficients) gives the
+  same solution, bit for bit, as a context set up for those coefficients from the start.
 """
 import numpy as np
 import pytest
@@ -92,3 +94,17 @@ def test_graph_path_matches_oracle_solution(nls):
     assert s.tuning()["graphs_captured"] > 0
     uo, _ = S.plain_newton(p, tol=1e-14)
     assert np.linalg.norm(u - uo) <= 1e-8 * np.linalg.norm(uo)
+
+
+def test_set_coefficients_matches_fresh_setup(nls):
+    n, per = 64, 4
+    k1, f1 = I.c4_elem_coefficients(7, n)
+    fresh = nls.make_solver(I.diffusion_c4(7, n=n, per_side=per), coupling="hybrid", outer_atol=1e-12)
+    u1, r1 = fresh.solve()
+    reused = nls.make_solver(I.diffusion_c4(8, n=n, per_side=per), coupling="hybrid", outer_atol=1e-12)
+    reused.solve()
+    reused.set_coefficients(k1, f1)
+    u2, r2 = reused.solve()
+    assert r1.status == 0 and r2.status == 0
+    assert np.array_equal(u1, u2)
+    assert np.array_equal(fresh.coarse_basis(), reused.coarse_basis())
