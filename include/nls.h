@@ -95,6 +95,14 @@ typedef struct nls_options {
                                  the current point only when a step contracts ||P_0^T F|| by less
                                  than half or fails the line search; 0: a fresh A_0 every coarse
                                  step.  The stopping test (inner_rtol, inner_atol) is the same. */
+  int32_t local_reuse;        /* 1 (default): inside nls_solve, from the second F_x evaluation
+                                 on, a subdomain whose previous local solve succeeded starts
+                                 with chord steps -- Newton steps with the factors (and local
+                                 Jacobian) of its previous converged state, which the tangent
+                                 kept -- until a step contracts the local residual by less than
+                                 a factor 10 or fails the line search; then the Jacobian is
+                                 formed at the current state.  The stopping test is the same;
+                                 nls_eval_Fx never reuses.  0: a fresh Jacobian every step. */
   int32_t autotune;           /* 1: on the first use, time the batched local Newton kernel with
                                  128- and 256-thread CTAs, the tangent kernel with CTA sizes
                                  from 32 + b to 256 and the coarse band factorization with 256,
@@ -120,6 +128,8 @@ typedef struct nls_report {
   double time_gmres_s;            /* GMRES incl. tangent applications ("GMRES") */
   double time_other_s;            /* the rest ("Other") */
   int64_t kernel_launches;        /* kernels launched by this call */
+  int64_t local_chord_steps;      /* of subdomain_newton_steps, those taken with stored factors
+                                     (no Jacobian assembly or factorization; local_reuse) */
 } nls_report;
 
 typedef struct nls_ctx nls_ctx;

@@ -47,6 +47,7 @@ void nls_options_default(nls_options* o) {
   o->threads_per_block = 0;
   o->cuda_graphs = 1;
   o->coarse_reuse = 1;
+  o->local_reuse = 1;
   o->autotune = 0;
   o->verbose = 0;
 }
@@ -218,8 +219,8 @@ int nls_set_options(nls_ctx* ctx, const nls_options* o) {
   if (o->threads_per_block != 0 && (o->threads_per_block < 64 || o->threads_per_block > 256 || o->threads_per_block % 32))
     return fail(ctx, NLS_E_ARG, "threads_per_block must be 0 or a multiple of 32 in [64, 256]");
   if ((o->cuda_graphs != 0 && o->cuda_graphs != 1) || (o->autotune != 0 && o->autotune != 1) ||
-      (o->coarse_reuse != 0 && o->coarse_reuse != 1))
-    return fail(ctx, NLS_E_ARG, "cuda_graphs, coarse_reuse and autotune must be 0 or 1");
+      (o->coarse_reuse != 0 && o->coarse_reuse != 1) || (o->local_reuse != 0 && o->local_reuse != 1))
+    return fail(ctx, NLS_E_ARG, "cuda_graphs, coarse_reuse, local_reuse and autotune must be 0 or 1");
   if (ctx->c.is_setup && (o->local_precision != ctx->c.opt.local_precision ||
                           o->coarse_precision != ctx->c.opt.coarse_precision))
     return fail(ctx, NLS_E_ARG, "the factor precisions are fixed by nls_setup; set them before it");

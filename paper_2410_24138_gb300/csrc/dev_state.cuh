@@ -93,6 +93,8 @@ struct Dev {
   double* gpart = nullptr;              // GEMV chunk partials
   bool ainv_valid = false;
   bool coarse_fact_valid = false;  // the coarse band factors hold A_0 at some earlier point
+  bool local_factors_valid = false;  // the local factors hold the previous evaluation's tangent factors
+  bool local_reuse_active = false;   // chord steps allowed (inside nls_solve with local_reuse)
   int clock_khz = 1;
   double* h_scal = nullptr;  // pinned
   int m = 0;                 // GMRES restart length allocated

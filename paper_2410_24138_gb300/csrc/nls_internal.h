@@ -59,7 +59,7 @@ struct DeviceLocalSet {
   void* dinv = nullptr;            // packed triangular-solve operands of the factors
   double* w = nullptr;             // local states, concatenated (total_n)
   double* work = nullptr;          // three FP64 work vectors per subdomain (3 x total_n)
-  int32_t *its = nullptr, *status = nullptr;
+  int32_t *its = nullptr, *status = nullptr, *chord = nullptr;
   int32_t* order = nullptr;        // processing order (longest first)
   int32_t* queue = nullptr;        // persistent work counter
 };

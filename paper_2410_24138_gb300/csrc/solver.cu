@@ -59,6 +59,8 @@ struct LocalArgs {
   double* work;        // three per-subdomain FP64 vectors (vec_off), `work_stride` apart
   int64_t work_stride;
   int32_t *its, *status;
+  int32_t* chord;  // per subdomain: steps of the last launch taken with the stored factors
+  int reuse;       // 1: a subdomain whose previous status is OK may start with chord steps
   const int32_t* order;
   int32_t* queue;
   const double *geom, *kcoef, *fext;
@@ -425,22 +427,28 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 128 ? 4 : 1)) k_local_newton(Lo
       __syncthreads();
       if (tid == 0 && A.accepted) A.accepted[sub] = take ? 1 : 0;
     }
-    int its = 0, status = ST_OK;
+    int its = 0, status = ST_OK, chord = 0;
     if (!isfinite(rn)) status = ST_NONFINITE;
+    // the stored factors (and local Jacobian) are those of this subdomain's converged state of
+    // the previous F_x evaluation when that evaluation succeeded here: chord steps with them
+    // until one contracts the residual by less than a factor 10 or fails the line search
+    bool stored = A.reuse && A.status[sub] == ST_OK;
     mark(0);
     while (status == ST_OK && rn > tol) {
       if (its >= A.maxit) {
         status = ST_MAXIT;
         break;
       }
-      local_jacobian<LAW, JT, FT>(A, m, xt, csr, F);
-      mark(1);
-      if (dev::band_lu_inplace<FT>(n, m.b, F, win, rp, flag)) {
-        status = ST_PIVOT;
-        break;
+      if (!stored) {
+        local_jacobian<LAW, JT, FT>(A, m, xt, csr, F);
+        mark(1);
+        if (dev::band_lu_inplace<FT>(n, m.b, F, win, rp, flag)) {
+          status = ST_PIVOT;
+          break;
+        }
+        dev::band_pack_solve<FT>(n, m.b, F, Dv, win, inv_warps);
+        mark(2);
       }
-      dev::band_pack_solve<FT>(n, m.b, F, Dv, win, inv_warps);
-      mark(2);
       local_solve<FT, false>(A, m, rowptr, colidx, csr, Dv, r, rn, s, res, yv, red);
       mark(3);
       for (int a = tid; a < n; a += blockDim.x) wb[a] = xt[a];
@@ -461,13 +469,22 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 128 ? 4 : 1)) k_local_newton(Lo
         }
         alpha *= 0.5;
       }
-      ++its;
       mark(4);
       if (!accepted) {
         for (int a = tid; a < n; a += blockDim.x) xt[a] = wb[a];
         __syncthreads();
+        if (stored) {  // retry the step with the Jacobian at the current state
+          stored = false;
+          continue;
+        }
+        ++its;
         status = ST_LS;
         break;
+      }
+      ++its;
+      if (stored) {
+        ++chord;
+        if (rtn > 0.1 * rn) stored = false;
       }
       for (int a = tid; a < n; a += blockDim.x) r[a] = racc[a];
       __syncthreads();
@@ -489,6 +506,7 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 128 ? 4 : 1)) k_local_newton(Lo
     }
     if (tid == 0) {
       A.its[sub] = its;
+      if (A.chord) A.chord[sub] = chord;
       A.status[sub] = status;
     }
     __syncthreads();
@@ -992,6 +1010,8 @@ LocalArgs make_args(const Context& c, const LocalSet& hs, const DeviceLocalSet& 
   A.work_stride = hs.total_n;
   A.its = ds.its;
   A.status = ds.status;
+  A.chord = ds.chord;
+  A.reuse = 0;
   A.order = ds.order;
   A.queue = ds.queue;
   A.geom = D.geom;
@@ -1134,6 +1154,7 @@ void launch_local_newton(Context& c, const double* x, double* out, double load, 
   A.guess_omega = g.omega;
   A.want_tangent = want_tangent ? 1 : 0;
   A.phase = D.prof ? D.phase : nullptr;
+  A.reuse = (D.local_reuse_active && D.local_factors_valid) ? 1 : 0;
   CK(cudaMemsetAsync(D.ov.queue, 0, sizeof(int32_t), D.s));
   dispatch_local_newton(c, c.ov, A, local_threads(c));
 }
@@ -1417,6 +1438,7 @@ void upload_set(Dev& D, const LocalSet& h, DeviceLocalSet& d, bool fp32_factor, 
   d.w = D.alloc<double>(h.total_n);
   d.work = D.alloc<double>(3 * (size_t)h.total_n);
   d.its = D.alloc<int32_t>(h.count);
+  d.chord = D.alloc<int32_t>(h.count);
   d.status = D.alloc<int32_t>(h.count);
   // longest first: cost ~ n b^2
   std::vector<int32_t> order(h.count);
@@ -1655,6 +1677,7 @@ struct FxInfo {
   int coarse_its = 0;
   int coarse_status = ST_OK;
   int64_t local_its = 0;
+  int64_t local_chord = 0;
   int local_failures = 0;
   int first_failed = -1;
   bool pivot_failure = false;
@@ -1679,14 +1702,17 @@ FxInfo evaluate_Fx(Context& c, const double* u, double load, double* t_inner, do
   const GuessProposal proposal = guess_propose(c, point, load);
   tune_local_newton(c, point, D.Fx, load, proposal);
   launch_local_newton(c, point, D.Fx, load, proposal, true);
+  D.local_factors_valid = true;  // every subdomain with status OK now holds its tangent factors
   guess_after_local(c, point, load, proposal.x != nullptr);
-  std::vector<int32_t> its(c.ov.count), st(c.ov.count);
+  std::vector<int32_t> its(c.ov.count), st(c.ov.count), ch(c.ov.count);
   CK(cudaMemcpyAsync(its.data(), D.ov.its, sizeof(int32_t) * its.size(), cudaMemcpyDeviceToHost, D.s));
   CK(cudaMemcpyAsync(st.data(), D.ov.status, sizeof(int32_t) * st.size(), cudaMemcpyDeviceToHost, D.s));
+  CK(cudaMemcpyAsync(ch.data(), D.ov.chord, sizeof(int32_t) * ch.size(), cudaMemcpyDeviceToHost, D.s));
   sync(D);
   auto t2 = std::chrono::steady_clock::now();
   for (int i = 0; i < c.ov.count; ++i) {
     info.local_its += its[i];
+    info.local_chord += ch[i];
     if (st[i] != ST_OK) {
       info.local_failures += 1;
       if (info.first_failed < 0) info.first_failed = i;
@@ -1915,6 +1941,12 @@ int solve(Context& c, double* u_user, int u_dev, nls_report* rep) {
     // iterations of this call, never from an earlier one
     D.coarse_fact_valid = false;
     D.ainv_valid = false;
+    D.local_factors_valid = false;
+    D.local_reuse_active = c.opt.local_reuse != 0;
+    struct ReuseScope {  // chord steps only inside this solve, never in a later nls_eval_Fx
+      Dev& d;
+      ~ReuseScope() { d.local_reuse_active = false; }
+    } reuse_scope{D};
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
@@ -1942,6 +1974,7 @@ int solve(Context& c, double* u_user, int u_dev, nls_report* rep) {
         }
         FxInfo fi = evaluate_Fx(c, D.u, load, &t_inner, &t_coarse);
         rp.subdomain_newton_steps += fi.local_its;
+        rp.local_chord_steps += fi.local_chord;
         rp.coarse_newton_steps += fi.coarse_its;
         rp.local_failures += fi.local_failures;
         if (rp.first_failed_subdomain < 0) rp.first_failed_subdomain = fi.first_failed;

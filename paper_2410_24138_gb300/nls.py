@@ -34,7 +34,7 @@ class Options(ctypes.Structure):
                 ("ir_rtol", ctypes.c_double), ("ir_max_sweeps", ctypes.c_int32),
                 ("threads_per_block", ctypes.c_int32), ("verbose", ctypes.c_int32),
                 ("profile_kernels", ctypes.c_int32), ("cuda_graphs", ctypes.c_int32),
-                ("coarse_reuse", ctypes.c_int32), ("autotune", ctypes.c_int32)]
+                ("coarse_reuse", ctypes.c_int32), ("local_reuse", ctypes.c_int32), ("autotune", ctypes.c_int32)]
 
 
 class Report(ctypes.Structure):
@@ -44,7 +44,8 @@ class Report(ctypes.Structure):
                 ("first_failed_subdomain", ctypes.c_int32), ("final_residual", ctypes.c_double),
                 ("time_total_s", ctypes.c_double), ("time_inner_s", ctypes.c_double),
                 ("time_coarse_s", ctypes.c_double), ("time_gmres_s", ctypes.c_double),
-                ("time_other_s", ctypes.c_double), ("kernel_launches", ctypes.c_int64)]
+                ("time_other_s", ctypes.c_double), ("kernel_launches", ctypes.c_int64),
+                ("local_chord_steps", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}

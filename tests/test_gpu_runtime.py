@@ -11,6 +11,10 @@ autotuner of the CTA sizes.
 * Each path converges to the oracle's solution of F(u) = 0 (Eq. 3) on the same problem.
 * Swapping the coefficients k, f of Eq. 1 on a set-up context (nls_set_coefficients) gives the
   same solution, bit for bit, as a context set up for those coefficients from the start.
+* Reusing the stored local factors for chord steps (local_reuse) and the previous tangent phase's
+  coarse factorization (coarse_reuse) only changes how the local and coarse problems are solved
+  to their stopping tests: the converged solution agrees with the fresh-Jacobian iteration within
+  the FP32-path bound (1e-6) and solves F(u) = 0 of the oracle to the outer tolerance.
 """
 import numpy as np
 import pytest
@@ -108,3 +112,16 @@ def test_set_coefficients_matches_fresh_setup(nls):
     assert r1.status == 0 and r2.status == 0
     assert np.array_equal(u1, u2)
     assert np.array_equal(fresh.coarse_basis(), reused.coarse_basis())
+
+
+def test_factor_reuse_keeps_the_solution(nls):
+    p = I.neohooke_problem(24, I.brick_partition(24, 2, 3, 5), 6, 2, traction_max=4.0, load_steps=2)
+    a = nls.make_solver(p, coupling="hybrid", outer_atol=1e-11, local_reuse=0, coarse_reuse=0)
+    ua, ra = a.solve()
+    b = nls.make_solver(p, coupling="hybrid", outer_atol=1e-11, local_reuse=1, coarse_reuse=1)
+    ub, rb = b.solve()
+    assert ra.status == 0 and rb.status == 0
+    assert ra.local_chord_steps == 0 and rb.local_chord_steps > 0
+    assert np.linalg.norm(ub - ua) <= 1e-6 * np.linalg.norm(ua)
+    F = fem.global_residual(fem.Model(p), ub)
+    assert np.linalg.norm(F) < 1e-8
