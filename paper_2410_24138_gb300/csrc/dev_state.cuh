@@ -107,6 +107,8 @@ struct Dev {
   double newton_ms[2] = {0.0, 0.0};
   // GMRES iteration graphs, one per Krylov index, valid while `graph_key` matches
   cudaStream_t cap = nullptr;  // private stream the graphs are captured on
+  cudaStream_t s2 = nullptr;   // second stream: the tangent phase's coarse work
+  cudaEvent_t ev_u0 = nullptr, ev_coarse = nullptr;
   std::vector<cudaGraphExec_t> it_exec;
   std::vector<int64_t> it_launches;
   std::string graph_key;
@@ -148,7 +150,7 @@ struct Dev {
   }
   void prof_flush() {
     if (!ev_used) return;
-    CK(cudaStreamSynchronize(s));
+    CK(cudaDeviceSynchronize());  // events may sit on the second stream too (profiling mode only)
     for (size_t i = 0; i < ev_used; ++i) {
       float ms = 0.f;
       CK(cudaEventElapsedTime(&ms, evs[i].a, evs[i].b));

@@ -1266,7 +1266,22 @@ size_t coarse_factor_smem(const Context& c, bool f32) {
 }
 
 // A_0(x) = P_0^T DF(x) P_0 -> band -> factor.  Returns false on a bad pivot.
+void coarse_matrix_launch(Context& c, const double* x);
+
+// Reads the coarse factorization's status word (synchronises the stream).
+bool coarse_status_ok(Dev& D) {
+  int32_t st = 0;
+  CK(cudaMemcpyAsync(&st, D.cstatus, sizeof(int32_t), cudaMemcpyDeviceToHost, D.s));
+  sync(D);
+  return st == ST_OK;
+}
+
 bool coarse_matrix(Context& c, const double* x) {
+  coarse_matrix_launch(c, x);
+  return coarse_status_ok(*c.dev);
+}
+
+void coarse_matrix_launch(Context& c, const double* x) {
   Dev& D = *c.dev;
   LocalArgs A = coarse_args(c);
   A.x = x;
@@ -1303,10 +1318,6 @@ bool coarse_matrix(Context& c, const double* x) {
     D.coarse_tuned = true;
   }
   factor(D.coarse_T);
-  int32_t st = 0;
-  CK(cudaMemcpyAsync(&st, D.cstatus, sizeof(int32_t), cudaMemcpyDeviceToHost, D.s));
-  sync(D);
-  return st == ST_OK;
 }
 
 void coarse_solve(Context& c, const double* g, double* z) {
@@ -1655,6 +1666,9 @@ void device_free(Context& c) {
   guess_free(c);
   D.reset_graphs();
   if (D.cap) cudaStreamDestroy(D.cap);
+  if (D.s2) cudaStreamSynchronize(D.s2), cudaStreamDestroy(D.s2);
+  if (D.ev_u0) cudaEventDestroy(D.ev_u0);
+  if (D.ev_coarse) cudaEventDestroy(D.ev_coarse);
   for (void* p : D.allocs)
     if (p) cudaFree(p);
   if (D.h_scal) cudaFreeHost(D.h_scal);
@@ -1683,6 +1697,28 @@ struct FxInfo {
   bool pivot_failure = false;
 };
 
+// The tangent phase's coarse work at u_0: DF(u_0) for the coarse term of Eq. 12, A_0(u_0) and
+// its factors, and (N_0 <= 8192) the explicit inverse the GMRES iterations' coarse solves use.
+// Issued on D.s; the factorization's status is read by the caller.
+void tangent_coarse_launch(Context& c) {
+  Dev& D = *c.dev;
+  global_jacobian(c, D.u0);
+  D.ainv_valid = false;
+  coarse_matrix_launch(c, D.u0);
+  if (D.ainv) {
+    const int N0 = c.cs.N0;
+    const size_t sm = (2 * sizeof(double) + (fp32_coarse(c) ? sizeof(float) : sizeof(double))) * N0 + 40 * sizeof(double);
+    const int T = std::max(64, (32 + c.cs.b0 + 31) / 32 * 32);
+    const int grid = std::min(N0, D.nsm * 8);
+    if (fp32_coarse(c))
+      LAUNCH(D, k_coarse_inverse<float>, grid, T, sm, N0, c.cs.b0, D.A0, (const float*)D.A0f,
+             (const float*)D.A0dinv, D.ainv, c.opt.ir_rtol, c.opt.ir_max_sweeps);
+    else
+      LAUNCH(D, k_coarse_inverse<double>, grid, T, sm, N0, c.cs.b0, D.A0, (const double*)D.A0f,
+             (const double*)D.A0dinv, D.ainv, c.opt.ir_rtol, c.opt.ir_max_sweeps);
+  }
+}
+
 // F_x(u) into D.Fx; prepares everything the tangent needs.
 FxInfo evaluate_Fx(Context& c, const double* u, double load, double* t_inner, double* t_coarse) {
   Dev& D = *c.dev;
@@ -1699,6 +1735,27 @@ FxInfo evaluate_Fx(Context& c, const double* u, double load, double* t_inner, do
   }
   sync(D);
   auto t1 = std::chrono::steady_clock::now();
+  // The tangent phase's coarse work depends on u_0 only: it runs on a second stream, issued
+  // before the batched local solves so that its single-CTA factorization overlaps them.
+  const bool two_level = cp != NLS_COUPLING_ONE;
+  if (two_level) {
+    if (!D.s2) {
+      CK(cudaStreamCreateWithFlags(&D.s2, cudaStreamNonBlocking));
+      CK(cudaEventCreateWithFlags(&D.ev_u0, cudaEventDisableTiming));
+      CK(cudaEventCreateWithFlags(&D.ev_coarse, cudaEventDisableTiming));
+    }
+    CK(cudaEventRecord(D.ev_u0, D.s));
+    CK(cudaStreamWaitEvent(D.s2, D.ev_u0, 0));
+    std::swap(D.s, D.s2);
+    try {
+      tangent_coarse_launch(c);
+    } catch (...) {
+      std::swap(D.s, D.s2);
+      throw;
+    }
+    CK(cudaEventRecord(D.ev_coarse, D.s));
+    std::swap(D.s, D.s2);
+  }
   const GuessProposal proposal = guess_propose(c, point, load);
   tune_local_newton(c, point, D.Fx, load, proposal);
   launch_local_newton(c, point, D.Fx, load, proposal, true);
@@ -1719,27 +1776,14 @@ FxInfo evaluate_Fx(Context& c, const double* u, double load, double* t_inner, do
       if (st[i] == ST_PIVOT) info.pivot_failure = true;
     }
   }
-  if (cp != NLS_COUPLING_ONE) {
-    // F_x += P0 T_0(u); the coarse part of the tangent at u_0 = u - P0 T_0(u)
+  if (two_level) {
+    // F_x += P0 T_0(u); the coarse part of the tangent at u_0 = u - P0 T_0(u) comes from the
+    // second stream
     LAUNCH(D, k_p0_apply, grid_for(c.N), 256, 0, c.N, D.p0_rowptr, D.p0_col, D.p0_val, D.c, 1.0, D.Fx, 1.0, D.Fx);
-    global_jacobian(c, D.u0);
-    D.ainv_valid = false;
-    D.coarse_fact_valid = coarse_matrix(c, D.u0);
+    CK(cudaStreamWaitEvent(D.s, D.ev_coarse, 0));
+    D.coarse_fact_valid = coarse_status_ok(D);
     if (!D.coarse_fact_valid) info.pivot_failure = true;
-    // the tangent's coarse solves (one per GMRES iteration) reuse A_0(u_0): form its inverse
-    else if (D.ainv) {
-      const int N0 = c.cs.N0;
-      const size_t sm = (2 * sizeof(double) + (fp32_coarse(c) ? sizeof(float) : sizeof(double))) * N0 + 40 * sizeof(double);
-      const int T = std::max(64, (32 + c.cs.b0 + 31) / 32 * 32);
-      const int grid = std::min(N0, D.nsm * 8);
-      if (fp32_coarse(c))
-        LAUNCH(D, k_coarse_inverse<float>, grid, T, sm, N0, c.cs.b0, D.A0, (const float*)D.A0f,
-               (const float*)D.A0dinv, D.ainv, c.opt.ir_rtol, c.opt.ir_max_sweeps);
-      else
-        LAUNCH(D, k_coarse_inverse<double>, grid, T, sm, N0, c.cs.b0, D.A0, (const double*)D.A0f,
-               (const double*)D.A0dinv, D.ainv, c.opt.ir_rtol, c.opt.ir_max_sweeps);
-      D.ainv_valid = true;
-    }
+    D.ainv_valid = D.coarse_fact_valid && D.ainv != nullptr;
   }
   sync(D);
   auto t3 = std::chrono::steady_clock::now();
