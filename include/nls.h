@@ -110,6 +110,10 @@ typedef struct nls_options {
                                  fastest (nls_get_tuning).  The choice changes the order of
                                  floating-point reductions only.  0 (default): the library's
                                  fixed choice or threads_per_block. */
+  int32_t l2_prefetch;        /* the triangular solves with the packed factors (local Newton
+                                 steps, tangent applications, coarse solves) prefetch the
+                                 operands of the 32-row block this many blocks ahead into L2;
+                                 0 = off, at most 64 (default 4).  Changes no result. */
 } nls_options;
 
 /* Per-solve report. */

@@ -641,9 +641,13 @@ __device__ void band_pack_solve(int n, int b, const FT* __restrict__ F, FT* __re
 // the next block are loaded into registers while the current one is applied (2 BS operand
 // registers per thread: for kernels with few CTAs per SM, where nothing else hides the load
 // latency); without PF each block's operands are loaded at the top of its step (BS registers,
-// for kernels that keep enough CTAs resident).  Needs blockDim.x >= 32 + b.
+// for kernels that keep enough CTAs resident).  With l2d > 0 the operands of the block l2d steps
+// ahead are prefetched into L2 (one 128-byte line per thread: the diagonal-block inverse by the
+// first BS^2 sizeof(FT) / 128 threads, the b coupling lines by the coupling threads), so that
+// the register loads of the current and next block wait for L2 rather than HBM.  Needs
+// blockDim.x >= 32 + b.
 template <typename FT, bool PF>
-__device__ void band_solve_packed(int n, int b, const FT* __restrict__ P, FT* y) {
+__device__ void band_solve_packed(int n, int b, const FT* __restrict__ P, FT* y, int l2d = 0) {
   constexpr int BS = SolveBlock<FT>::BS;
   constexpr int NB = PF ? 2 : 1;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -664,10 +668,21 @@ __device__ void band_solve_packed(int n, int b, const FT* __restrict__ P, FT* y)
       for (int j = 0; j < BS; ++j) buf[which][j] = Pt[oc + j * b + r];
     }
   };
+  constexpr int LINE = 128 / (int)sizeof(FT);            // entries per 128-byte line
+  constexpr int DLINES = BS * BS * (int)sizeof(FT) / 128;  // lines of one diagonal-block inverse
+  auto l2pf = [&](int t, int64_t od, int64_t oc) {
+    const FT* Pt = P + (int64_t)t * PB;
+    const FT* a = nullptr;
+    if (tid < DLINES) a = Pt + od + (int64_t)tid * LINE;
+    else if (offd) a = Pt + oc + (int64_t)r * LINE;
+    if (a) asm volatile("prefetch.global.L2 [%0];" ::"l"(__cvta_generic_to_global(a)));
+  };
   // forward: diag lanes read inv(L_tt), coupling threads read CL
   if (PF && nblk > 0) load(0, 0, oL, oCL);
+  for (int q = 1; q < l2d && q < nblk; ++q) l2pf(q, oL, oCL);
   for (int t = 0; t < nblk; ++t) {
     const int k0 = t * BS, kb = min(BS, n - k0);
+    if (l2d > 0 && t + l2d < nblk) l2pf(t + l2d, oL, oCL);
     if (PF) {
       if (t + 1 < nblk) load(t + 1, NB - 1, oL, oCL);
     } else {
@@ -707,8 +722,10 @@ __device__ void band_solve_packed(int n, int b, const FT* __restrict__ P, FT* y)
   }
   // backward: diag lanes read inv(U_tt), coupling threads read CU
   if (PF && nblk > 0) load(nblk - 1, 0, oU, oCU);
+  for (int q = 1; q < l2d && nblk - 1 - q >= 0; ++q) l2pf(nblk - 1 - q, oU, oCU);
   for (int t = nblk - 1; t >= 0; --t) {
     const int k0 = t * BS, kb = min(BS, n - k0);
+    if (l2d > 0 && t - l2d >= 0) l2pf(t - l2d, oU, oCU);
     if (PF) {
       if (t > 0) load(t - 1, NB - 1, oU, oCU);
     } else {

@@ -68,6 +68,7 @@ struct LocalArgs {
   int ndof, nen, count, max_n, max_nt, max_b;
   double rtol, atol, armijo, ir_rtol;
   int maxit, ls_trials, ir_max;
+  int l2_dist;            // L2 prefetch distance of the triangular solves (blocks; 0 = off)
   const double* x;        // evaluation point (global)
   double* out;            // F_x: owned entries receive x - w
   const double* guess;    // optional start states (concatenated local vectors)
@@ -305,7 +306,7 @@ __device__ int local_solve(const LocalArgs& A, const SubMeta& m, const int32_t* 
   const int n = m.n;
   for (int a = threadIdx.x; a < n; a += blockDim.x) yv[a] = (FT)rhs[a];
   __syncthreads();
-  dev::band_solve_packed<FT, PF>(n, m.b, Dv, yv);
+  dev::band_solve_packed<FT, PF>(n, m.b, Dv, yv, A.l2_dist);
   for (int a = threadIdx.x; a < n; a += blockDim.x) s[a] = (double)yv[a];
   __syncthreads();
   int sweeps = 0;
@@ -325,7 +326,7 @@ __device__ int local_solve(const LocalArgs& A, const SubMeta& m, const int32_t* 
       if (!(rn > A.ir_rtol * rhs_norm)) break;
       for (int a = threadIdx.x; a < n; a += blockDim.x) yv[a] = (FT)res[a];
       __syncthreads();
-      dev::band_solve_packed<FT, PF>(n, m.b, Dv, yv);
+      dev::band_solve_packed<FT, PF>(n, m.b, Dv, yv, A.l2_dist);
       for (int a = threadIdx.x; a < n; a += blockDim.x) s[a] += (double)yv[a];
       __syncthreads();
       ++sweeps;
@@ -683,7 +684,7 @@ __global__ void __launch_bounds__(1024) k_coarse_factor(int N0, int b0, const do
 // Stored transposed (AinvT[col][row]) so that the GEMV below reads it coalesced.
 template <typename FT>
 __global__ void __launch_bounds__(256) k_coarse_inverse(int N0, int b0, const double* A0, const FT* F, const FT* Dinv,
-                                                         double* AinvT, double ir_rtol, int ir_max) {
+                                                         double* AinvT, double ir_rtol, int ir_max, int l2d) {
   extern __shared__ __align__(16) unsigned char smem[];
   double* z = (double*)smem;
   double* res = z + N0;
@@ -693,7 +694,7 @@ __global__ void __launch_bounds__(256) k_coarse_inverse(int N0, int b0, const do
   for (int col = blockIdx.x; col < N0; col += gridDim.x) {
     for (int a = threadIdx.x; a < N0; a += blockDim.x) y[a] = (a == col) ? (FT)1 : (FT)0;
     __syncthreads();
-    dev::band_solve_packed<FT, false>(N0, b0, Dinv, y);
+    dev::band_solve_packed<FT, false>(N0, b0, Dinv, y, l2d);
     for (int a = threadIdx.x; a < N0; a += blockDim.x) z[a] = (double)y[a];
     __syncthreads();
     if (sizeof(FT) == 4) {
@@ -712,7 +713,7 @@ __global__ void __launch_bounds__(256) k_coarse_inverse(int N0, int b0, const do
         if (!(rn > ir_rtol)) break;
         for (int a = threadIdx.x; a < N0; a += blockDim.x) y[a] = (FT)res[a];
         __syncthreads();
-        dev::band_solve_packed<FT, false>(N0, b0, Dinv, y);
+        dev::band_solve_packed<FT, false>(N0, b0, Dinv, y, l2d);
         for (int a = threadIdx.x; a < N0; a += blockDim.x) z[a] += (double)y[a];
         __syncthreads();
       }
@@ -758,7 +759,7 @@ __global__ void k_gemv_finish(int N0, int chunks, const double* part, double* z)
 template <typename FT>
 __global__ void __launch_bounds__(256) k_coarse_solve(int N0, int b0, const double* A0, const FT* F, const FT* Dinv,
                                                        const double* g, double* z, double* res, FT* y, double ir_rtol,
-                                                       int ir_max) {
+                                                       int ir_max, int l2d) {
   __shared__ double red[40];
   const int W = 2 * b0 + 1;
   double loc = 0.0;
@@ -767,7 +768,7 @@ __global__ void __launch_bounds__(256) k_coarse_solve(int N0, int b0, const doub
     loc += g[a] * g[a];
   }
   const double gn = sqrt(dev::block_sum(loc, red));
-  dev::band_solve_packed<FT, true>(N0, b0, Dinv, y);
+  dev::band_solve_packed<FT, true>(N0, b0, Dinv, y, l2d);
   for (int a = threadIdx.x; a < N0; a += blockDim.x) z[a] = (double)y[a];
   __syncthreads();
   if (sizeof(FT) == 4) {
@@ -786,7 +787,7 @@ __global__ void __launch_bounds__(256) k_coarse_solve(int N0, int b0, const doub
       if (!(rn > ir_rtol * gn)) break;
       for (int a = threadIdx.x; a < N0; a += blockDim.x) y[a] = (FT)res[a];
       __syncthreads();
-      dev::band_solve_packed<FT, true>(N0, b0, Dinv, y);
+      dev::band_solve_packed<FT, true>(N0, b0, Dinv, y, l2d);
       for (int a = threadIdx.x; a < N0; a += blockDim.x) z[a] += (double)y[a];
       __syncthreads();
     }
@@ -1034,6 +1035,7 @@ LocalArgs make_args(const Context& c, const LocalSet& hs, const DeviceLocalSet& 
   A.maxit = c.opt.inner_maxit;
   A.ls_trials = c.opt.ls_trials;
   A.ir_max = c.opt.ir_max_sweeps;
+  A.l2_dist = c.opt.l2_prefetch;
   return A;
 }
 
@@ -1330,10 +1332,12 @@ void coarse_solve(Context& c, const double* g, double* z) {
   }
   if (fp32_coarse(c))
     LAUNCH(D, k_coarse_solve<float>, 1, 256, 0, c.cs.N0, c.cs.b0, D.A0, (const float*)D.A0f,
-           (const float*)D.A0dinv, g, z, D.cres, (float*)D.cy, c.opt.ir_rtol, c.opt.ir_max_sweeps);
+           (const float*)D.A0dinv, g, z, D.cres, (float*)D.cy, c.opt.ir_rtol, c.opt.ir_max_sweeps,
+           c.opt.l2_prefetch);
   else
     LAUNCH(D, k_coarse_solve<double>, 1, 256, 0, c.cs.N0, c.cs.b0, D.A0, (const double*)D.A0f,
-           (const double*)D.A0dinv, g, z, D.cres, (double*)D.cy, c.opt.ir_rtol, c.opt.ir_max_sweeps);
+           (const double*)D.A0dinv, g, z, D.cres, (double*)D.cy, c.opt.ir_rtol, c.opt.ir_max_sweeps,
+           c.opt.l2_prefetch);
 }
 
 // x = u - P0 c
@@ -1712,10 +1716,10 @@ void tangent_coarse_launch(Context& c) {
     const int grid = std::min(N0, D.nsm * 8);
     if (fp32_coarse(c))
       LAUNCH(D, k_coarse_inverse<float>, grid, T, sm, N0, c.cs.b0, D.A0, (const float*)D.A0f,
-             (const float*)D.A0dinv, D.ainv, c.opt.ir_rtol, c.opt.ir_max_sweeps);
+             (const float*)D.A0dinv, D.ainv, c.opt.ir_rtol, c.opt.ir_max_sweeps, c.opt.l2_prefetch);
     else
       LAUNCH(D, k_coarse_inverse<double>, grid, T, sm, N0, c.cs.b0, D.A0, (const double*)D.A0f,
-             (const double*)D.A0dinv, D.ainv, c.opt.ir_rtol, c.opt.ir_max_sweeps);
+             (const double*)D.A0dinv, D.ainv, c.opt.ir_rtol, c.opt.ir_max_sweeps, c.opt.l2_prefetch);
   }
 }
 

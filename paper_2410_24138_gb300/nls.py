@@ -34,7 +34,8 @@ class Options(ctypes.Structure):
                 ("ir_rtol", ctypes.c_double), ("ir_max_sweeps", ctypes.c_int32),
                 ("threads_per_block", ctypes.c_int32), ("verbose", ctypes.c_int32),
                 ("profile_kernels", ctypes.c_int32), ("cuda_graphs", ctypes.c_int32),
-                ("coarse_reuse", ctypes.c_int32), ("local_reuse", ctypes.c_int32), ("autotune", ctypes.c_int32)]
+                ("coarse_reuse", ctypes.c_int32), ("local_reuse", ctypes.c_int32), ("autotune", ctypes.c_int32),
+                ("l2_prefetch", ctypes.c_int32)]
 
 
 class Report(ctypes.Structure):

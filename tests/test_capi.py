@@ -52,6 +52,11 @@ def test_argument_errors(nls):
         s.set_options(threads_per_block=100)
     with pytest.raises(nls.NLSError):
         s.set_options(load_steps=0)
+    with pytest.raises(nls.NLSError):
+        s.set_options(l2_prefetch=-1)
+    with pytest.raises(nls.NLSError):
+        s.set_options(l2_prefetch=65)
+    s.set_options(l2_prefetch=0)
     bad = I.diffusion_c1()
     bad.elem_to_sub = bad.elem_to_sub.copy()
     bad.elem_to_sub[:] = 0
