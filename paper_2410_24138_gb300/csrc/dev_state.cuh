@@ -89,8 +89,10 @@ struct Dev {
   double *V = nullptr, *partial = nullptr, *scal = nullptr, *coef = nullptr;
   int* bad = nullptr;
   unsigned long long* phase = nullptr;  // k_local_newton phase clocks (profiling)
-  double* ainv = nullptr;               // explicit A_0^-1 (transposed) for the tangent phase
+  void* ainv = nullptr;                 // explicit A_0^-1 (transposed, factor precision) for the tangent phase
   double* gpart = nullptr;              // GEMV chunk partials
+  double* cpart = nullptr;              // refinement of the explicit-inverse solves: per-CTA partial norms
+  int* cflag = nullptr;                 // [0] refinement converged, [1] ticket counter
   bool ainv_valid = false;
   bool coarse_fact_valid = false;  // the coarse band factors hold A_0 at some earlier point
   bool local_factors_valid = false;  // the local factors hold the previous evaluation's tangent factors

@@ -644,10 +644,10 @@ __device__ void band_pack_solve(int n, int b, const FT* __restrict__ F, FT* __re
 // for kernels that keep enough CTAs resident).  With l2d > 0 the operands of the block l2d steps
 // ahead are prefetched into L2 (one 128-byte line per thread: the diagonal-block inverse by the
 // first BS^2 sizeof(FT) / 128 threads, the b coupling lines by the coupling threads), so that
-// the register loads of the current and next block wait for L2 rather than HBM.  Needs
-// blockDim.x >= 32 + b.
+// the register loads of the current and next block wait for L2 rather than HBM.  The forward
+// sweep starts at block t0: y must vanish in the rows before it.  Needs blockDim.x >= 32 + b.
 template <typename FT, bool PF>
-__device__ void band_solve_packed(int n, int b, const FT* __restrict__ P, FT* y, int l2d = 0) {
+__device__ void band_solve_packed(int n, int b, const FT* __restrict__ P, FT* y, int l2d = 0, int t0 = 0) {
   constexpr int BS = SolveBlock<FT>::BS;
   constexpr int NB = PF ? 2 : 1;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -678,9 +678,9 @@ __device__ void band_solve_packed(int n, int b, const FT* __restrict__ P, FT* y,
     if (a) asm volatile("prefetch.global.L2 [%0];" ::"l"(__cvta_generic_to_global(a)));
   };
   // forward: diag lanes read inv(L_tt), coupling threads read CL
-  if (PF && nblk > 0) load(0, 0, oL, oCL);
-  for (int q = 1; q < l2d && q < nblk; ++q) l2pf(q, oL, oCL);
-  for (int t = 0; t < nblk; ++t) {
+  if (PF && t0 < nblk) load(t0, 0, oL, oCL);
+  for (int q = t0 + 1; q < t0 + l2d && q < nblk; ++q) l2pf(q, oL, oCL);
+  for (int t = t0; t < nblk; ++t) {
     const int k0 = t * BS, kb = min(BS, n - k0);
     if (l2d > 0 && t + l2d < nblk) l2pf(t + l2d, oL, oCL);
     if (PF) {

@@ -679,46 +679,22 @@ __global__ void __launch_bounds__(1024) k_coarse_factor(int N0, int b0, const do
   if (threadIdx.x == 0) *status = bad ? ST_PIVOT : ST_OK;
 }
 
-// Columns of A_0^-1 (one CTA per column, shared-memory vectors): the band factors solve
-// A_0 z = e_col, FP64 refinement against the band A_0 brings every column to FP64 accuracy.
-// Stored transposed (AinvT[col][row]) so that the GEMV below reads it coalesced.
+// Columns of A_0^-1 from the band factors (one CTA per column, the solve vector in shared
+// memory): one solve A_0 z = e_col in the factors' precision (the forward sweep starts at the
+// block of `col`, above which e_col and z vanish), stored in that precision and transposed
+// (AinvT[col][row]) so that the GEMV below reads it coalesced.  FP32 columns are refined where
+// they are applied (coarse_solve): the FP64 residual of one vector costs N0 (2 b0 + 1)
+// multiply-adds, that of every column of the inverse N0 times as many.
 template <typename FT>
-__global__ void __launch_bounds__(256) k_coarse_inverse(int N0, int b0, const double* A0, const FT* F, const FT* Dinv,
-                                                         double* AinvT, double ir_rtol, int ir_max, int l2d) {
+__global__ void __launch_bounds__(256) k_coarse_inverse(int N0, int b0, const FT* Dinv, FT* AinvT, int l2d) {
   extern __shared__ __align__(16) unsigned char smem[];
-  double* z = (double*)smem;
-  double* res = z + N0;
-  double* red = res + N0;
-  FT* y = (FT*)(red + 40);
-  const int W = 2 * b0 + 1;
+  FT* y = (FT*)smem;
+  constexpr int BS = dev::SolveBlock<FT>::BS;
   for (int col = blockIdx.x; col < N0; col += gridDim.x) {
     for (int a = threadIdx.x; a < N0; a += blockDim.x) y[a] = (a == col) ? (FT)1 : (FT)0;
     __syncthreads();
-    dev::band_solve_packed<FT, false>(N0, b0, Dinv, y, l2d);
-    for (int a = threadIdx.x; a < N0; a += blockDim.x) z[a] = (double)y[a];
-    __syncthreads();
-    if (sizeof(FT) == 4) {
-      for (int sw = 0; sw < ir_max; ++sw) {
-        double l2 = 0.0;
-        for (int a = threadIdx.x; a < N0; a += blockDim.x) {
-          double acc = (a == col) ? 1.0 : 0.0;
-          for (int d = 0; d < W; ++d) {
-            const int cc = a - b0 + d;
-            if (cc >= 0 && cc < N0) acc -= A0[(int64_t)a * W + d] * z[cc];
-          }
-          res[a] = acc;
-          l2 += acc * acc;
-        }
-        const double rn = sqrt(dev::block_sum(l2, red));
-        if (!(rn > ir_rtol)) break;
-        for (int a = threadIdx.x; a < N0; a += blockDim.x) y[a] = (FT)res[a];
-        __syncthreads();
-        dev::band_solve_packed<FT, false>(N0, b0, Dinv, y, l2d);
-        for (int a = threadIdx.x; a < N0; a += blockDim.x) z[a] += (double)y[a];
-        __syncthreads();
-      }
-    }
-    for (int a = threadIdx.x; a < N0; a += blockDim.x) AinvT[(int64_t)col * N0 + a] = z[a];
+    dev::band_solve_packed<FT, false>(N0, b0, Dinv, y, l2d, col / BS);
+    for (int a = threadIdx.x; a < N0; a += blockDim.x) AinvT[(int64_t)col * N0 + a] = y[a];
     __syncthreads();
   }
 }
@@ -727,8 +703,12 @@ __global__ void __launch_bounds__(256) k_coarse_inverse(int N0, int b0, const do
 // chunks): lane = row, the 8 warps of a CTA stride over the chunk's columns (coalesced rows of
 // AinvT), warp partials are summed in shared memory in warp order, chunk partials go to
 // `part` and k_gemv_finish adds them in chunk order (no atomics: the result is reproducible).
+// With `skip` set (a refinement that has converged) both kernels return at once.
 constexpr int kGemvChunks = 16;
-__global__ void __launch_bounds__(256) k_dense_gemv_t(int N0, const double* AinvT, const double* g, double* part) {
+template <typename FT>
+__global__ void __launch_bounds__(256) k_dense_gemv_t(int N0, const FT* AinvT, const double* g, double* part,
+                                                       const int* skip) {
+  if (skip && *skip) return;
   __shared__ double acc_s[8][33];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int row = blockIdx.x * 32 + lane;
@@ -736,7 +716,7 @@ __global__ void __launch_bounds__(256) k_dense_gemv_t(int N0, const double* Ainv
   const int c0 = blockIdx.y * per, c1 = min(N0, c0 + per);
   double acc = 0.0;
   if (row < N0)
-    for (int col = c0 + wid; col < c1; col += 8) acc += AinvT[(int64_t)col * N0 + row] * g[col];
+    for (int col = c0 + wid; col < c1; col += 8) acc += (double)AinvT[(int64_t)col * N0 + row] * g[col];
   acc_s[wid][lane] = acc;
   __syncthreads();
   if (wid == 0 && row < N0) {
@@ -747,11 +727,66 @@ __global__ void __launch_bounds__(256) k_dense_gemv_t(int N0, const double* Ainv
   }
 }
 
-__global__ void k_gemv_finish(int N0, int chunks, const double* part, double* z) {
+// z = sum of the chunk partials (accumulate = 0) or z += it (accumulate = 1); `reset`, if
+// given, is cleared (the refinement flag of the solve that starts here).
+__global__ void k_gemv_finish(int N0, int chunks, const double* part, double* z, int accumulate, const int* skip,
+                              int* reset) {
+  if (skip && *skip) return;
+  if (reset && blockIdx.x == 0 && threadIdx.x == 0) *reset = 0;
   for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < N0; row += gridDim.x * blockDim.x) {
     double t = 0.0;
     for (int c = 0; c < chunks; ++c) t += part[(int64_t)c * N0 + row];
-    z[row] = t;
+    z[row] = accumulate ? z[row] + t : t;
+  }
+}
+
+// One step of the refinement of an explicit-inverse coarse solve: r = g - A_0 z (FP64 band
+// A_0, one warp per row, 8 rows per CTA) and its test.  Every CTA stores its partial sums of
+// r^2 and g^2; the last CTA to finish (atomic ticket) adds them in CTA order and sets *done
+// when ||r|| <= ir_rtol ||g|| (or the norms are not finite), then returns the ticket counter
+// to 0.  With *done already set the kernel does nothing.
+__global__ void __launch_bounds__(256) k_coarse_residual(int N0, int b0, const double* A0, const double* g,
+                                                          const double* z, double* r, double* part,
+                                                          unsigned* ticket, int* done, double ir_rtol) {
+  if (*done) return;
+  __shared__ double s_r[8], s_g[8];
+  __shared__ int s_last;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int a = blockIdx.x * 8 + wid, W = 2 * b0 + 1;
+  double rr = 0.0, gg = 0.0;
+  if (a < N0) {
+    double acc = 0.0;
+    for (int d = lane; d < W; d += 32) {
+      const int cc = a - b0 + d;
+      if (cc >= 0 && cc < N0) acc += A0[(int64_t)a * W + d] * z[cc];
+    }
+    acc = dev::warp_sum(acc);
+    const double ra = g[a] - acc;
+    if (lane == 0) r[a] = ra;
+    rr = ra * ra;
+    gg = g[a] * g[a];
+  }
+  if (lane == 0) s_r[wid] = rr, s_g[wid] = gg;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tr = 0.0, tg = 0.0;
+    for (int w = 0; w < 8; ++w) tr += s_r[w], tg += s_g[w];
+    part[2 * blockIdx.x] = tr;
+    part[2 * blockIdx.x + 1] = tg;
+    __threadfence();
+    s_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (s_last && wid == 0) {
+    __threadfence();
+    double tr = 0.0, tg = 0.0;
+    for (int b = lane; b < (int)gridDim.x; b += 32) tr += __ldcg(part + 2 * b), tg += __ldcg(part + 2 * b + 1);
+    tr = dev::warp_sum(tr);
+    tg = dev::warp_sum(tg);
+    if (lane == 0) {
+      *done = !(sqrt(tr) > ir_rtol * sqrt(tg)) ? 1 : 0;
+      *ticket = 0;
+    }
   }
 }
 
@@ -1325,9 +1360,24 @@ void coarse_matrix_launch(Context& c, const double* x) {
 void coarse_solve(Context& c, const double* g, double* z) {
   Dev& D = *c.dev;
   if (D.ainv_valid) {
+    // z = A_0^-1 g, then (FP32 inverse) up to min(ir_max_sweeps, 3) refinement steps
+    // z += A_0^-1 (g - A_0 z) until ||g - A_0 z|| <= ir_rtol ||g||: a fixed sequence of launches
+    // (graph-capturable) whose steps after convergence return at once
     const int N0 = c.cs.N0;
-    LAUNCH(D, k_dense_gemv_t, dim3((N0 + 31) / 32, kGemvChunks), 256, 0, N0, D.ainv, g, D.gpart);
-    LAUNCH(D, k_gemv_finish, grid_for(N0), 256, 0, N0, kGemvChunks, D.gpart, z);
+    const dim3 gg((N0 + 31) / 32, kGemvChunks);
+    const bool f32 = fp32_coarse(c);
+    auto apply_inverse = [&](const double* rhs, int accumulate, const int* skip, int* reset) {
+      if (f32) LAUNCH(D, k_dense_gemv_t<float>, gg, 256, 0, N0, (const float*)D.ainv, rhs, D.gpart, skip);
+      else LAUNCH(D, k_dense_gemv_t<double>, gg, 256, 0, N0, (const double*)D.ainv, rhs, D.gpart, skip);
+      LAUNCH(D, k_gemv_finish, grid_for(N0), 256, 0, N0, kGemvChunks, D.gpart, z, accumulate, skip, reset);
+    };
+    apply_inverse(g, 0, nullptr, D.cflag);
+    const int sweeps = f32 ? std::min(c.opt.ir_max_sweeps, 3) : 0;
+    for (int sw = 0; sw < sweeps; ++sw) {
+      LAUNCH(D, k_coarse_residual, (N0 + 7) / 8, 256, 0, N0, c.cs.b0, D.A0, g, z, D.cres, D.cpart,
+             (unsigned*)(D.cflag + 1), D.cflag, c.opt.ir_rtol);
+      apply_inverse(D.cres, 1, D.cflag, nullptr);
+    }
     return;
   }
   if (fp32_coarse(c))
@@ -1601,9 +1651,13 @@ int device_setup(Context& c) {
         D.cy = D.alloc<double>(cs.N0);
       }
       D.cstatus = D.alloc<int32_t>(1);
-      if (cs.N0 <= 8192 && (3 * sizeof(double)) * (size_t)cs.N0 + 40 * sizeof(double) <= lim) {
-        D.ainv = D.alloc<double>((size_t)cs.N0 * cs.N0);
+      if (cs.N0 <= 8192) {
+        if (fp32_coarse(c)) D.ainv = D.alloc<float>((size_t)cs.N0 * cs.N0);
+        else D.ainv = D.alloc<double>((size_t)cs.N0 * cs.N0);
         D.gpart = D.alloc<double>((size_t)cs.N0 * kGemvChunks);
+        D.cpart = D.alloc<double>(2 * (size_t)((cs.N0 + 7) / 8));
+        D.cflag = D.alloc<int>(2);
+        CK(cudaMemsetAsync(D.cflag, 0, 2 * sizeof(int), D.s));
         set_smem(k_coarse_inverse<float>, lim);
         set_smem(k_coarse_inverse<double>, lim);
       }
@@ -1711,15 +1765,14 @@ void tangent_coarse_launch(Context& c) {
   coarse_matrix_launch(c, D.u0);
   if (D.ainv) {
     const int N0 = c.cs.N0;
-    const size_t sm = (2 * sizeof(double) + (fp32_coarse(c) ? sizeof(float) : sizeof(double))) * N0 + 40 * sizeof(double);
     const int T = std::max(64, (32 + c.cs.b0 + 31) / 32 * 32);
     const int grid = std::min(N0, D.nsm * 8);
     if (fp32_coarse(c))
-      LAUNCH(D, k_coarse_inverse<float>, grid, T, sm, N0, c.cs.b0, D.A0, (const float*)D.A0f,
-             (const float*)D.A0dinv, D.ainv, c.opt.ir_rtol, c.opt.ir_max_sweeps, c.opt.l2_prefetch);
+      LAUNCH(D, k_coarse_inverse<float>, grid, T, sizeof(float) * N0, N0, c.cs.b0, (const float*)D.A0dinv,
+             (float*)D.ainv, c.opt.l2_prefetch);
     else
-      LAUNCH(D, k_coarse_inverse<double>, grid, T, sm, N0, c.cs.b0, D.A0, (const double*)D.A0f,
-             (const double*)D.A0dinv, D.ainv, c.opt.ir_rtol, c.opt.ir_max_sweeps, c.opt.l2_prefetch);
+      LAUNCH(D, k_coarse_inverse<double>, grid, T, sizeof(double) * N0, N0, c.cs.b0, (const double*)D.A0dinv,
+             (double*)D.ainv, c.opt.l2_prefetch);
   }
 }
 
@@ -1837,7 +1890,8 @@ void run_iteration_graph(Context& c, int j, F&& body) {
   key += std::to_string(apply_threads(c));
   // scratch vectors the tangent writes (some are swapped by the coarse Newton iteration)
   for (const void* p : {(const void*)D.t1, (const void*)D.t2, (const void*)D.w0, (const void*)D.gt,
-                        (const void*)D.dc, (const void*)D.gpart, (const void*)D.cres, (const void*)D.cy})
+                        (const void*)D.dc, (const void*)D.gpart, (const void*)D.cres, (const void*)D.cy,
+                        (const void*)D.cpart, (const void*)D.cflag})
     key += std::to_string((uintptr_t)p) + ",";
   if (key != D.graph_key || (int)D.it_exec.size() != D.m) {
     D.reset_graphs();
