@@ -1304,6 +1304,7 @@ size_t coarse_factor_smem(const Context& c, bool f32) {
 
 // A_0(x) = P_0^T DF(x) P_0 -> band -> factor.  Returns false on a bad pivot.
 void coarse_matrix_launch(Context& c, const double* x);
+void coarse_inverse_launch(Context& c);
 
 // Reads the coarse factorization's status word (synchronises the stream).
 bool coarse_status_ok(Dev& D) {
@@ -1439,6 +1440,12 @@ CoarseResult coarse_newton(Context& c, const double* u, double load) {
       if (!D.coarse_fact_valid) {
         R.status = ST_PIVOT;
         break;
+      }
+      // the explicit inverse costs about a third of one band solve, and every solve with it
+      // (GEMV + FP64 refinement) a tenth
+      if (D.ainv) {
+        coarse_inverse_launch(c);
+        D.ainv_valid = true;
       }
     }
     coarse_solve(c, D.g, D.dc);
@@ -1755,6 +1762,22 @@ struct FxInfo {
   bool pivot_failure = false;
 };
 
+// Explicit A_0^-1 from the current coarse factors (N0 <= 8192), issued on D.s; coarse solves use
+// it (refined in FP64 against A_0 where it is applied) once ainv_valid is set.
+void coarse_inverse_launch(Context& c) {
+  Dev& D = *c.dev;
+  if (!D.ainv) return;
+  const int N0 = c.cs.N0;
+  const int T = std::max(64, (32 + c.cs.b0 + 31) / 32 * 32);
+  const int grid = std::min(N0, D.nsm * 8);
+  if (fp32_coarse(c))
+    LAUNCH(D, k_coarse_inverse<float>, grid, T, sizeof(float) * N0, N0, c.cs.b0, (const float*)D.A0dinv,
+           (float*)D.ainv, c.opt.l2_prefetch);
+  else
+    LAUNCH(D, k_coarse_inverse<double>, grid, T, sizeof(double) * N0, N0, c.cs.b0, (const double*)D.A0dinv,
+           (double*)D.ainv, c.opt.l2_prefetch);
+}
+
 // The tangent phase's coarse work at u_0: DF(u_0) for the coarse term of Eq. 12, A_0(u_0) and
 // its factors, and (N_0 <= 8192) the explicit inverse the GMRES iterations' coarse solves use.
 // Issued on D.s; the factorization's status is read by the caller.
@@ -1763,17 +1786,7 @@ void tangent_coarse_launch(Context& c) {
   global_jacobian(c, D.u0);
   D.ainv_valid = false;
   coarse_matrix_launch(c, D.u0);
-  if (D.ainv) {
-    const int N0 = c.cs.N0;
-    const int T = std::max(64, (32 + c.cs.b0 + 31) / 32 * 32);
-    const int grid = std::min(N0, D.nsm * 8);
-    if (fp32_coarse(c))
-      LAUNCH(D, k_coarse_inverse<float>, grid, T, sizeof(float) * N0, N0, c.cs.b0, (const float*)D.A0dinv,
-             (float*)D.ainv, c.opt.l2_prefetch);
-    else
-      LAUNCH(D, k_coarse_inverse<double>, grid, T, sizeof(double) * N0, N0, c.cs.b0, (const double*)D.A0dinv,
-             (double*)D.ainv, c.opt.l2_prefetch);
-  }
+  coarse_inverse_launch(c);
 }
 
 // F_x(u) into D.Fx; prepares everything the tangent needs.
