@@ -69,6 +69,9 @@ struct Dev {
   }
   // mesh
   int32_t *conn = nullptr, *g_elem = nullptr, *g_rowptr = nullptr, *g_col = nullptr, *g_epos = nullptr;
+  int64_t* star_ptr = nullptr;  // node stars (ascending element ids) for the global residual's node sums
+  int32_t* star_ref = nullptr;  // e nen + a per star entry
+  double* Re = nullptr;         // element residuals [e][a][dof]
   double *geom = nullptr, *kcoef = nullptr, *fext = nullptr, *ubc = nullptr, *g_val = nullptr;
   uint8_t* free_dof = nullptr;
   DeviceLocalSet ov, nov;

@@ -12,7 +12,9 @@
 //   k_harmonic       energy-minimising extension of the RGDSW interface values (setup).
 //   k_galerkin       per non-overlapping subdomain: Phi_j^T K^(j)(x) Phi_j (coarse matrix).
 //   k_coarse_*       band LU / solve of A_0 = P_0^T DF P_0 in one CTA (Eq. 9).
-//   k_global_*       colour-ordered global residual F(u) and Jacobian DF(u) (Eq. 3).
+//   k_elem_residual, k_node_residual   global residual F(u): element contributions, then fixed-order
+//                    sums per node.
+//   k_global_jacobian  colour-ordered global Jacobian DF(u) (Eq. 3).
 //   k_vec_*          GMRES vector kernels with fixed-order (deterministic) reductions.
 #include <cuda_runtime.h>
 
@@ -830,24 +832,26 @@ __global__ void __launch_bounds__(256) k_coarse_solve(int N0, int b0, const doub
 }
 
 // ------------------------------------------------------------------------------------------
-// global assembly (colour passes: elements of one colour share no node)
+// global assembly: the residual by element contributions and node sums, the Jacobian in colour
+// passes (elements of one colour share no node)
 // ------------------------------------------------------------------------------------------
+// Element residuals (the weak forms of Eqs. 1 and 2) of every element, one thread per element,
+// into Re[(e nen + a) ndof + d]; k_node_residual adds them up per node.
 template <int LAW>
-__global__ void k_global_residual(const int32_t* elems, int e0, int e1, const int32_t* conn, const double* geom,
-                                  const double* kcoef, const double* x, double* F, double mu, double lam, int* bad) {
-  for (int i = e0 + blockIdx.x * blockDim.x + threadIdx.x; i < e1; i += gridDim.x * blockDim.x) {
-    const int32_t e = elems[i];
+__global__ void k_elem_residual(int64_t ne, const int32_t* conn, const double* geom, const double* kcoef,
+                                const double* x, double* Re, double mu, double lam, int* bad) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < ne; e += (int64_t)gridDim.x * blockDim.x) {
     if (LAW == NLS_LAW_DIFFUSION) {
-      const int32_t* c = conn + (int64_t)e * 3;
-      const double* geo = geom + (int64_t)e * 8;
+      const int32_t* c = conn + e * 3;
+      const double* geo = geom + e * 8;
       const dev::P1State st = dev::p1_state(geo, kcoef[e], x[c[0]], x[c[1]], x[c[2]]);
       double re[3];
       dev::p1_residual(geo, st, re);
 #pragma unroll
-      for (int a = 0; a < 3; ++a) F[c[a]] += re[a];
+      for (int a = 0; a < 3; ++a) Re[e * 3 + a] = re[a];
     } else {
-      const int32_t* c = conn + (int64_t)e * 4;
-      const double* geo = geom + (int64_t)e * 40;
+      const int32_t* c = conn + e * 4;
+      const double* geo = geom + e * 40;
       double ue[8], re[8];
 #pragma unroll
       for (int a = 0; a < 4; ++a) {
@@ -858,10 +862,28 @@ __global__ void k_global_residual(const int32_t* elems, int e0, int e1, const in
       dev::nh_residual(geo, ue, mu, lam, re, ok);
       if (!ok) *bad = 1;
 #pragma unroll
-      for (int a = 0; a < 4; ++a) {
-        F[2 * (int64_t)c[a]] += re[2 * a];
-        F[2 * (int64_t)c[a] + 1] += re[2 * a + 1];
-      }
+      for (int q = 0; q < 8; ++q) Re[e * 8 + q] = re[q];
+    }
+  }
+}
+
+// F = -load fext + the contributions of the elements around every node, added in ascending
+// element order (star_ref[k] = e nen + a: element e, where the node is e's a-th); 0 on the
+// Dirichlet dofs.
+__global__ void k_node_residual(int64_t n_nodes, int nd, const int64_t* star_ptr, const int32_t* star_ref,
+                                const double* Re, double load, const double* fext, const uint8_t* free_dof,
+                                double* F) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n_nodes;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    double acc0 = 0.0, acc1 = 0.0;
+    for (int64_t k = star_ptr[v]; k < star_ptr[v + 1]; ++k) {
+      const int64_t r = (int64_t)star_ref[k] * nd;
+      acc0 += Re[r];
+      if (nd == 2) acc1 += Re[r + 1];
+    }
+    for (int d = 0; d < nd; ++d) {
+      const int64_t i = v * nd + d;
+      F[i] = free_dof[i] ? -load * fext[i] + (d == 0 ? acc0 : acc1) : 0.0;
     }
   }
 }
@@ -907,11 +929,6 @@ __global__ void k_axpby(int64_t n, double a, const double* x, double b, const do
     z[i] = a * x[i] + (y ? b * y[i] : 0.0);
 }
 
-__global__ void k_init_residual(int64_t n, double load, const double* fext, double* F) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    F[i] = -load * fext[i];
-}
-
 __global__ void k_mask(int64_t n, const uint8_t* free_dof, double* x) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     if (!free_dof[i]) x[i] = 0.0;
@@ -943,15 +960,16 @@ __global__ void k_p0_apply(int64_t n, const int32_t* rowptr, const int32_t* col,
   }
 }
 
-// g = P0^T v, one warp per coarse row
-__global__ void k_p0t_apply(int n0, const int32_t* rowptr, const int32_t* col, const double* val, const double* v,
-                            double* g) {
-  const int lane = threadIdx.x & 31;
-  for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < n0; r += (gridDim.x * blockDim.x) >> 5) {
+// g = P0^T v, one CTA per coarse row (the rows are long: every fine dof in the support of the
+// coarse function); fixed-order warp and CTA sums.
+__global__ void __launch_bounds__(256) k_p0t_apply(int n0, const int32_t* rowptr, const int32_t* col,
+                                                    const double* val, const double* v, double* g) {
+  __shared__ double red[40];
+  for (int r = blockIdx.x; r < n0; r += gridDim.x) {
     double acc = 0.0;
-    for (int32_t k = rowptr[r] + lane; k < rowptr[r + 1]; k += 32) acc += val[k] * v[col[k]];
-    acc = dev::warp_sum(acc);
-    if (lane == 0) g[r] = acc;
+    for (int32_t k = rowptr[r] + threadIdx.x; k < rowptr[r + 1]; k += blockDim.x) acc += val[k] * v[col[k]];
+    acc = dev::block_sum(acc, red);
+    if (threadIdx.x == 0) g[r] = acc;
   }
 }
 
@@ -1101,17 +1119,14 @@ void global_residual(Context& c, const double* x, double* F, double load) {
   Dev& D = *c.dev;
   const double E = c.young, nu = c.poisson;
   const double mu = E / (2.0 * (1.0 + nu)), lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
-  LAUNCH(D, k_init_residual, grid_for(c.N), 256, 0, c.N, load, D.fext, F);
-  for (size_t k = 0; k + 1 < c.g_color_ptr.size(); ++k) {
-    const int e0 = c.g_color_ptr[k], e1 = c.g_color_ptr[k + 1];
-    if (c.law == NLS_LAW_DIFFUSION)
-      LAUNCH(D, k_global_residual<NLS_LAW_DIFFUSION>, grid_for(e1 - e0), 256, 0, D.g_elem, e0, e1, D.conn, D.geom,
-             D.kcoef, x, F, mu, lam, D.bad);
-    else
-      LAUNCH(D, k_global_residual<NLS_LAW_NEOHOOKE>, grid_for(e1 - e0), 256, 0, D.g_elem, e0, e1, D.conn, D.geom,
-             D.kcoef, x, F, mu, lam, D.bad);
-  }
-  LAUNCH(D, k_mask, grid_for(c.N), 256, 0, c.N, D.free_dof, F);
+  if (c.law == NLS_LAW_DIFFUSION)
+    LAUNCH(D, k_elem_residual<NLS_LAW_DIFFUSION>, grid_for(c.n_elems), 256, 0, c.n_elems, D.conn, D.geom, D.kcoef, x,
+           D.Re, mu, lam, D.bad);
+  else
+    LAUNCH(D, k_elem_residual<NLS_LAW_NEOHOOKE>, grid_for(c.n_elems), 256, 0, c.n_elems, D.conn, D.geom, D.kcoef, x,
+           D.Re, mu, lam, D.bad);
+  LAUNCH(D, k_node_residual, grid_for(c.n_nodes), 256, 0, c.n_nodes, c.ndof, D.star_ptr, D.star_ref, D.Re, load,
+         D.fext, D.free_dof, F);
 }
 
 void global_jacobian(Context& c, const double* x) {
@@ -1399,7 +1414,7 @@ void p0_update(Context& c, const double* u, const double* cv, double* x) {
 
 void p0t(Context& c, const double* v, double* g) {
   Dev& D = *c.dev;
-  LAUNCH(D, k_p0t_apply, grid_for((int64_t)c.cs.N0 * 32), 256, 0, c.cs.N0, D.p0t_rowptr, D.p0t_col, D.p0t_val, v, g);
+  LAUNCH(D, k_p0t_apply, c.cs.N0, 256, 0, c.cs.N0, D.p0t_rowptr, D.p0t_col, D.p0t_val, v, g);
 }
 
 struct CoarseResult {
@@ -1580,6 +1595,20 @@ int device_setup(Context& c) {
     D.ubc = D.upload(c.ubc);
     D.free_dof = D.upload(c.free_dof);
     D.g_elem = D.upload(c.g_elem);
+    {
+      // node stars as element-local references (e nen + a), ascending element ids
+      std::vector<int32_t> ref(c.star_el.size());
+      for (int64_t v = 0; v < c.n_nodes; ++v)
+        for (int64_t k = c.star_ptr[v]; k < c.star_ptr[v + 1]; ++k) {
+          const int32_t e = c.star_el[k];
+          int a = 0;
+          while (a < c.nen - 1 && c.conn[(int64_t)e * c.nen + a] != v) ++a;
+          ref[k] = e * c.nen + a;
+        }
+      D.star_ptr = D.upload(c.star_ptr);
+      D.star_ref = D.upload(ref);
+      D.Re = D.alloc<double>((size_t)c.n_elems * c.nen * c.ndof);
+    }
     D.g_rowptr = D.upload(c.g_rowptr);
     D.g_col = D.upload(c.g_col);
     D.g_epos = D.upload(c.g_epos);
