@@ -439,8 +439,8 @@ def fp32_peak_tflops(peaks):
 # captures summarised in profiles/ (first launch of a solve of the 1024 x 1024 diffusion
 # workload); a kernel changed since its capture has no entry.
 NCU_TRAFFIC_BYTES = {
-    "k_local_newton<diffusion, float, 128>": 6.980124e9 + 4.117160e9,
-    "k_local_apply<float>": 2.492434e9 + 0.074270e9,
+    "k_local_newton<diffusion, float, 128>": 7.337879e9 + 4.212179e9,
+    "k_local_apply<float>": 2.434448e9 + 0.073884e9,
 }
 
 
