@@ -1169,7 +1169,12 @@ template <int LAW, typename FT, int MAXT>
 void launch_newton_t(Dev& D, int count, int T, size_t sm, const LocalArgs& A) {
   int occ = 0;
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_local_newton<LAW, FT, MAXT>, T, sm));
-  const int grid = std::min(count, D.nsm * std::max(1, occ));
+  occ = std::max(1, occ);
+  // With one CTA per SM a concurrent one-CTA coarse factorization could never share an SM with
+  // this persistent grid: leave it one (the CTAs pull subdomains from the work counter, so one
+  // fewer CTA only means more subdomains for the others).
+  const int spare = (D.coarse_beside && occ == 1 && D.nsm > 1) ? 1 : 0;
+  const int grid = std::min(count, (D.nsm - spare) * occ);
   LAUNCH_NAMED(D, newton_kernel_name(LAW, sizeof(FT) == 4, MAXT), (k_local_newton<LAW, FT, MAXT>), grid, T, sm, A);
 }
 
@@ -1177,6 +1182,24 @@ template <int LAW, typename FT>
 void launch_newton_law(Dev& D, int count, int T, size_t sm, const LocalArgs& A) {
   if (T <= 128) launch_newton_t<LAW, FT, 128>(D, count, T, sm, A);
   else launch_newton_t<LAW, FT, 256>(D, count, T, sm, A);
+}
+
+// CTAs of the batched local Newton kernel resident per SM at the current CTA size.
+int newton_ctas_per_sm(Context& c) {
+  const int T = local_threads(c);
+  const bool f32 = fp32_local(c);
+  const size_t sm = f32 ? local_newton_smem<float>(c.ov) : local_newton_smem<double>(c.ov);
+  int occ = 0;
+  auto q = [&](auto kernel) { CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, T, sm)); };
+  const bool big = T > 128;
+  if (c.law == NLS_LAW_DIFFUSION) {
+    if (f32) big ? q(k_local_newton<NLS_LAW_DIFFUSION, float, 256>) : q(k_local_newton<NLS_LAW_DIFFUSION, float, 128>);
+    else big ? q(k_local_newton<NLS_LAW_DIFFUSION, double, 256>) : q(k_local_newton<NLS_LAW_DIFFUSION, double, 128>);
+  } else {
+    if (f32) big ? q(k_local_newton<NLS_LAW_NEOHOOKE, float, 256>) : q(k_local_newton<NLS_LAW_NEOHOOKE, float, 128>);
+    else big ? q(k_local_newton<NLS_LAW_NEOHOOKE, double, 256>) : q(k_local_newton<NLS_LAW_NEOHOOKE, double, 128>);
+  }
+  return std::max(1, occ);
 }
 
 void dispatch_local_newton(Context& c, const LocalSet& s, const LocalArgs& A, int T) {
@@ -1334,7 +1357,9 @@ bool coarse_matrix(Context& c, const double* x) {
   return coarse_status_ok(*c.dev);
 }
 
-void coarse_matrix_launch(Context& c, const double* x) {
+// A_0(x) = P_0^T DF(x) P_0 in band storage (D.A0): Galerkin blocks per non-overlapping subdomain
+// and their gather.
+void coarse_assemble_launch(Context& c, const double* x) {
   Dev& D = *c.dev;
   LocalArgs A = coarse_args(c);
   A.x = x;
@@ -1345,6 +1370,12 @@ void coarse_matrix_launch(Context& c, const double* x) {
   else LAUNCH(D, (k_galerkin<NLS_LAW_NEOHOOKE, double>), c.nov.count, T, sm, A);
   const int64_t ne = (int64_t)c.cs.N0 * (2 * c.cs.b0 + 1);
   LAUNCH(D, k_a0_gather, grid_for(ne), 256, 0, ne, D.a0_ptr, D.a0_src, D.blk, D.A0);
+}
+
+// Band factorization of D.A0 (one CTA; its size autotuned at the first call) into the packed
+// solve operands; the status word is read by coarse_status_ok.
+void coarse_factor_launch(Context& c) {
+  Dev& D = *c.dev;
   const bool f32 = fp32_coarse(c);
   const size_t fsm = coarse_factor_smem(c, f32);
   auto factor = [&](int T) {
@@ -1371,6 +1402,11 @@ void coarse_matrix_launch(Context& c, const double* x) {
     D.coarse_tuned = true;
   }
   factor(D.coarse_T);
+}
+
+void coarse_matrix_launch(Context& c, const double* x) {
+  coarse_assemble_launch(c, x);
+  coarse_factor_launch(c);
 }
 
 void coarse_solve(Context& c, const double* g, double* z) {
@@ -1807,14 +1843,21 @@ void coarse_inverse_launch(Context& c) {
            (double*)D.ainv, c.opt.l2_prefetch);
 }
 
-// The tangent phase's coarse work at u_0: DF(u_0) for the coarse term of Eq. 12, A_0(u_0) and
-// its factors, and (N_0 <= 8192) the explicit inverse the GMRES iterations' coarse solves use.
-// Issued on D.s; the factorization's status is read by the caller.
-void tangent_coarse_launch(Context& c) {
+// The tangent phase's coarse work at u_0, first part (issued on D.s): DF(u_0) for the coarse term
+// of Eq. 12 and A_0(u_0).  These kernels use many CTAs and run before the persistent local
+// Newton launch, which then holds every SM.
+void tangent_coarse_assemble(Context& c) {
   Dev& D = *c.dev;
   global_jacobian(c, D.u0);
   D.ainv_valid = false;
-  coarse_matrix_launch(c, D.u0);
+  coarse_assemble_launch(c, D.u0);
+}
+
+// Second part (issued on the high-priority second stream): the one-CTA factorization of A_0(u_0),
+// placed beside the local Newton CTAs, and (N_0 <= 8192) the explicit inverse the GMRES
+// iterations' coarse solves use.  The factorization's status is read by the caller.
+void tangent_coarse_factor(Context& c) {
+  coarse_factor_launch(c);
   coarse_inverse_launch(c);
 }
 
@@ -1834,12 +1877,24 @@ FxInfo evaluate_Fx(Context& c, const double* u, double load, double* t_inner, do
   }
   sync(D);
   auto t1 = std::chrono::steady_clock::now();
-  // The tangent phase's coarse work depends on u_0 only: it runs on a second stream, issued
-  // before the batched local solves so that its single-CTA factorization overlaps them.
+  // The tangent phase's coarse work depends on u_0 only: it goes on a second stream of the
+  // highest priority, issued before the batched local solves, so that it runs beside them.  The
+  // persistent local Newton grid fills every SM, so how it shares them depends on its occupancy:
+  // - several CTAs per SM: DF(u_0) and A_0(u_0) (many CTAs) go first on this stream, and the
+  //   single-CTA factorization of A_0 is dispatched together with the local solves, beside
+  //   some of their CTAs (the kernel pulls subdomains from a work counter, so a CTA of it that
+  //   starts late only takes fewer of them);
+  // - one CTA per SM (none can share an SM with the factorization): the whole chain goes on
+  //   the second stream, its assembly overlapping the start of the local solves, and the local
+  //   Newton grid leaves one SM to the factorization.
   const bool two_level = cp != NLS_COUPLING_ONE;
+  const bool spare_sm = two_level && newton_ctas_per_sm(c) == 1;
   if (two_level) {
+    if (!spare_sm) tangent_coarse_assemble(c);
     if (!D.s2) {
-      CK(cudaStreamCreateWithFlags(&D.s2, cudaStreamNonBlocking));
+      int least = 0, greatest = 0;
+      CK(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+      CK(cudaStreamCreateWithPriority(&D.s2, cudaStreamNonBlocking, greatest));
       CK(cudaEventCreateWithFlags(&D.ev_u0, cudaEventDisableTiming));
       CK(cudaEventCreateWithFlags(&D.ev_coarse, cudaEventDisableTiming));
     }
@@ -1847,7 +1902,8 @@ FxInfo evaluate_Fx(Context& c, const double* u, double load, double* t_inner, do
     CK(cudaStreamWaitEvent(D.s2, D.ev_u0, 0));
     std::swap(D.s, D.s2);
     try {
-      tangent_coarse_launch(c);
+      if (spare_sm) tangent_coarse_assemble(c);
+      tangent_coarse_factor(c);
     } catch (...) {
       std::swap(D.s, D.s2);
       throw;
@@ -1857,7 +1913,9 @@ FxInfo evaluate_Fx(Context& c, const double* u, double load, double* t_inner, do
   }
   const GuessProposal proposal = guess_propose(c, point, load);
   tune_local_newton(c, point, D.Fx, load, proposal);
+  D.coarse_beside = spare_sm;
   launch_local_newton(c, point, D.Fx, load, proposal, true);
+  D.coarse_beside = false;
   D.local_factors_valid = true;  // every subdomain with status OK now holds its tangent factors
   guess_after_local(c, point, load, proposal.x != nullptr);
   std::vector<int32_t> its(c.ov.count), st(c.ov.count), ch(c.ov.count);
