@@ -44,7 +44,8 @@ extern "C" {
 #define NLS_E_GMRES (-7)          /* GMRES reached its iteration limit */
 #define NLS_E_DIVERGED (-8)       /* non-finite outer residual */
 #define NLS_E_DEVICE_TIMEOUT (-9) /* a bounded device-side wait gave up */
-#define NLS_W_NOT_CONVERGED 1     /* outer Newton stopped at its iteration limit */
+#define NLS_W_NOT_CONVERGED 1     /* outer Newton stopped at its iteration limit, or every correction vanished
+                                     because local or coarse solves failed */
 
 /* ---- enumerations --------------------------------------------------------------------- */
 #define NLS_P1_TRI 1              /* 3-node triangles, nodes counter-clockwise */
@@ -161,6 +162,14 @@ int nls_set_dirichlet(nls_ctx* ctx, int64_t n, const int64_t* dofs, const double
 /* Dead-load traction g_N of Eq. 2 on boundary segments: edge_nodes [n_edges * 2],
  * traction [n_edges * 2] force per unit length at load factor 1. */
 int nls_set_traction(nls_ctx* ctx, int64_t n_edges, const int32_t* edge_nodes, const double* traction);
+
+/* Dead-load volume force f_vol of Eq. 2 (NLS_LAW_NEOHOOKE; call after nls_set_material):
+ * f_vol [n_elems * 2], force per unit area, constant on each element, at load factor 1 (ramped
+ * with the traction by the load steps); NULL removes it.  Assembled into the external load
+ * vector as int_e f_vol . N_a (2 x 2 Gauss, exact for a constant force on a bilinear element).
+ * May follow nls_setup: the load vector is then rebuilt on the device.  NLS_E_ARG for another
+ * law or non-finite values. */
+int nls_set_volume_force(nls_ctx* ctx, const double* f_vol);
 
 /* Material law.  NLS_LAW_DIFFUSION: params unused, k_elem and f_elem [n_elems] (NULL = 1).
  * NLS_LAW_NEOHOOKE: params = {E, nu}; k_elem, f_elem must be NULL. */

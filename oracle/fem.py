@@ -11,7 +11,9 @@ CPU-baseline leg.  Parity of every function here is pinned by ``tests/test_oracl
   P(F) = mu (F - F^-T) + lambda ln(det F) F^-T  with mu = E / (2 (1 + nu)) and
   lambda = E nu / ((1 + nu)(1 - 2 nu)).  (The printed formula has "E/(1(1+nu))" and
   "ln(det(F) F^-T)"; both are read as this standard law.)  2x2 Gauss quadrature; dead
-  load traction on boundary segments by 2-point Gauss (exact for a constant traction).
+  load traction on boundary segments by 2-point Gauss (exact for a constant traction) and a
+  dead-load volume force f_vol, constant per element, by 2x2 Gauss (exact: N_a det J is at
+  most quadratic in each reference coordinate).
 """
 from __future__ import annotations
 
@@ -129,6 +131,22 @@ def neohooke_q1(X: np.ndarray, ue: np.ndarray, mu: float, lam: float, want_jac: 
     return r.reshape(E, 8), (K.reshape(E, 8, 8) if want_jac else None), detmin
 
 
+def q1_shape_values(xi: float, eta: float) -> np.ndarray:
+    """N_a(xi, eta) = (1 + xi xi_a)(1 + eta eta_a) / 4 at the four corners a."""
+    return 0.25 * (1.0 + xi * Q1_CORNERS[:, 0]) * (1.0 + eta * Q1_CORNERS[:, 1])
+
+
+def volume_load(X: np.ndarray, f: np.ndarray) -> np.ndarray:
+    """External force int_e f . N_a dA of a constant volume force f [E, 2] on Q1 elements X [E, 4, 2]:
+    [E, 8] (dof = 2 * node + component)."""
+    w = np.zeros((X.shape[0], 4))
+    for xi, eta in Q1_GAUSS:
+        Jm = np.einsum("eai,aj->eij", X, q1_shape_derivatives(xi, eta))
+        detJm = Jm[:, 0, 0] * Jm[:, 1, 1] - Jm[:, 0, 1] * Jm[:, 1, 0]
+        w += detJm[:, None] * q1_shape_values(xi, eta)[None, :]
+    return (w[:, :, None] * f[:, None, :]).reshape(X.shape[0], 8)
+
+
 def traction_load(Xe: np.ndarray, t: np.ndarray) -> np.ndarray:
     """External force int_edge t N_a ds on each boundary segment: [M, 4] (dof = 2 * node + comp).
 
@@ -155,12 +173,14 @@ class Model:
         self.k = np.ones(n_el) if prob.k_elem is None else np.asarray(prob.k_elem, dtype=np.float64)
         self.f = np.ones(n_el) if prob.f_elem is None else np.asarray(prob.f_elem, dtype=np.float64)
         self.mu, self.lam = lame(prob.young, prob.poisson)
+        self.fvol = None if prob.f_vol is None else np.asarray(prob.f_vol, dtype=np.float64).reshape(n_el, 2)
 
     def element_terms(self, elems: np.ndarray, Xe: np.ndarray, ue: np.ndarray, want_jac: bool = True,
                       load: float = 1.0):
         """(r [E, nen*ndof], K [E, nen*ndof, nen*ndof] or None, ok flag) for the listed elements.
 
-        ``load`` scales the external source f of Eq. 1 (load stepping ramps every external load).
+        ``load`` scales the external source f of Eq. 1 and the volume force of Eq. 2 (load stepping
+        ramps every external load).
         ``ok`` is False when a Neo-Hooke element has det F <= 0 at a Gauss point.
         """
         if self.prob.law == LAW_DIFFUSION:
@@ -168,6 +188,8 @@ class Model:
             return r, K, True
         with np.errstate(invalid="ignore", divide="ignore"):
             r, K, detmin = neohooke_q1(Xe, ue, self.mu, self.lam, want_jac)
+        if self.fvol is not None:
+            r = r - load * volume_load(Xe, self.fvol[elems])
         return r, K, bool(np.all(detmin > 0.0))
 
     def external_load(self, edges: np.ndarray, Xe: np.ndarray, load: float) -> np.ndarray:

@@ -132,6 +132,23 @@ int nls_set_traction(nls_ctx* ctx, int64_t n_edges, const int32_t* edge_nodes, c
   return NLS_OK;
 }
 
+int nls_set_volume_force(nls_ctx* ctx, const double* f_vol) {
+  if (!ctx || !ctx->c.have_material) return fail(ctx, NLS_E_ARG, "set the material first");
+  Context& c = ctx->c;
+  if (c.law != NLS_LAW_NEOHOOKE) return fail(ctx, NLS_E_ARG, "the volume force applies to the Neo-Hooke law");
+  if (f_vol)
+    for (int64_t k = 0; k < 2 * c.n_elems; ++k)
+      if (!std::isfinite(f_vol[k])) return fail(ctx, NLS_E_ARG, "non-finite volume force");
+  c.f_vol.clear();
+  if (f_vol) c.f_vol.assign(f_vol, f_vol + 2 * c.n_elems);
+  if (!c.is_setup) return NLS_OK;
+  nls::build_fext(c);
+  if (!c.dev) return NLS_OK;  // host-only setup
+  const int st = nls::device_upload_fext(c);
+  if (st != NLS_OK) return fail(ctx, st, c.last_error.c_str());
+  return NLS_OK;
+}
+
 int nls_set_material(nls_ctx* ctx, int law, const double* params, const double* k_elem, const double* f_elem) {
   if (!ctx || !ctx->c.have_mesh) return fail(ctx, NLS_E_ARG, "set the mesh first");
   Context& c = ctx->c;
@@ -154,6 +171,7 @@ int nls_set_material(nls_ctx* ctx, int law, const double* params, const double* 
     return fail(ctx, NLS_E_ARG, "unknown material law");
   }
   c.law = law;
+  c.f_vol.clear();
   c.have_material = true;
   c.is_setup = false;
   return NLS_OK;

@@ -106,6 +106,7 @@ struct Context {
   std::vector<double> tr_vals;
   double young = 210.0, poisson = 0.3;
   std::vector<double> k_elem, f_elem;
+  std::vector<double> f_vol;        // Neo-Hooke volume force per element (fx, fy), load factor 1
   int32_t n_sub = 0, overlap = 1;
   std::vector<int32_t> elem_to_sub;
   int coarse_kind = NLS_COARSE_NONE;
@@ -133,6 +134,7 @@ struct Context {
 int build_setup(Context& c);
 void build_fext(Context& c);
 int device_set_coefficients(Context& c);  // after nls_setup: new k / f on the device, coarse basis rebuilt
+int device_upload_fext(Context& c);       // after nls_setup: the rebuilt external load vector to the device
 void guess_coefficients_changed(Context& c);
 void build_local_set(Context& c, LocalSet& s, int layers, bool neumann_rows, bool keep_overlap_lists);
 // solver.cu

@@ -686,6 +686,30 @@ void build_fext(Context& c) {
       for (int a = 0; a < 3; ++a) c.fext[c.conn[e * 3 + a]] += f * a3;
     }
   }
+  if (c.law == NLS_LAW_NEOHOOKE && !c.f_vol.empty()) {
+    // int_e f N_a dA by 2 x 2 Gauss: N_a and det J are bilinear, so the rule is exact
+    const double g = 1.0 / std::sqrt(3.0);
+    const double gp[4][2] = {{-g, -g}, {g, -g}, {g, g}, {-g, g}};
+    const double sa[4] = {-1, 1, 1, -1}, ta[4] = {-1, -1, 1, 1};  // reference corners, counter-clockwise
+    for (int64_t e = 0; e < c.n_elems; ++e) {
+      const int32_t* cn = &c.conn[e * 4];
+      double w[4] = {0, 0, 0, 0};
+      for (const auto& q : gp) {
+        double J[2][2] = {{0, 0}, {0, 0}};
+        for (int a = 0; a < 4; ++a) {
+          const double dxi = 0.25 * sa[a] * (1 + ta[a] * q[1]), deta = 0.25 * ta[a] * (1 + sa[a] * q[0]);
+          for (int i = 0; i < 2; ++i) {
+            J[i][0] += c.xy[2 * cn[a] + i] * dxi;
+            J[i][1] += c.xy[2 * cn[a] + i] * deta;
+          }
+        }
+        const double det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+        for (int a = 0; a < 4; ++a) w[a] += 0.25 * (1 + sa[a] * q[0]) * (1 + ta[a] * q[1]) * det;
+      }
+      for (int a = 0; a < 4; ++a)
+        for (int d = 0; d < 2; ++d) c.fext[2 * (int64_t)cn[a] + d] += c.f_vol[2 * e + d] * w[a];
+    }
+  }
   for (size_t k = 0; k < c.tr_edges.size() / 2; ++k) {
     int32_t n0 = c.tr_edges[2 * k], n1 = c.tr_edges[2 * k + 1];
     double L = std::hypot(c.xy[2 * n1] - c.xy[2 * n0], c.xy[2 * n1 + 1] - c.xy[2 * n0 + 1]);

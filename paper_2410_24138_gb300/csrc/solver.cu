@@ -707,6 +707,9 @@ __global__ void __launch_bounds__(256) k_coarse_inverse(int N0, int b0, const FT
 // `part` and k_gemv_finish adds them in chunk order (no atomics: the result is reproducible).
 // With `skip` set (a refinement that has converged) both kernels return at once.
 constexpr int kGemvChunks = 16;
+// Largest coarse dimension with an explicit inverse (N0^2 entries in the factors' precision:
+// 1 GB in FP32 at the limit); larger coarse problems use the one-CTA band solve.
+constexpr int kMaxInverseN0 = 16384;
 template <typename FT>
 __global__ void __launch_bounds__(256) k_dense_gemv_t(int N0, const FT* AinvT, const double* g, double* part,
                                                        const int* skip) {
@@ -1723,7 +1726,7 @@ int device_setup(Context& c) {
         D.cy = D.alloc<double>(cs.N0);
       }
       D.cstatus = D.alloc<int32_t>(1);
-      if (cs.N0 <= 8192) {
+      if (cs.N0 <= kMaxInverseN0) {
         if (fp32_coarse(c)) D.ainv = D.alloc<float>((size_t)cs.N0 * cs.N0);
         else D.ainv = D.alloc<double>((size_t)cs.N0 * cs.N0);
         D.gpart = D.alloc<double>((size_t)cs.N0 * kGemvChunks);
@@ -1788,6 +1791,19 @@ int device_set_coefficients(Context& c) {
   return NLS_OK;
 }
 
+int device_upload_fext(Context& c) {
+  try {
+    Dev& D = *c.dev;
+    CK(cudaSetDevice(c.device));
+    CK(cudaMemcpyAsync(D.fext, c.fext.data(), sizeof(double) * c.fext.size(), cudaMemcpyHostToDevice, D.s));
+    sync(D);
+  } catch (const CudaFailure& ex) {
+    c.last_error = ex.what();
+    return NLS_E_CUDA;
+  }
+  return NLS_OK;
+}
+
 void device_free(Context& c) {
   if (!c.dev) return;
   Dev& D = *c.dev;
@@ -1827,7 +1843,7 @@ struct FxInfo {
   bool pivot_failure = false;
 };
 
-// Explicit A_0^-1 from the current coarse factors (N0 <= 8192), issued on D.s; coarse solves use
+// Explicit A_0^-1 from the current coarse factors (N0 <= kMaxInverseN0), issued on D.s; coarse solves use
 // it (refined in FP64 against A_0 where it is applied) once ainv_valid is set.
 void coarse_inverse_launch(Context& c) {
   Dev& D = *c.dev;
@@ -1854,7 +1870,7 @@ void tangent_coarse_assemble(Context& c) {
 }
 
 // Second part (issued on the high-priority second stream): the one-CTA factorization of A_0(u_0),
-// placed beside the local Newton CTAs, and (N_0 <= 8192) the explicit inverse the GMRES
+// placed beside the local Newton CTAs, and (N_0 <= kMaxInverseN0) the explicit inverse the GMRES
 // iterations' coarse solves use.  The factorization's status is read by the caller.
 void tangent_coarse_factor(Context& c) {
   coarse_factor_launch(c);
@@ -2185,7 +2201,13 @@ int solve(Context& c, double* u_user, int u_dev, nls_report* rep) {
           break;
         }
         const double fxn = norm2(D, N, D.Fx);
-        if (fxn == 0.0) break;  // every correction vanished: no further progress possible
+        if (fxn == 0.0) {
+          // Every correction vanished.  With all local and coarse solves converged, ||F|| is below
+          // what their stopping tests resolve: the outer iteration has converged as far as it can.
+          // With failed solves (their corrections are dropped) it cannot progress: not converged.
+          if (fi.local_failures > 0 || fi.coarse_status != ST_OK) status = NLS_W_NOT_CONVERGED;
+          break;
+        }
         auto g0 = std::chrono::steady_clock::now();
         GmresResult gr = gmres(c, D.Fx);
         sync(D);

@@ -17,6 +17,8 @@ Workloads (node ids are lexicographic, x fastest; cell (i, j) has id j*n + i):
 * ``diffusion_c4``  512x512 P1 cells, log-normal k (Gaussian covariance,
   correlation length 1/16, sigma 1), f constant per instance drawn in [0.5, 2].
 * ``neohooke_c5``   2048x2048 Q1 cells, 64x64 bricks, otherwise as c3.
+* ``beam_problem``  the beam of Section 1: 5 x 1 Neo-Hooke rectangle clamped at both ends under
+  a volume force f_x, laid out along y, m x 5m Q1 cells, px x py bricks.
 """
 from __future__ import annotations
 
@@ -67,17 +69,23 @@ def uniform01(gen: SplitMix64, count: int) -> np.ndarray:
 # ----------------------------------------------------------------------------------------------
 
 def structured_mesh(n: int, elem_type: int, lx: float = 1.0, ly: float = 1.0):
-    """Uniform n x n cell mesh of [0, lx] x [0, ly].
+    """Uniform n x n cell mesh of [0, lx] x [0, ly] (see structured_rect_mesh)."""
+    return structured_rect_mesh(n, n, elem_type, lx, ly)
+
+
+def structured_rect_mesh(nx: int, ny: int, elem_type: int, lx: float = 1.0, ly: float = 1.0):
+    """Uniform nx x ny cell mesh of [0, lx] x [0, ly]; node (i, j) has id j (nx + 1) + i, cell (i, j)
+    has id j nx + i.
 
     P1: every cell (i, j) is cut along its SW-NE diagonal into the triangles
     {(i,j),(i+1,j),(i+1,j+1)} (element 2c) and {(i,j),(i+1,j+1),(i,j+1)} (element 2c+1).
     Q1: the cell itself, nodes counter-clockwise from its SW corner.
     Returns (xy [n_nodes, 2] float64, conn [n_elems, nen] int32).
     """
-    m = n + 1
-    jj, ii = np.meshgrid(np.arange(m), np.arange(m), indexing="ij")
-    xy = np.stack([ii.ravel() * (lx / n), jj.ravel() * (ly / n)], axis=1).astype(np.float64)
-    cj, ci = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    m = nx + 1
+    jj, ii = np.meshgrid(np.arange(ny + 1), np.arange(m), indexing="ij")
+    xy = np.stack([ii.ravel() * (lx / nx), jj.ravel() * (ly / ny)], axis=1).astype(np.float64)
+    cj, ci = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
     ci = ci.ravel()
     cj = cj.ravel()
     sw = cj * m + ci
@@ -85,7 +93,7 @@ def structured_mesh(n: int, elem_type: int, lx: float = 1.0, ly: float = 1.0):
     ne = sw + m + 1
     nw = sw + m
     if elem_type == P1_TRI:
-        conn = np.empty((2 * n * n, 3), dtype=np.int32)
+        conn = np.empty((2 * nx * ny, 3), dtype=np.int32)
         conn[0::2] = np.stack([sw, se, ne], axis=1)
         conn[1::2] = np.stack([sw, ne, nw], axis=1)
     elif elem_type == Q1_QUAD:
@@ -126,7 +134,14 @@ def _cuts(n: int, sizes: np.ndarray) -> np.ndarray:
 
 
 def brick_partition(n: int, n_bands: int, per_band: int, seed: int, spread: float = 0.3) -> np.ndarray:
-    """Seeded uneven brick partition of an n x n cell grid.
+    """Seeded uneven brick partition of an n x n cell grid (see rect_brick_partition)."""
+    return rect_brick_partition(n, n, n_bands, per_band, seed, spread)
+
+
+def rect_brick_partition(nx: int, ny: int, n_bands: int, per_band: int, seed: int,
+                         spread: float = 0.3) -> np.ndarray:
+    """Seeded uneven brick partition of an nx x ny cell grid: n_bands bands along y, per_band
+    bricks along x in every band.
 
     Band heights h_j and, independently in every band, brick widths w_{j,k} are
     nominal * (1 + spread * (U - 0.5)) with U uniform in [0, 1) (each side varies by
@@ -134,11 +149,11 @@ def brick_partition(n: int, n_bands: int, per_band: int, seed: int, spread: floa
     """
     gen = splitmix64(seed)
     heights = 1.0 + spread * (uniform01(gen, n_bands) - 0.5)
-    ycut = _cuts(n, heights)
-    cell_to_sub = np.empty((n, n), dtype=np.int32)
+    ycut = _cuts(ny, heights)
+    cell_to_sub = np.empty((ny, nx), dtype=np.int32)
     for j in range(n_bands):
         widths = 1.0 + spread * (uniform01(gen, per_band) - 0.5)
-        xcut = _cuts(n, widths)
+        xcut = _cuts(nx, widths)
         for k in range(per_band):
             cell_to_sub[ycut[j]:ycut[j + 1], xcut[k]:xcut[k + 1]] = j * per_band + k
     return cell_to_sub.ravel()
@@ -210,6 +225,7 @@ class Problem:
     f_elem: Optional[np.ndarray] = None  # source per element (None = 1)
     traction_edges: Optional[np.ndarray] = None   # [n_edges, 2] node pairs
     traction: Optional[np.ndarray] = None         # [n_edges, 2] force per unit length at load factor 1
+    f_vol: Optional[np.ndarray] = None            # [n_elems, 2] Neo-Hooke volume force per unit area, load factor 1
     young: float = 210.0
     poisson: float = 0.3
     load_steps: int = 1
@@ -292,3 +308,30 @@ def diffusion_c4(field_seed: int, n: int = 512, per_side: int = 16, seed: int = 
 
 def neohooke_c5(n: int = 2048, per_side: int = 64, seed: int = PARTITION_SEED) -> Problem:
     return neohooke_c3(n=n, per_side=per_side, seed=seed)
+
+
+BEAM_LENGTH = 5.0
+
+
+def beam_problem(m: int, px: int, py: int, f_x: float, overlap: int = 2, seed: int = PARTITION_SEED,
+                 load_steps: int = 1) -> Problem:
+    """The beam of Section 1 (Eq. 2): a 5 x 1 rectangle of Neo-Hooke material (E = 210, nu = 0.3),
+    clamped (u = 0) at both ends, g_N = 0 elsewhere, under a volume force of size f_x across the
+    beam (the paper's f_vol = (0, -f_x) with E in GPa and f_x in GN / m^3).
+
+    The beam is laid out along y -- the paper's beam turned by 90 degrees, the force pointing
+    along -x -- so that the lexicographic node numbering runs across its short side and the
+    local and coarse band widths stay those of the subdomains' widths: m x 5m Q1 cells, clamped
+    edges y = 0 and y = 5, px x py uneven bricks (py bands along the length).
+    """
+    nx, ny = m, int(round(BEAM_LENGTH * m))
+    xy, conn = structured_rect_mesh(nx, ny, Q1_QUAD, 1.0, BEAM_LENGTH)
+    j = np.arange(xy.shape[0]) // (nx + 1)
+    clamped = np.nonzero((j == 0) | (j == ny))[0].astype(np.int64)
+    cell_to_sub = rect_brick_partition(nx, ny, py, px, seed)
+    f_vol = np.zeros((conn.shape[0], 2))
+    f_vol[:, 0] = -f_x
+    return Problem(name=f"beam_{nx}x{ny}_Q1_{px * py}_bricks_f{f_x:g}", n=nx, elem_type=Q1_QUAD, law=LAW_NEOHOOKE,
+                   xy=xy, conn=conn, dirichlet_nodes=clamped,
+                   elem_to_sub=cell_to_elem_partition(cell_to_sub, Q1_QUAD), n_sub=px * py, overlap=overlap,
+                   f_vol=f_vol, load_steps=load_steps)

@@ -93,7 +93,8 @@ EXPORTS = ["nls_options_default", "nls_create", "nls_destroy", "nls_strerror", "
            "nls_reset_kernel_stats", "nls_local_corrections_noalloc", "nls_guess_create", "nls_guess_destroy",
            "nls_guess_attach", "nls_guess_train", "nls_guess_pairs", "nls_guess_get_params", "nls_guess_set_params",
            "nls_guess_get_normalisation", "nls_guess_set_normalisation", "nls_guess_gradient", "nls_guess_forward",
-           "nls_guess_counts", "nls_get_tuning", "nls_guess_set_smoothing", "nls_set_coefficients"]
+           "nls_guess_counts", "nls_get_tuning", "nls_guess_set_smoothing", "nls_set_coefficients",
+           "nls_set_volume_force"]
 
 _LIB = None
 _P = ctypes.c_void_p
@@ -123,6 +124,7 @@ def load() -> ctypes.CDLL:
         "nls_set_dirichlet": (ctypes.c_int, [_P, i64, _P, _P]),
         "nls_set_traction": (ctypes.c_int, [_P, i64, _P, _P]),
         "nls_set_material": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P]),
+        "nls_set_volume_force": (ctypes.c_int, [_P, _P]),
         "nls_set_partition": (ctypes.c_int, [_P, i32, _P, i32]),
         "nls_set_coarse": (ctypes.c_int, [_P, ctypes.c_int]),
         "nls_set_options": (ctypes.c_int, [_P, ctypes.POINTER(Options)]),
@@ -236,6 +238,8 @@ class Solver:
         else:
             params = np.array([p.young, p.poisson], dtype=np.float64)
             self._check(self.lib.nls_set_material(self.h, law, _ptr(params), None, None), "nls_set_material")
+            if p.f_vol is not None:
+                self.set_volume_force(p.f_vol)
         dofs = np.ascontiguousarray(p.dirichlet_dofs(), dtype=np.int64)
         vals = np.zeros(dofs.shape[0])
         self._check(self.lib.nls_set_dirichlet(self.h, dofs.shape[0], _ptr(dofs), _ptr(vals)), "nls_set_dirichlet")
@@ -343,6 +347,11 @@ class Solver:
         n = ctypes.c_int32()
         self._check(self.lib.nls_get_kernel_stats(self.h, cap, arr, ctypes.byref(n)), "nls_get_kernel_stats")
         return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].total_ms)) for i in range(n.value)}
+
+    def set_volume_force(self, f_vol=None):
+        """Neo-Hooke volume force per element [n_elems, 2] at load factor 1 (None removes it)."""
+        f = None if f_vol is None else np.ascontiguousarray(f_vol, dtype=np.float64).reshape(-1)
+        self._check(self.lib.nls_set_volume_force(self.h, _ptr(f)), "nls_set_volume_force")
 
     def set_coefficients(self, k_elem=None, f_elem=None):
         """New per-element k and f (diffusion), keeping the maps of the current setup."""

@@ -130,3 +130,20 @@ def test_full_size_c2_maps_sampled(nls):
         np.add.at(count, d[o], 1)
     free = fem.free_mask(p)
     assert np.all(count[free] == 1) and np.all(count[~free] == 0)
+
+
+def test_volume_force_validation(nls):
+    s = nls.Solver()
+    p = I.diffusion_c1()
+    s.set_problem(p)
+    with pytest.raises(nls.NLSError):  # the diffusion law has no volume force
+        s.set_volume_force(np.zeros((p.conn.shape[0], 2)))
+    b = I.beam_problem(4, 2, 2, 4.0)
+    s2 = nls.Solver()
+    s2.set_problem(b)
+    bad = b.f_vol.copy()
+    bad[3, 1] = np.nan
+    with pytest.raises(nls.NLSError):
+        s2.set_volume_force(bad)
+    s2.set_volume_force(None)
+    s2.set_volume_force(b.f_vol)

@@ -42,10 +42,12 @@ def _small_problems():
         "c1": I.diffusion_c1(),
         "brick": I.diffusion_problem(40, I.brick_partition(40, 3, 4, 11), 12, 2),
         "nh": I.neohooke_problem(16, I.brick_partition(16, 2, 3, 5), 6, 2, traction_max=4.0),
+        # the beam of Section 1 (volume force, both ends clamped) at 6 x 30 cells, 2 x 3 bricks
+        "beam": I.beam_problem(6, 2, 3, 4.0),
     }
 
 
-@pytest.mark.parametrize("name", ["c1", "brick", "nh"])
+@pytest.mark.parametrize("name", ["c1", "brick", "nh", "beam"])
 def test_global_residual(nls, name):
     p = _small_problems()[name]
     s = nls.make_solver(p, coupling="one")
@@ -56,7 +58,7 @@ def test_global_residual(nls, name):
         assert np.max(np.abs(F - Fo)) <= 1e-13 * np.max(np.abs(Fo))
 
 
-@pytest.mark.parametrize("name", ["c1", "brick", "nh"])
+@pytest.mark.parametrize("name", ["c1", "brick", "nh", "beam"])
 def test_coarse_basis(nls, name):
     p = _small_problems()[name]
     s = nls.make_solver(p, coupling="hybrid")
@@ -71,7 +73,7 @@ def test_coarse_basis(nls, name):
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 @pytest.mark.parametrize("coupling", ["one", "add", "hybrid"])
-@pytest.mark.parametrize("name", ["c1", "brick", "nh"])
+@pytest.mark.parametrize("name", ["c1", "brick", "nh", "beam"])
 def test_Fx_and_tangent(nls, name, coupling, precision):
     p = _small_problems()[name]
     s = nls.make_solver(p, coupling=coupling, precision=precision, **TIGHT)
@@ -146,6 +148,36 @@ def test_neohooke_load_steps(nls):
         u, rep = s.solve()
         assert rep.status == 0
         assert np.linalg.norm(u - ustar) / np.linalg.norm(ustar) < tol
+
+
+@pytest.mark.parametrize("f_x", [4.0, 7.5])
+def test_beam_solution(nls, f_x):
+    """The beam of Section 1 under the volume force: both two-level couplings reach the plain
+    Newton solution of the oracle (1e-8 FP64 / 1e-6 FP32 relative), the GPU's outer iteration
+    counts within one of the oracle's own nonlinear Schwarz iteration."""
+    p = I.beam_problem(6, 2, 3, f_x)
+    ustar, _ = S.plain_newton(p, tol=1e-12)
+    for coupling in ("hybrid", "add"):
+        sw = S.Schwarz(p, S.Options(coupling=coupling, outer_atol=1e-10, gmres_maxit=100))
+        _, hist, _ = sw.solve()
+        outer_o = len([h for h in hist if "gmres_its" in h])
+        for precision, tol in (("fp64", 1e-8), ("fp32", 1e-6)):
+            s = nls.make_solver(p, coupling=coupling, precision=precision, outer_atol=1e-10, gmres_maxit=100)
+            u, rep = s.solve()
+            assert rep.status == 0 and rep.final_residual < 1e-10
+            assert np.linalg.norm(u - ustar) / np.linalg.norm(ustar) < tol
+            assert abs(rep.outer_iterations - outer_o) <= 1
+
+
+def test_volume_force_after_setup(nls):
+    """nls_set_volume_force after nls_setup rebuilds the load vector on the device."""
+    p4, p6 = I.beam_problem(6, 2, 3, 4.0), I.beam_problem(6, 2, 3, 6.0)
+    s = nls.make_solver(p4, coupling="hybrid")
+    s.set_volume_force(p6.f_vol)
+    u, _ = _random_state(p6, 6, 0.01)
+    F = s.eval_F(u, 1.0)
+    Fo = fem.global_residual(fem.Model(p6), u, 1.0)
+    assert np.max(np.abs(F - Fo)) <= 1e-13 * np.max(np.abs(Fo))
 
 
 def test_device_arrays(nls):

@@ -215,3 +215,31 @@ def test_traction_load_total_force():
     # zero displacement: internal forces vanish, so F = -(external load); total vertical load = -tau * 1 * 0.5
     np.testing.assert_allclose(F[1::2].sum(), 1.0, rtol=1e-14)
     assert abs(F[0::2].sum()) < 1e-14
+
+
+def test_volume_load_nodal_shares_and_total():
+    """Constant volume force f on Q1 elements: each element gives each of its nodes f |e| / 4 on a
+    parallelogram, so on the uniform beam mesh an interior node carries f h_x h_y, an edge node half
+    and a corner a quarter; on a distorted quad mesh the total is f times the area (sum_a N_a = 1),
+    the area taken from the shoelace formula."""
+    m, fx = 4, 3.0
+    p = I.beam_problem(m, 2, 2, fx)
+    hx, hy = 1.0 / m, I.BEAM_LENGTH / (I.BEAM_LENGTH * m)
+    model = fem.Model(p)
+    F = fem.global_residual(model, np.zeros(p.n_nodes * 2), load=0.5)
+    # zero displacement: internal forces vanish, F = -(external load) on the free dofs
+    nx = m + 1
+    i, j = np.arange(p.n_nodes) % nx, np.arange(p.n_nodes) // nx
+    ny = int(round(I.BEAM_LENGTH * m))
+    share = np.where((i == 0) | (i == m), 0.5, 1.0) * np.where((j == 0) | (j == ny), 0.5, 1.0)
+    free = fem.free_mask(p).reshape(-1, 2)[:, 0]
+    np.testing.assert_allclose(F[0::2][free], 0.5 * fx * hx * hy * share[free], rtol=1e-13)
+    assert np.all(F[1::2] == 0.0)
+    # distorted mesh: total force = f * area
+    rng = np.random.default_rng(4)
+    X = p.xy[p.conn] + 0.2 * hx * rng.uniform(-1, 1, (p.conn.shape[0], 4, 2))
+    f = np.tile([[1.5, -2.0]], (p.conn.shape[0], 1))
+    fe = fem.volume_load(X, f).reshape(-1, 4, 2)
+    x, y = X[..., 0], X[..., 1]
+    area = 0.5 * np.abs(np.sum(x * np.roll(y, -1, axis=1) - np.roll(x, -1, axis=1) * y, axis=1))
+    np.testing.assert_allclose(fe.sum(axis=1), area[:, None] * f, rtol=1e-13)
