@@ -115,6 +115,11 @@ typedef struct nls_options {
                                  steps, tangent applications, coarse solves) prefetch the
                                  operands of the 32-row block this many blocks ahead into L2;
                                  0 = off, at most 64 (default 4).  Changes no result. */
+  int32_t outer_backtrack;    /* 1: the outer Newton step u <- u - alpha du takes the first of
+                                 alpha = 1, 1/2, ... (at most min(ls_trials, 5)) with ||F(u')|| <
+                                 outer_atol or ||F_x(u')|| <= (1 - armijo alpha) ||F_x(u)||, the last
+                                 trial otherwise; an accepted trial's F_x serves the next outer
+                                 iteration.  0 (default): always the full step, as in the paper. */
 } nls_options;
 
 /* Per-solve report. */

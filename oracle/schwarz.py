@@ -14,7 +14,8 @@ The method follows Section 2 of the paper:
 * exact tangents (Eqs. 6, 7, 12): Q_i(x) = P_i (R_i DF(x) P_i)^-1 R_i DF(x) with P~_i on the
   outside of every local term;
 * the outer loop is Newton's method on F_x(u) = 0 with the tangent system of Eq. 13 solved
-  by restarted GMRES, u <- u - du;
+  by restarted GMRES, u <- u - du (optionally with backtracking on ||F_x||, a reading: the
+  paper states no globalisation of the outer step);
 * the stopping test of the outer loop uses the original residual, ||F(u)||_2 < tol.
 
 Readings where the paper is silent (all listed in the design notes): local and coarse
@@ -61,6 +62,7 @@ class Options:
     outer_atol: float = 1e-8
     outer_maxit: int = 30
     load_steps: int = 1
+    outer_backtrack: bool = False
 
 
 # ----------------------------------------------------------------------------------------------
@@ -307,11 +309,13 @@ class Schwarz:
         steps = max(1, opts.load_steps)
         for step in range(steps):
             load = (step + 1) / steps
+            cached = None  # F_x and its linearisation at u, from the previous step's backtracking
             for k in range(opts.outer_maxit + 1):
                 nF = float(np.linalg.norm(self.F(u, load)))
                 if nF < opts.outer_atol or k == opts.outer_maxit:
                     break
-                Fx, st = self.evaluate(u, load)
+                Fx, st = cached if cached is not None else self.evaluate(u, load)
+                cached = None
                 if not np.any(Fx):
                     break  # every correction is exactly zero: the iteration cannot move any more
                 A = self.tangent(st)
@@ -324,7 +328,25 @@ class Schwarz:
                 history.append(rec)
                 if log:
                     log(rec)
-                u = u - du
+                if not opts.outer_backtrack:
+                    u = u - du
+                    continue
+                # backtracking on ||F_x|| (the reading of the outer step): the first of
+                # alpha = 1, 1/2, ... (at most min(ls_trials, 5)) with ||F(u')|| < outer_atol or
+                # ||F_x(u')|| <= (1 - armijo alpha) ||F_x(u)||; the last trial is taken otherwise
+                nFx, alpha = float(np.linalg.norm(Fx)), 1.0
+                trials = min(opts.ls_trials, 5)
+                for t in range(trials):
+                    ut = u - alpha * du
+                    if float(np.linalg.norm(self.F(ut, load))) < opts.outer_atol:
+                        u = ut
+                        break
+                    Fxt, stt = self.evaluate(ut, load)
+                    nt = float(np.linalg.norm(Fxt))
+                    if (np.isfinite(nt) and nt <= (1.0 - opts.armijo * alpha) * nFx) or t == trials - 1:
+                        u, cached = ut, (Fxt, stt)
+                        break
+                    alpha *= 0.5
             history.append({"load": load, "final_normF": nF})
         return u, history, time.perf_counter() - t0
 

@@ -85,6 +85,7 @@ struct Dev {
   void* A0dinv = nullptr;
   int32_t* cstatus = nullptr;
   // vectors
+  double* ut = nullptr;  // trial point of the outer backtracking
   double *u = nullptr, *x = nullptr, *u0 = nullptr, *Fx = nullptr, *F = nullptr, *t1 = nullptr, *t2 = nullptr,
          *w0 = nullptr, *gx = nullptr;
   double *c = nullptr, *ct = nullptr, *dc = nullptr, *g = nullptr, *gt = nullptr, *cres = nullptr;

@@ -130,6 +130,21 @@ struct LocalPlan {
   size_t xt, racc, red, win, rp, flag, total;
 };
 
+// Shared memory of the harmonic extension (k_harmonic): the table state, the solve vector and
+// the window of dev::band_lu ((b + 2) rows of 2b + 1 entries, reciprocal pivots, flag), FP64.
+__host__ __device__ inline SmemPlan harmonic_plan(int max_n, int max_nt, int max_b) {
+  SmemPlan p;
+  size_t o = 0;
+  p.xt = o; o += align_up(sizeof(double) * max_nt, 16);
+  p.r = p.rt = p.s = p.red = 0;  // unused
+  p.yv = o; o += align_up(sizeof(double) * max_n, 16);
+  p.win = o; o += align_up(sizeof(double) * (size_t)(max_b + 2) * (2 * max_b + 1), 16);
+  p.rp = o; o += align_up(sizeof(double) * (max_b + 2), 16);
+  p.flag = o; o += 16;
+  p.total = o;
+  return p;
+}
+
 template <typename FT>
 __host__ __device__ inline LocalPlan newton_plan(int max_n, int max_nt, int max_b) {
   LocalPlan p;
@@ -561,10 +576,8 @@ __global__ void __launch_bounds__(512) k_local_apply(LocalArgs A) {
 template <int LAW>
 __global__ void __launch_bounds__(256) k_harmonic(LocalArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const SmemPlan P = smem_plan<double>(A.max_n, A.max_nt, A.max_b, true);
+  const SmemPlan P = harmonic_plan(A.max_n, A.max_nt, A.max_b);
   double* xt = (double*)(smem + P.xt);
-  double* q = (double*)(smem + P.r);
-  double* red = (double*)(smem + P.red);
   double* yv = (double*)(smem + P.yv);
   double* win = (double*)(smem + P.win);
   double* rp = (double*)(smem + P.rp);
@@ -602,8 +615,6 @@ __global__ void __launch_bounds__(256) k_harmonic(LocalArgs A) {
     for (int a = tid; a < n; a += blockDim.x) phi[(int64_t)a * nc + lc] = yv[a];
     __syncthreads();
   }
-  (void)q;
-  (void)red;
 }
 
 template <int LAW, typename JT>
@@ -1595,7 +1606,7 @@ void coarse_extension(Context& c) {
   CK(cudaMemcpyAsync(D.x, D.ubc, sizeof(double) * N, cudaMemcpyDeviceToDevice, D.s));
   LocalArgs A = coarse_args(c);
   A.x = D.x;
-  const size_t sm = smem_plan<double>(c.nov.max_n, c.nov.max_nt, c.nov.max_b, true).total;
+  const size_t sm = harmonic_plan(c.nov.max_n, c.nov.max_nt, c.nov.max_b).total;
   need(sm, "coarse harmonic extension");
   if (c.law == NLS_LAW_DIFFUSION) LAUNCH(D, k_harmonic<NLS_LAW_DIFFUSION>, c.nov.count, 256, sm, A);
   else LAUNCH(D, k_harmonic<NLS_LAW_NEOHOOKE>, c.nov.count, 256, sm, A);
@@ -1655,6 +1666,7 @@ int device_setup(Context& c) {
     upload_set(D, c.ov, D.ov, fp32_local(c));
     const int N = (int)c.N;
     D.u = D.alloc<double>(N);
+    D.ut = D.alloc<double>(N);
     D.x = D.alloc<double>(N);
     D.u0 = D.alloc<double>(N);
     D.Fx = D.alloc<double>(N);
@@ -2175,8 +2187,20 @@ int solve(Context& c, double* u_user, int u_dev, nls_report* rep) {
     double t_inner = 0, t_coarse = 0, t_gmres = 0;
     const int L = std::max(1, c.opt.load_steps);
     double nF = INFINITY;
+    // F_x at a point, with the statistics of its local and coarse solves
+    auto eval_fx = [&](const double* x, double load) {
+      FxInfo f = evaluate_Fx(c, x, load, &t_inner, &t_coarse);
+      rp.subdomain_newton_steps += f.local_its;
+      rp.local_chord_steps += f.local_chord;
+      rp.coarse_newton_steps += f.coarse_its;
+      rp.local_failures += f.local_failures;
+      if (rp.first_failed_subdomain < 0) rp.first_failed_subdomain = f.first_failed;
+      return f;
+    };
     for (int step = 1; step <= L && status == NLS_OK; ++step) {
       const double load = (double)step / L;
+      bool have_fx = false;  // D.Fx and the tangent data belong to D.u (from the backtracking)
+      FxInfo fi;
       for (int k = 0;; ++k) {
         global_residual(c, D.u, D.F, load);
         nF = norm2(D, N, D.F);
@@ -2190,12 +2214,8 @@ int solve(Context& c, double* u_user, int u_dev, nls_report* rep) {
           status = NLS_W_NOT_CONVERGED;
           break;
         }
-        FxInfo fi = evaluate_Fx(c, D.u, load, &t_inner, &t_coarse);
-        rp.subdomain_newton_steps += fi.local_its;
-        rp.local_chord_steps += fi.local_chord;
-        rp.coarse_newton_steps += fi.coarse_its;
-        rp.local_failures += fi.local_failures;
-        if (rp.first_failed_subdomain < 0) rp.first_failed_subdomain = fi.first_failed;
+        if (!have_fx) fi = eval_fx(D.u, load);
+        have_fx = false;
         if (fi.pivot_failure) {
           status = NLS_E_PIVOT;
           break;
@@ -2217,7 +2237,33 @@ int solve(Context& c, double* u_user, int u_dev, nls_report* rep) {
         if (c.opt.verbose)
           std::fprintf(stderr, "[nls]   ||Fx|| = %.3e gmres %d (rel %.2e) local its %lld coarse its %d\n", fxn, gr.its,
                        gr.relres, (long long)fi.local_its, fi.coarse_its);
-        LAUNCH(D, k_axpby, grid_for(N), 256, 0, N, 1.0, D.u, -1.0, D.gx, D.u);
+        if (!c.opt.outer_backtrack) {
+          LAUNCH(D, k_axpby, grid_for(N), 256, 0, N, 1.0, D.u, -1.0, D.gx, D.u);
+          continue;
+        }
+        // Backtracking on ||F_x||: the first of alpha = 1, 1/2, ... (at most min(ls_trials, 5))
+        // with ||F(u')|| < outer_atol or ||F_x(u')|| <= (1 - armijo alpha) ||F_x(u)||, u' = u - alpha
+        // du; the last trial is taken otherwise.  An accepted trial's F_x and tangent data serve
+        // the next outer iteration, so a full step costs nothing extra.
+        const int trials = std::max(1, std::min(c.opt.ls_trials, 5));
+        double alpha = 1.0;
+        for (int t = 0; t < trials; ++t) {
+          LAUNCH(D, k_axpby, grid_for(N), 256, 0, N, 1.0, D.u, -alpha, D.gx, D.ut);
+          global_residual(c, D.ut, D.F, load);
+          const double nFt = norm2(D, N, D.F);
+          if (nFt < c.opt.outer_atol) break;
+          const FxInfo ft = eval_fx(D.ut, load);
+          const double fxt = norm2(D, N, D.Fx);
+          if ((std::isfinite(fxt) && fxt <= (1.0 - c.opt.armijo * alpha) * fxn) || t + 1 == trials ||
+              ft.pivot_failure) {
+            fi = ft;
+            have_fx = true;
+            break;
+          }
+          alpha *= 0.5;
+        }
+        if (c.opt.verbose && alpha < 1.0) std::fprintf(stderr, "[nls]   outer step alpha = %.4g\n", alpha);
+        std::swap(D.u, D.ut);
       }
     }
     rp.final_residual = nF;

@@ -169,6 +169,22 @@ def test_beam_solution(nls, f_x):
             assert abs(rep.outer_iterations - outer_o) <= 1
 
 
+def test_outer_backtracking(nls):
+    """With backtracking on ||F_x|| both sides take the same outer steps and reach the same solution."""
+    p = I.beam_problem(6, 2, 3, 7.5)
+    ustar, _ = S.plain_newton(p, tol=1e-12)
+    for coupling in ("hybrid", "add"):
+        sw = S.Schwarz(p, S.Options(coupling=coupling, outer_atol=1e-10, gmres_maxit=100, outer_backtrack=True))
+        _, hist, _ = sw.solve()
+        outer_o = len([h for h in hist if "gmres_its" in h])
+        s = nls.make_solver(p, coupling=coupling, precision="fp64", outer_atol=1e-10, gmres_maxit=100,
+                            outer_backtrack=1)
+        u, rep = s.solve()
+        assert rep.status == 0 and rep.final_residual < 1e-10
+        assert np.linalg.norm(u - ustar) / np.linalg.norm(ustar) < 1e-8
+        assert abs(rep.outer_iterations - outer_o) <= 1
+
+
 def test_volume_force_after_setup(nls):
     """nls_set_volume_force after nls_setup rebuilds the load vector on the device."""
     p4, p6 = I.beam_problem(6, 2, 3, 4.0), I.beam_problem(6, 2, 3, 6.0)
