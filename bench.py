@@ -280,7 +280,8 @@ def run_beam(args):
         s.set_problem(p)
         s.set_coarse(nls.COARSE_RGDSW)
         s.set_options(coupling=nls.COUPLING[coupling], load_steps=1, local_precision=nls.PREC_FP32_IR,
-                      coarse_precision=nls.PREC_FP32_IR, autotune=1, gmres_maxit=100)
+                      coarse_precision=nls.PREC_FP32_IR, autotune=1, gmres_maxit=100,
+                      coarse_rebuild=1 if args.coarse_rebuild else 0)
         t0 = time.perf_counter()
         s.setup()
         setup[coupling] = time.perf_counter() - t0
@@ -323,7 +324,8 @@ def run_beam(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
         "config": {"workload": f"Neo-Hooke beam 5 x 1 (Section 1), {p.conn.shape[0]} Q1 cells "
                                f"({sizes.n_dofs} dofs), {sizes.n_sub} uneven subdomains, overlap 2, clamped ends, "
-                               "volume force, no load steps, GMRES max 100",
+                               "volume force, no load steps, GMRES max 100"
+                               + (", coarse basis rebuilt at every outer iterate" if args.coarse_rebuild else ""),
                    "setup_s": setup, "n_dofs": sizes.n_dofs, "n_sub": sizes.n_sub,
                    "coarse_dofs": sizes.n_coarse_dofs, "max_local_dofs": sizes.max_local_dofs,
                    "max_half_band": sizes.max_half_band, "coarse_half_band": sizes.coarse_half_band,
@@ -567,6 +569,7 @@ def main():
     ap.add_argument("--beam-px", type=int, default=8, help="bricks across the beam")
     ap.add_argument("--beam-py", type=int, default=32, help="bricks along the beam")
     ap.add_argument("--beam-forces", default="4,5,6,7,7.5,8,9,10")
+    ap.add_argument("--coarse-rebuild", action="store_true", help="beam: rebuild the coarse basis at every outer iterate")
     ap.add_argument("--c4-pairs", type=int, default=50000)
     ap.add_argument("--c4-train-steps", type=int, default=4000)
     ap.add_argument("--c4-sweeps", type=int, default=6)

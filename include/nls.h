@@ -120,6 +120,9 @@ typedef struct nls_options {
                                  outer_atol or ||F_x(u')|| <= (1 - armijo alpha) ||F_x(u)||, the last
                                  trial otherwise; an accepted trial's F_x serves the next outer
                                  iteration.  0 (default): always the full step, as in the paper. */
+  int32_t coarse_rebuild;     /* 1: inside nls_solve the RGDSW basis is rebuilt at every outer iterate
+                                 u from DF(u) (the energy-minimising extension of the same interface
+                                 values); 0 (default): built once at setup from DF(u^(0)). */
 } nls_options;
 
 /* Per-solve report. */

@@ -16,6 +16,8 @@ The method follows Section 2 of the paper:
 * the outer loop is Newton's method on F_x(u) = 0 with the tangent system of Eq. 13 solved
   by restarted GMRES, u <- u - du (optionally with backtracking on ||F_x||, a reading: the
   paper states no globalisation of the outer step);
+* the coarse basis is built once from DF(u^(0)), or (option, a reading) rebuilt from DF(u) at
+  every outer iterate u;
 * the stopping test of the outer loop uses the original residual, ||F(u)||_2 < tol.
 
 Readings where the paper is silent (all listed in the design notes): local and coarse
@@ -63,6 +65,7 @@ class Options:
     outer_maxit: int = 30
     load_steps: int = 1
     outer_backtrack: bool = False
+    coarse_rebuild: bool = False
 
 
 # ----------------------------------------------------------------------------------------------
@@ -190,10 +193,11 @@ class Schwarz:
         self.locals = [LocalProblem(self.model, s) for s in self.subs]
         need_coarse = opts.coupling != ONE_LEVEL if with_coarse is None else with_coarse
         self.cs = None
+        self.star = None
         if need_coarse:
-            star = dec.node_star(prob.conn, prob.n_nodes)
+            self.star = dec.node_star(prob.conn, prob.n_nodes)
             K0 = fem.global_jacobian(self.model, np.zeros(self.N))
-            self.cs = coarse_mod.rgdsw_coarse_space(prob, star, K0)
+            self.cs = coarse_mod.rgdsw_coarse_space(prob, self.star, K0)
         self.stats = {"subdomain_newton_steps": 0}
 
     # -- global residual and tangent --------------------------------------------------------
@@ -314,6 +318,9 @@ class Schwarz:
                 nF = float(np.linalg.norm(self.F(u, load)))
                 if nF < opts.outer_atol or k == opts.outer_maxit:
                     break
+                if cached is None and opts.coarse_rebuild and self.cs is not None:
+                    # the coarse basis from the tangent at the current iterate (same interface values)
+                    self.cs = coarse_mod.rgdsw_coarse_space(self.prob, self.star, self.DF(u))
                 Fx, st = cached if cached is not None else self.evaluate(u, load)
                 cached = None
                 if not np.any(Fx):

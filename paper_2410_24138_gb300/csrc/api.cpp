@@ -51,6 +51,7 @@ void nls_options_default(nls_options* o) {
   o->autotune = 0;
   o->l2_prefetch = 4;
   o->outer_backtrack = 0;
+  o->coarse_rebuild = 0;
   o->verbose = 0;
 }
 
@@ -243,6 +244,7 @@ int nls_set_options(nls_ctx* ctx, const nls_options* o) {
     return fail(ctx, NLS_E_ARG, "cuda_graphs, coarse_reuse, local_reuse and autotune must be 0 or 1");
   if (o->l2_prefetch < 0 || o->l2_prefetch > 64) return fail(ctx, NLS_E_ARG, "l2_prefetch must be in [0, 64]");
   if (o->outer_backtrack != 0 && o->outer_backtrack != 1) return fail(ctx, NLS_E_ARG, "outer_backtrack must be 0 or 1");
+  if (o->coarse_rebuild != 0 && o->coarse_rebuild != 1) return fail(ctx, NLS_E_ARG, "coarse_rebuild must be 0 or 1");
   if (ctx->c.is_setup && (o->local_precision != ctx->c.opt.local_precision ||
                           o->coarse_precision != ctx->c.opt.coarse_precision))
     return fail(ctx, NLS_E_ARG, "the factor precisions are fixed by nls_setup; set them before it");

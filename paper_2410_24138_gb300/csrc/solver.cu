@@ -1593,7 +1593,11 @@ void upload_set(Dev& D, const LocalSet& h, DeviceLocalSet& d, bool fp32_factor, 
 // Energy-minimising extension of the interface values of the coarse basis (RGDSW, Section 2)
 // with K = DF(u^(0)), u^(0) = Dirichlet data and zero elsewhere, then the values of P_0 and
 // P_0^T.  The factors of the non-overlapping problems are needed for the extension only.
-void coarse_extension(Context& c) {
+// RGDSW coarse basis: the interface values (host) extended into every non-overlapping
+// subdomain by the energy-minimising (harmonic) extension with DF(x) (k_harmonic), then P_0 and
+// P_0^T gathered.  x = nullptr: the Dirichlet data u^(0) (the basis built once, at setup);
+// otherwise the current outer iterate (coarse_rebuild).
+void coarse_extension(Context& c, const double* x = nullptr) {
   Dev& D = *c.dev;
   Coarse& cs = c.cs;
   const int64_t N = c.N;
@@ -1603,7 +1607,7 @@ void coarse_extension(Context& c) {
   };
   if (!D.nov.factor) D.nov.factor = D.alloc<double>(c.nov.total_factor);
   CK(cudaMemcpyAsync(D.phi, cs.phi_host.data(), sizeof(double) * cs.phi_host.size(), cudaMemcpyHostToDevice, D.s));
-  CK(cudaMemcpyAsync(D.x, D.ubc, sizeof(double) * N, cudaMemcpyDeviceToDevice, D.s));
+  CK(cudaMemcpyAsync(D.x, x ? x : D.ubc, sizeof(double) * N, cudaMemcpyDeviceToDevice, D.s));
   LocalArgs A = coarse_args(c);
   A.x = D.x;
   const size_t sm = harmonic_plan(c.nov.max_n, c.nov.max_nt, c.nov.max_b).total;
@@ -1618,8 +1622,10 @@ void coarse_extension(Context& c) {
   const int64_t np = (int64_t)cs.p0_col.size();
   LAUNCH(D, k_gather_values, grid_for(np), 256, 0, np, D.p0_src, D.phi, D.p0_val);
   LAUNCH(D, k_gather_values32, grid_for(np), 256, 0, np, D.p0t_src, D.p0_val, D.p0t_val);
-  D.release(D.nov.factor);
-  D.nov.factor = nullptr;
+  if (!c.opt.coarse_rebuild) {  // rebuilt every outer iteration otherwise: keep the factor storage
+    D.release(D.nov.factor);
+    D.nov.factor = nullptr;
+  }
 }
 
 int device_setup(Context& c) {
@@ -2214,7 +2220,15 @@ int solve(Context& c, double* u_user, int u_dev, nls_report* rep) {
           status = NLS_W_NOT_CONVERGED;
           break;
         }
-        if (!have_fx) fi = eval_fx(D.u, load);
+        if (!have_fx) {
+          if (c.opt.coarse_rebuild && c.opt.coupling != NLS_COUPLING_ONE && c.coarse_kind == NLS_COARSE_RGDSW) {
+            // the coarse basis from the current tangent: P_0 changes, so does every A_0
+            coarse_extension(c, D.u);
+            D.coarse_fact_valid = false;
+            D.ainv_valid = false;
+          }
+          fi = eval_fx(D.u, load);
+        }
         have_fx = false;
         if (fi.pivot_failure) {
           status = NLS_E_PIVOT;

@@ -35,7 +35,8 @@ class Options(ctypes.Structure):
                 ("threads_per_block", ctypes.c_int32), ("verbose", ctypes.c_int32),
                 ("profile_kernels", ctypes.c_int32), ("cuda_graphs", ctypes.c_int32),
                 ("coarse_reuse", ctypes.c_int32), ("local_reuse", ctypes.c_int32), ("autotune", ctypes.c_int32),
-                ("l2_prefetch", ctypes.c_int32), ("outer_backtrack", ctypes.c_int32)]
+                ("l2_prefetch", ctypes.c_int32), ("outer_backtrack", ctypes.c_int32),
+                ("coarse_rebuild", ctypes.c_int32)]
 
 
 class Report(ctypes.Structure):

@@ -185,6 +185,26 @@ def test_outer_backtracking(nls):
         assert abs(rep.outer_iterations - outer_o) <= 1
 
 
+def test_coarse_rebuild(nls):
+    """The coarse basis rebuilt from DF(u) at every outer iterate: the same outer iteration as the
+    oracle with the same rule (outer counts within one, GMRES totals within 10 %: CGS2 against the
+    oracle's modified Gram-Schmidt) and the same solution."""
+    p = I.beam_problem(6, 2, 3, 7.5)
+    ustar, _ = S.plain_newton(p, tol=1e-12)
+    for coupling in ("hybrid", "add"):
+        sw = S.Schwarz(p, S.Options(coupling=coupling, outer_atol=1e-10, gmres_maxit=100, coarse_rebuild=True))
+        _, hist, _ = sw.solve()
+        outer = [h for h in hist if "gmres_its" in h]
+        gm_o = sum(h["gmres_its"] for h in outer)
+        s = nls.make_solver(p, coupling=coupling, precision="fp64", outer_atol=1e-10, gmres_maxit=100,
+                            coarse_rebuild=1)
+        u, rep = s.solve()
+        assert rep.status == 0 and rep.final_residual < 1e-10
+        assert np.linalg.norm(u - ustar) / np.linalg.norm(ustar) < 1e-8
+        assert abs(rep.outer_iterations - len(outer)) <= 1
+        assert abs(rep.gmres_iterations - gm_o) <= max(2, 0.1 * gm_o)
+
+
 def test_volume_force_after_setup(nls):
     """nls_set_volume_force after nls_setup rebuilds the load vector on the device."""
     p4, p6 = I.beam_problem(6, 2, 3, 4.0), I.beam_problem(6, 2, 3, 6.0)

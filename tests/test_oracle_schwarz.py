@@ -143,3 +143,19 @@ def test_fig1_shape_one_level_grows_two_level_flat():
             counts[nb, coupling] = sum(h["gmres_its"] for h in hist if "gmres_its" in h)
     assert counts[8, S.ONE_LEVEL] > 2 * counts[2, S.ONE_LEVEL]
     assert counts[8, S.HYBRID] < 1.3 * counts[2, S.HYBRID]
+
+
+@pytest.mark.parametrize("coupling", [S.ADDITIVE, S.HYBRID])
+def test_rebuilt_coarse_basis_keeps_the_fixed_point(coupling):
+    """The coarse space only accelerates: rebuilt from DF(u) at every outer iterate, the outer
+    iteration still converges to the plain Newton solution of F(u) = 0 (the beam of Section 1, large
+    deformation), and a basis fitted to the current tangent does not need more GMRES iterations."""
+    p = I.beam_problem(6, 2, 3, 7.5)
+    ustar, _ = S.plain_newton(p, tol=1e-12)
+    its = {}
+    for rebuild in (False, True):
+        sw = S.Schwarz(p, S.Options(coupling=coupling, outer_atol=1e-10, gmres_maxit=100, coarse_rebuild=rebuild))
+        u, hist, _ = sw.solve()
+        assert np.linalg.norm(u - ustar) <= 1e-9 * np.linalg.norm(ustar)
+        its[rebuild] = sum(h["gmres_its"] for h in hist if "gmres_its" in h)
+    assert its[True] <= its[False]
