@@ -361,6 +361,18 @@ def timed_solves(torch, solver, n_dofs, steps, flush_buf):
     return times, reps
 
 
+def replica_throughput(torch, dist, world, total_ms, units, device):
+    """Whole-job throughput of ``world`` independent replicas (one per GPU, no exchange on the data
+    path): the units all ranks processed divided by the slowest rank's time.  Returns (units per
+    second, max ms, summed units); a plain division for one process."""
+    ms_t = torch.tensor([float(total_ms)], device=device, dtype=torch.float64)
+    st_t = torch.tensor([float(units)], device=device, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(st_t, op=dist.ReduceOp.SUM)
+    return st_t.item() / (ms_t.item() * 1e-3), ms_t.item(), st_t.item()
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -410,12 +422,7 @@ def run_gpu(args):
     # the metric counts every local Newton iteration (residual, solve, line search), with or
     # without a fresh factorization; the chord steps (stored factors) are also reported apart
     steps_local = sum(r.subdomain_newton_steps for r in reps)
-    ms_t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-    st_t = torch.tensor([float(steps_local)], device="cuda", dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-        dist.all_reduce(st_t, op=dist.ReduceOp.SUM)
-    value = st_t.item() / (ms_t.item() * 1e-3)
+    value, _, _ = replica_throughput(torch, dist, world, total_ms, steps_local, "cuda")
     rep0 = reps[-1]
 
     # per-kernel timing of one more solve (CUDA events on the launching stream)

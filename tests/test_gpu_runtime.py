@@ -125,3 +125,20 @@ def test_factor_reuse_keeps_the_solution(nls):
     assert np.linalg.norm(ub - ua) <= 1e-6 * np.linalg.norm(ua)
     F = fem.global_residual(fem.Model(p), ub)
     assert np.linalg.norm(F) < 1e-8
+
+
+@pytest.mark.parametrize("coupling", ["one", "hybrid"])
+def test_l2_prefetch_changes_no_result(nls, coupling):
+    """The L2 prefetch of the triangular solves' operands is a hint: solutions and iteration
+    counts are bit-identical with it off and on."""
+    p = _brick()
+    runs = []
+    for dist in (0, 4):
+        s = nls.make_solver(p, coupling=coupling, outer_atol=1e-12, l2_prefetch=dist)
+        u, rep = s.solve()
+        assert rep.status == 0
+        runs.append((u, rep))
+    (u0, r0), (u4, r4) = runs
+    assert np.array_equal(u0, u4)
+    for k in ("outer_iterations", "gmres_iterations", "subdomain_newton_steps", "local_chord_steps"):
+        assert getattr(r0, k) == getattr(r4, k), k
