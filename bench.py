@@ -198,12 +198,14 @@ def run_c4(args):
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
     flush_buf = torch.zeros(64 * 1024 * 1024, dtype=torch.float64, device="cuda")
-    res = {"plain": [], "guess": []}
+    res = {"plain": [], "guess": [], "guess_first_outer": []}
     accepted = proposed = 0
+    counts = {}
     test_seeds = list(range(1001, 1001 + args.steps))
-    for mode in ("plain", "guess"):
-        nls.attach_guess(s, net if mode == "guess" else None, nls.GUESS_USE)
-        if mode == "guess":
+    for mode in ("plain", "guess", "guess_first_outer"):
+        flags = nls.GUESS_USE | (nls.GUESS_FIRST_OUTER if mode == "guess_first_outer" else 0)
+        nls.attach_guess(s, None if mode == "plain" else net, flags)
+        if mode != "plain":
             nls.set_guess_smoothing(s, args.c4_sweeps, 0.8)
         for i, sd in enumerate([1001, 1002, 1003] + test_seeds):  # the first three warm up
             s.set_coefficients(*I.c4_elem_coefficients(sd, n))
@@ -215,26 +217,31 @@ def run_c4(args):
             u, rep = s.solve(u)
             e1.record()
             e1.synchronize()
-            if mode == "guess":
+            if mode != "plain":
                 p_, a_ = nls.guess_counts(s)
             if i >= 3:
                 res[mode].append((e0.elapsed_time(e1), rep.subdomain_newton_steps - rep.local_chord_steps,
                                   rep.outer_iterations, rep.final_residual, rep.local_chord_steps,
                                   rep.subdomain_newton_steps))
+                if mode != "plain":
+                    pc, ac = counts.get(mode, (0, 0))
+                    counts[mode] = (pc + p_, ac + a_)
                 if mode == "guess":
                     proposed += p_
                     accepted += a_
     ms_plain = sum(r[0] for r in res["plain"])
     ms_guess = sum(r[0] for r in res["guess"])
+    ms_first = sum(r[0] for r in res["guess_first_outer"])
     st_plain = sum(r[1] for r in res["plain"])
     st_guess = sum(r[1] for r in res["guess"])
     line = {
-        "metric": METRIC, "value": sum(r[5] for r in res["guess"]) / (ms_guess * 1e-3), "unit": UNIT, "n_gpus": 1,
-        "steps": args.steps,
-        "warmup": 3, "ms_per_step": ms_guess / args.steps, "higher_is_better": True, "scaling": "weak",
+        "metric": METRIC, "value": sum(r[5] for r in res["guess_first_outer"]) / (ms_first * 1e-3), "unit": UNIT,
+        "n_gpus": 1, "steps": args.steps,
+        "warmup": 3, "ms_per_step": ms_first / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64+f32 (bf16 network training)", "data": "synthetic",
         "config": {"workload": "log-normal diffusion 512x512 P1 (263k dofs), 256 uneven subdomains, overlap 2; "
-                               "learned initial guess", "coupling": "hybrid",
+                               "learned initial guess proposed at the first outer iteration of every solve",
+                   "coupling": "hybrid",
                    "l2": "512 MB buffer written between steps", "setup_s": setup_s,
                    "n_dofs": sizes.n_dofs, "n_sub": sizes.n_sub, "coarse_dofs": sizes.n_coarse_dofs},
         "guess": {"pairs": net.pairs(), "harvest_solves": harvest_solves, "harvest_s": harvest_s,
@@ -248,6 +255,12 @@ def run_c4(args):
                                            "guess": sum(r[4] for r in res["guess"])},
                      "outer_iterations": {"plain": [r[2] for r in res["plain"]], "guess": [r[2] for r in res["guess"]]},
                      "max_final_residual": max(r[3] for r in res["plain"] + res["guess"])},
+        "held_out_first_outer_only": {
+            "time_to_solution_ms": sum(r[0] for r in res["guess_first_outer"]) / args.steps,
+            "full_newton_steps": sum(r[1] for r in res["guess_first_outer"]),
+            "local_chord_steps": sum(r[4] for r in res["guess_first_outer"]),
+            "proposed_accepted": counts.get("guess_first_outer"),
+            "max_final_residual": max(r[3] for r in res["guess_first_outer"])},
         "tuning": s.tuning(),
     }
     print(json.dumps(line), flush=True)

@@ -323,6 +323,8 @@ typedef struct nls_guess_net nls_guess_net;
 #define NLS_GUESS_OUTPUTS 1024
 #define NLS_GUESS_USE 1      /* propose starting points in nls_solve / nls_eval_Fx */
 #define NLS_GUESS_HARVEST 2  /* record (features, converged local state) pairs after every local solve */
+#define NLS_GUESS_FIRST_OUTER 4  /* with NLS_GUESS_USE: propose only at the first outer iteration of each
+                                    load step of nls_solve (later iterations start from R_i u) */
 
 /* Create a network with hidden widths h1, h2 (multiples of 16), weights drawn from splitmix64
  * `seed`, on `device`, with room for `capacity` training pairs. */

@@ -114,7 +114,8 @@ struct Dev {
   // GMRES iteration graphs, one per Krylov index, valid while `graph_key` matches
   cudaStream_t cap = nullptr;  // private stream the graphs are captured on
   cudaStream_t s2 = nullptr;   // second stream: the tangent phase's coarse work
-  bool coarse_beside = false;  // a coarse factorization runs on s2 during the next local Newton launch
+  bool coarse_beside = false;
+  int outer_k = 0;  // outer iteration of the current load step inside nls_solve (-1 outside)  // a coarse factorization runs on s2 during the next local Newton launch
   cudaEvent_t ev_u0 = nullptr, ev_coarse = nullptr;
   std::vector<cudaGraphExec_t> it_exec;
   std::vector<int64_t> it_launches;

@@ -715,6 +715,7 @@ GuessProposal guess_propose(Context& c, const double* x, double load) {
   GuessCtx* G = (GuessCtx*)D.guess;
   GuessProposal out;
   if (!G || !(G->mode & NLS_GUESS_USE) || !G->net) return out;
+  if ((G->mode & NLS_GUESS_FIRST_OUTER) && D.outer_k > 0) return out;
   GuessNet& N = *G->net;
   N.ensure_batch(G->nsub);
   GeoArgs a = geo_args(c, *G, x, load);

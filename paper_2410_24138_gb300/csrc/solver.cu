@@ -2227,7 +2227,9 @@ int solve(Context& c, double* u_user, int u_dev, nls_report* rep) {
             D.coarse_fact_valid = false;
             D.ainv_valid = false;
           }
+          D.outer_k = k;
           fi = eval_fx(D.u, load);
+          D.outer_k = -1;
         }
         have_fx = false;
         if (fi.pivot_failure) {
@@ -2266,7 +2268,9 @@ int solve(Context& c, double* u_user, int u_dev, nls_report* rep) {
           global_residual(c, D.ut, D.F, load);
           const double nFt = norm2(D, N, D.F);
           if (nFt < c.opt.outer_atol) break;
+          D.outer_k = k + 1;  // a trial point: the next outer iterate
           const FxInfo ft = eval_fx(D.ut, load);
+          D.outer_k = -1;
           const double fxt = norm2(D, N, D.Fx);
           if ((std::isfinite(fxt) && fxt <= (1.0 - c.opt.armijo * alpha) * fxn) || t + 1 == trials ||
               ft.pivot_failure) {

@@ -381,7 +381,7 @@ class Solver:
         return out
 
 
-GUESS_USE, GUESS_HARVEST = 1, 2
+GUESS_USE, GUESS_HARVEST, GUESS_FIRST_OUTER = 1, 2, 4
 GUESS_FEATURES, GUESS_OUTPUTS = 391, 1024
 
 

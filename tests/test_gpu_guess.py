@@ -84,6 +84,22 @@ def test_garbage_network_does_not_change_the_solution(nls):
     assert np.linalg.norm(u - u_ref) <= 1e-6 * np.linalg.norm(u_ref)
 
 
+def test_first_outer_policy_proposes_once_per_load_step(nls):
+    """NLS_GUESS_FIRST_OUTER: proposals only at the first outer iteration of each load step; the
+    solution is the method's own."""
+    p = _c4_family(1001, n=96, per=3)
+    ref = nls.make_solver(p, coupling="hybrid")
+    u_ref, _ = ref.solve()
+    s = nls.make_solver(p, coupling="hybrid")
+    net = nls.GuessNet(h1=32, h2=32, seed=9)
+    nls.attach_guess(s, net, nls.GUESS_USE | nls.GUESS_FIRST_OUTER)
+    u, rep = s.solve()
+    proposed, _ = nls.guess_counts(s)
+    assert rep.status == 0 and rep.outer_iterations >= 2
+    assert proposed == p.n_sub
+    assert np.linalg.norm(u - u_ref) <= 1e-6 * np.linalg.norm(u_ref)
+
+
 def _train(nls, seeds, fscale):
     net = nls.GuessNet(h1=256, h2=256, seed=11, capacity=20000)
     for seed in seeds:
