@@ -201,6 +201,7 @@ def run_c4(args):
     res = {"plain": [], "guess": [], "guess_first_outer": []}
     accepted = proposed = 0
     counts = {}
+    launches = 0
     test_seeds = list(range(1001, 1001 + args.steps))
     for mode in ("plain", "guess", "guess_first_outer"):
         flags = nls.GUESS_USE | (nls.GUESS_FIRST_OUTER if mode == "guess_first_outer" else 0)
@@ -223,6 +224,8 @@ def run_c4(args):
                 res[mode].append((e0.elapsed_time(e1), rep.subdomain_newton_steps - rep.local_chord_steps,
                                   rep.outer_iterations, rep.final_residual, rep.local_chord_steps,
                                   rep.subdomain_newton_steps))
+                if mode == "guess_first_outer":
+                    launches += rep.kernel_launches
                 if mode != "plain":
                     pc, ac = counts.get(mode, (0, 0))
                     counts[mode] = (pc + p_, ac + a_)
@@ -262,6 +265,7 @@ def run_c4(args):
             "proposed_accepted": counts.get("guess_first_outer"),
             "max_final_residual": max(r[3] for r in res["guess_first_outer"])},
         "tuning": s.tuning(),
+        "gpu_launches": launches,
     }
     print(json.dumps(line), flush=True)
 
