@@ -238,3 +238,23 @@ def test_bad_arguments(nls):
     with pytest.raises(nls.NLSError):
         s.set_options(coupling=1)  # additive without a coarse space
         s.setup()
+
+
+def test_failures_are_reported_not_hidden(nls):
+    """Host-side fault injection: a NaN planted in the initial state ends the solve with
+    NLS_E_DIVERGED; local solves forced to fail (no Newton iteration allowed) leave no correction
+    and the solve stops as not converged with the failures counted; neither hangs the device, and
+    the context stays usable for a correct solve afterwards."""
+    p = I.diffusion_c1()
+    s = nls.make_solver(p, coupling="hybrid")
+    u0 = np.zeros(p.n_nodes)
+    u0[100] = np.nan
+    with pytest.raises(nls.NLSError) as ex:
+        s.solve(u0)
+    assert ex.value.status == -8  # NLS_E_DIVERGED
+    s.set_options(inner_maxit=0)
+    _, rep = s.solve()
+    assert rep.status == 1 and rep.local_failures > 0 and rep.final_residual > 1e-8
+    s.set_options(inner_maxit=50)
+    u, rep = s.solve()
+    assert rep.status == 0 and rep.final_residual < 1e-8
