@@ -1126,7 +1126,12 @@ double dot(Dev& D, int64_t n, const double* x, const double* y) {
   return D.h_scal[0];
 }
 
-double norm2(Dev& D, int64_t n, const double* x) { return std::sqrt(std::max(0.0, dot(D, n, x, x))); }
+// A NaN or infinite sum of squares stays non-finite (std::max(0.0, NaN) would give 0: a NaN state
+// must never read as converged).
+double norm2(Dev& D, int64_t n, const double* x) {
+  const double d = dot(D, n, x, x);
+  return std::isfinite(d) ? std::sqrt(std::max(0.0, d)) : d;
+}
 
 // ---- global residual / Jacobian ------------------------------------------------------------
 void global_residual(Context& c, const double* x, double* F, double load) {
