@@ -542,10 +542,13 @@ def fp32_peak_tflops(peaks):
 
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch, from the ncu
-# captures summarised in profiles/ (first launch of a solve of the 1024 x 1024 diffusion
-# workload); a kernel changed since its capture has no entry.
+# captures summarised in profiles/: the first launch of a solve of the 1024 x 1024 diffusion
+# workload, and for the Neo-Hooke kernel the mean over the 17 launches of one solve of the
+# 512 x 512 workload (its launches differ by load step); a kernel changed since its capture
+# has no entry.
 NCU_TRAFFIC_BYTES = {
     "k_local_newton<diffusion, float, 128>": 7.337879e9 + 4.212179e9,
+    "k_local_newton<neohooke, float, 256>": 5.707471e9 + 2.054406e9,
     "k_local_apply<float>": 2.434448e9 + 0.073884e9,
 }
 
