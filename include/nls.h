@@ -183,6 +183,16 @@ int nls_set_volume_force(nls_ctx* ctx, const double* f_vol);
  * NLS_LAW_NEOHOOKE: params = {E, nu}; k_elem, f_elem must be NULL. */
 int nls_set_material(nls_ctx* ctx, int law, const double* params, const double* k_elem, const double* f_elem);
 
+/* Which Lame lambda the 2D Neo-Hooke law of Eq. 2 uses with mu = E / (2 (1 + nu)).
+ * NLS_LAMBDA_PRINTED (the default, and what nls_set_material restores): the lambda the paper
+ * prints, E nu / ((1 + nu)(1 - 2 nu)).  NLS_LAMBDA_PLANE_STRESS: the plane-stress reduction
+ * lambda* = 2 mu lambda / (lambda + 2 mu) (= E nu / (1 - nu^2)), for Section 1's "plane stress"
+ * taken literally.  Call after nls_set_material and before nls_setup (a later call marks the
+ * context as not set up).  NLS_E_ARG for another law or an unknown mode. */
+#define NLS_LAMBDA_PRINTED 0
+#define NLS_LAMBDA_PLANE_STRESS 1
+int nls_set_lambda_mode(nls_ctx* ctx, int mode);
+
 /* Non-overlapping element partition elem_to_sub [n_elems] with ids 0..n_sub-1, grown by
  * `overlap` >= 1 layers of node-sharing elements (Section 2: element-based overlap). */
 int nls_set_partition(nls_ctx* ctx, int32_t n_sub, const int32_t* elem_to_sub, int32_t overlap);

@@ -20,13 +20,17 @@ from __future__ import annotations
 import numpy as np
 import scipy.sparse as sp
 
-from paper_2410_24138_gb300.inputs import LAW_DIFFUSION, LAW_NEOHOOKE, Problem
+from paper_2410_24138_gb300.inputs import LAMBDA_PLANE_STRESS, LAW_DIFFUSION, LAW_NEOHOOKE, Problem
 
 
-def lame(young: float, poisson: float):
-    """(mu, lambda) of the compressible Neo-Hooke law, Eq. 2."""
+def lame(young: float, poisson: float, plane_stress: bool = False):
+    """(mu, lambda) of the compressible Neo-Hooke law, Eq. 2: lambda as printed, or (plane_stress)
+    reduced so that the out-of-plane stress of the linearised law vanishes, lambda* = 2 mu lambda /
+    (lambda + 2 mu)."""
     mu = young / (2.0 * (1.0 + poisson))
     lam = young * poisson / ((1.0 + poisson) * (1.0 - 2.0 * poisson))
+    if plane_stress:
+        lam = 2.0 * mu * lam / (lam + 2.0 * mu)
     return mu, lam
 
 
@@ -172,7 +176,7 @@ class Model:
         n_el = prob.conn.shape[0]
         self.k = np.ones(n_el) if prob.k_elem is None else np.asarray(prob.k_elem, dtype=np.float64)
         self.f = np.ones(n_el) if prob.f_elem is None else np.asarray(prob.f_elem, dtype=np.float64)
-        self.mu, self.lam = lame(prob.young, prob.poisson)
+        self.mu, self.lam = lame(prob.young, prob.poisson, prob.lambda_mode == LAMBDA_PLANE_STRESS)
         self.fvol = None if prob.f_vol is None else np.asarray(prob.f_vol, dtype=np.float64).reshape(n_el, 2)
 
     def element_terms(self, elems: np.ndarray, Xe: np.ndarray, ue: np.ndarray, want_jac: bool = True,

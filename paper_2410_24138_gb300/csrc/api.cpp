@@ -174,8 +174,19 @@ int nls_set_material(nls_ctx* ctx, int law, const double* params, const double* 
   }
   c.law = law;
   c.f_vol.clear();
+  c.lambda_mode = NLS_LAMBDA_PRINTED;
   c.have_material = true;
   c.is_setup = false;
+  return NLS_OK;
+}
+
+int nls_set_lambda_mode(nls_ctx* ctx, int mode) {
+  if (!ctx || !ctx->c.have_material) return fail(ctx, NLS_E_ARG, "set the material first");
+  Context& c = ctx->c;
+  if (c.law != NLS_LAW_NEOHOOKE) return fail(ctx, NLS_E_ARG, "the lambda mode applies to the Neo-Hooke law");
+  if (mode != NLS_LAMBDA_PRINTED && mode != NLS_LAMBDA_PLANE_STRESS) return fail(ctx, NLS_E_ARG, "unknown lambda mode");
+  if (mode != c.lambda_mode) c.is_setup = false;
+  c.lambda_mode = mode;
   return NLS_OK;
 }
 

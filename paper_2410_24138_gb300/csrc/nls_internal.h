@@ -105,6 +105,7 @@ struct Context {
   std::vector<int32_t> tr_edges;
   std::vector<double> tr_vals;
   double young = 210.0, poisson = 0.3;
+  int lambda_mode = NLS_LAMBDA_PRINTED;
   std::vector<double> k_elem, f_elem;
   std::vector<double> f_vol;        // Neo-Hooke volume force per element (fx, fy), load factor 1
   int32_t n_sub = 0, overlap = 1;
@@ -132,6 +133,15 @@ struct Context {
 
 // setup.cpp
 int build_setup(Context& c);
+// Lame parameters of Eq. 2: mu = E / (2 (1 + nu)); lambda as printed, E nu / ((1 + nu)(1 - 2 nu)),
+// or its plane-stress reduction 2 mu lambda / (lambda + 2 mu) (NLS_LAMBDA_PLANE_STRESS).
+inline void lame(const Context& c, double& mu, double& lam) {
+  const double E = c.young, nu = c.poisson;
+  mu = E / (2.0 * (1.0 + nu));
+  lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+  if (c.lambda_mode == NLS_LAMBDA_PLANE_STRESS) lam = 2.0 * mu * lam / (lam + 2.0 * mu);
+}
+
 void build_fext(Context& c);
 int device_set_coefficients(Context& c);  // after nls_setup: new k / f on the device, coarse basis rebuilt
 int device_upload_fext(Context& c);       // after nls_setup: the rebuilt external load vector to the device

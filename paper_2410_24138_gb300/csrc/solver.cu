@@ -1085,9 +1085,7 @@ LocalArgs make_args(const Context& c, const LocalSet& hs, const DeviceLocalSet& 
   A.geom = D.geom;
   A.kcoef = D.kcoef;
   A.fext = D.fext;
-  const double E = c.young, nu = c.poisson;
-  A.mu = E / (2.0 * (1.0 + nu));
-  A.lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+  lame(c, A.mu, A.lam);
   A.load = 1.0;
   A.ndof = c.ndof;
   A.nen = c.nen;
@@ -1136,8 +1134,8 @@ double norm2(Dev& D, int64_t n, const double* x) {
 // ---- global residual / Jacobian ------------------------------------------------------------
 void global_residual(Context& c, const double* x, double* F, double load) {
   Dev& D = *c.dev;
-  const double E = c.young, nu = c.poisson;
-  const double mu = E / (2.0 * (1.0 + nu)), lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+  double mu, lam;
+  lame(c, mu, lam);
   if (c.law == NLS_LAW_DIFFUSION)
     LAUNCH(D, k_elem_residual<NLS_LAW_DIFFUSION>, grid_for(c.n_elems), 256, 0, c.n_elems, D.conn, D.geom, D.kcoef, x,
            D.Re, mu, lam, D.bad);
@@ -1150,8 +1148,8 @@ void global_residual(Context& c, const double* x, double* F, double load) {
 
 void global_jacobian(Context& c, const double* x) {
   Dev& D = *c.dev;
-  const double E = c.young, nu = c.poisson;
-  const double mu = E / (2.0 * (1.0 + nu)), lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+  double mu, lam;
+  lame(c, mu, lam);
   CK(cudaMemsetAsync(D.g_val, 0, sizeof(double) * c.g_col.size(), D.s));
   for (size_t k = 0; k + 1 < c.g_color_ptr.size(); ++k) {
     const int e0 = c.g_color_ptr[k], e1 = c.g_color_ptr[k + 1];

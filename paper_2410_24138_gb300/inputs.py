@@ -34,6 +34,8 @@ P1_TRI = 1
 Q1_QUAD = 2
 LAW_DIFFUSION = 1
 LAW_NEOHOOKE = 2
+LAMBDA_PRINTED = 0        # Eq. 2 with the Lame lambda as printed
+LAMBDA_PLANE_STRESS = 1   # Eq. 2 with the plane-stress reduction of lambda
 
 
 class SplitMix64:
@@ -228,6 +230,7 @@ class Problem:
     f_vol: Optional[np.ndarray] = None            # [n_elems, 2] Neo-Hooke volume force per unit area, load factor 1
     young: float = 210.0
     poisson: float = 0.3
+    lambda_mode: int = LAMBDA_PRINTED
     load_steps: int = 1
 
     @property

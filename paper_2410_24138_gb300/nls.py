@@ -13,7 +13,7 @@ from typing import Optional
 import numpy as np
 
 from . import build as _build
-from .inputs import LAW_DIFFUSION, LAW_NEOHOOKE, Problem
+from .inputs import LAMBDA_PLANE_STRESS, LAMBDA_PRINTED, LAW_DIFFUSION, LAW_NEOHOOKE, Problem
 
 P1_TRI, Q1_QUAD = 1, 2
 COUPLING = {"one": 0, "add": 1, "hybrid": 2}
@@ -95,7 +95,7 @@ EXPORTS = ["nls_options_default", "nls_create", "nls_destroy", "nls_strerror", "
            "nls_guess_attach", "nls_guess_train", "nls_guess_pairs", "nls_guess_get_params", "nls_guess_set_params",
            "nls_guess_get_normalisation", "nls_guess_set_normalisation", "nls_guess_gradient", "nls_guess_forward",
            "nls_guess_counts", "nls_get_tuning", "nls_guess_set_smoothing", "nls_set_coefficients",
-           "nls_set_volume_force"]
+           "nls_set_volume_force", "nls_set_lambda_mode"]
 
 _LIB = None
 _P = ctypes.c_void_p
@@ -126,6 +126,7 @@ def load() -> ctypes.CDLL:
         "nls_set_traction": (ctypes.c_int, [_P, i64, _P, _P]),
         "nls_set_material": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P]),
         "nls_set_volume_force": (ctypes.c_int, [_P, _P]),
+        "nls_set_lambda_mode": (ctypes.c_int, [_P, ctypes.c_int]),
         "nls_set_partition": (ctypes.c_int, [_P, i32, _P, i32]),
         "nls_set_coarse": (ctypes.c_int, [_P, ctypes.c_int]),
         "nls_set_options": (ctypes.c_int, [_P, ctypes.POINTER(Options)]),
@@ -239,6 +240,8 @@ class Solver:
         else:
             params = np.array([p.young, p.poisson], dtype=np.float64)
             self._check(self.lib.nls_set_material(self.h, law, _ptr(params), None, None), "nls_set_material")
+            if p.lambda_mode != LAMBDA_PRINTED:
+                self.set_lambda_mode(p.lambda_mode)
             if p.f_vol is not None:
                 self.set_volume_force(p.f_vol)
         dofs = np.ascontiguousarray(p.dirichlet_dofs(), dtype=np.int64)
@@ -353,6 +356,10 @@ class Solver:
         """Neo-Hooke volume force per element [n_elems, 2] at load factor 1 (None removes it)."""
         f = None if f_vol is None else np.ascontiguousarray(f_vol, dtype=np.float64).reshape(-1)
         self._check(self.lib.nls_set_volume_force(self.h, _ptr(f)), "nls_set_volume_force")
+
+    def set_lambda_mode(self, mode: int):
+        """Lame lambda of Eq. 2: LAMBDA_PRINTED or LAMBDA_PLANE_STRESS (before setup)."""
+        self._check(self.lib.nls_set_lambda_mode(self.h, int(mode)), "nls_set_lambda_mode")
 
     def set_coefficients(self, k_elem=None, f_elem=None):
         """New per-element k and f (diffusion), keeping the maps of the current setup."""

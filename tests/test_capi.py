@@ -147,3 +147,16 @@ def test_volume_force_validation(nls):
         s2.set_volume_force(bad)
     s2.set_volume_force(None)
     s2.set_volume_force(b.f_vol)
+
+
+def test_lambda_mode_validation(nls):
+    s = nls.Solver()
+    s.set_problem(I.diffusion_c1())
+    with pytest.raises(nls.NLSError):  # the diffusion law has no Lame lambda
+        s.set_lambda_mode(nls.LAMBDA_PLANE_STRESS)
+    s2 = nls.Solver()
+    s2.set_problem(I.neohooke_problem(8, I.brick_partition(8, 2, 2, 1), 4, 1, traction_max=1.0))
+    with pytest.raises(nls.NLSError):
+        s2.set_lambda_mode(7)
+    s2.set_lambda_mode(nls.LAMBDA_PLANE_STRESS)
+    s2.set_lambda_mode(nls.LAMBDA_PRINTED)

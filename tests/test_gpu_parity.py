@@ -258,3 +258,31 @@ def test_failures_are_reported_not_hidden(nls):
     s.set_options(inner_maxit=50)
     u, rep = s.solve()
     assert rep.status == 0 and rep.final_residual < 1e-8
+
+
+def test_plane_stress_lambda(nls):
+    """NLS_LAMBDA_PLANE_STRESS: F(u), F_x and the tangent against the oracle with the reduced Lame
+    lambda (FP64 bounds), the converged load-stepped solution against the oracle's plain Newton
+    (1e-8); at the same state the printed lambda gives a visibly different residual."""
+    import dataclasses
+    base = _small_problems()["nh"]
+    p = dataclasses.replace(base, lambda_mode=I.LAMBDA_PLANE_STRESS)
+    u, _ = _random_state(p, 2, 0.01)
+    load = 0.6
+    s = nls.make_solver(p, coupling="hybrid", precision="fp64", **TIGHT)
+    F = s.eval_F(u, load)
+    Fo = fem.global_residual(fem.Model(p), u, load)
+    assert np.max(np.abs(F - Fo)) <= 1e-13 * np.max(np.abs(Fo))
+    assert np.max(np.abs(fem.global_residual(fem.Model(base), u, load) - Fo)) > 1e-3 * np.max(np.abs(Fo))
+    sw = S.Schwarz(p, S.Options(coupling="hybrid", **TIGHT))
+    Fx, its, st = s.eval_Fx(u, load)
+    Fxo, sto = sw.evaluate(u, load)
+    assert np.all(st == 0)
+    assert np.linalg.norm(Fx - Fxo) <= 1e-9 * np.linalg.norm(Fxo)
+    v, _ = _random_state(p, 3, 1.0)
+    assert np.linalg.norm(s.apply_tangent(v) - sw.tangent(sto)(v)) <= 1e-9 * np.linalg.norm(sw.tangent(sto)(v))
+    ustar, _ = S.plain_newton(p, tol=1e-12, load_steps=p.load_steps)
+    s2 = nls.make_solver(p, coupling="hybrid", precision="fp64", outer_atol=1e-10, gmres_maxit=100)
+    u2, rep = s2.solve()
+    assert rep.status == 0
+    assert np.linalg.norm(u2 - ustar) / np.linalg.norm(ustar) < 1e-8

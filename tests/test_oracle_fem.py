@@ -208,6 +208,36 @@ def test_neohooke_uniaxial_stretch_closed_form():
     np.testing.assert_allclose(fem.lame(210.0, 0.3), (210.0 / 2.6, 210.0 * 0.3 / (1.3 * 0.4)), rtol=1e-15)
 
 
+def test_plane_stress_lambda_is_the_textbook_constant():
+    """The plane-stress reduction lambda* = 2 mu lambda / (lambda + 2 mu) equals the textbook
+    plane-stress Lame constant E nu / (1 - nu^2); mu is unchanged."""
+    for E, nu in ((210.0, 0.3), (1.0, 0.45), (70.0, 0.0)):
+        mu, lam = fem.lame(E, nu, plane_stress=True)
+        np.testing.assert_allclose(lam, E * nu / (1.0 - nu * nu), rtol=1e-14, atol=1e-300)
+        np.testing.assert_allclose(mu, fem.lame(E, nu)[0], rtol=1e-15)
+
+
+@pytest.mark.parametrize("plane_stress", [True, False])
+def test_uniaxial_stress_modulus_and_contraction(plane_stress):
+    """A small uniaxial stress state: stretch eps along x, the transverse stretch eta found from
+    P_yy = 0.  With the plane-stress lambda the 2D modulus P_xx / eps is Young's E and the
+    contraction -eta / eps is nu; with the printed (plane-strain) lambda they are E / (1 - nu^2)
+    and nu / (1 - nu) (both to O(eps))."""
+    from scipy.optimize import brentq
+    E, nu, eps = 210.0, 0.3, 1e-6
+    mu, lam = fem.lame(E, nu, plane_stress=plane_stress)
+
+    def stress(eta):
+        return fem.neohooke_stress(np.array([[1.0 + eps, 0.0], [0.0, 1.0 + eta]]), mu, lam)[0]
+
+    eta = brentq(lambda t: stress(t)[1, 1], -10 * eps, 10 * eps, xtol=1e-18, rtol=1e-15)
+    modulus, contraction = stress(eta)[0, 0] / eps, -eta / eps
+    if plane_stress:
+        np.testing.assert_allclose([modulus, contraction], [E, nu], rtol=1e-4)
+    else:
+        np.testing.assert_allclose([modulus, contraction], [E / (1 - nu * nu), nu / (1 - nu)], rtol=1e-4)
+
+
 def test_traction_load_total_force():
     p = I.neohooke_c3(n=8, per_side=2, traction_max=2.0)
     model = fem.Model(p)
