@@ -11,8 +11,9 @@ their local Newton loops to 1e-14, so the bounds are those of the small-size tes
 F_x, 1e-7 for the tangent (FP32 factors refined to 1e-10), and local iteration counts within
 one.
 
-The 512 x 512 Neo-Hooke workload (Eq. 2, Q1, 0.53M dofs, 256 uneven subdomains, overlap 2) is
-checked the same way on five subdomains, at the first load step's traction (load factor 0.2) and
+The 512 x 512 Neo-Hooke workload (Eq. 2, Q1, 0.53M dofs, 256 uneven subdomains, overlap 2), and
+the local path of the 2048 x 2048 one (8.4M dofs, 4096 subdomains; its coarse problem is not
+built), are checked the same way on five subdomains, at the first load step's traction (load factor 0.2) and
 a smooth bending state u_y = -0.02 x^2 with a seeded perturbation of 1e-5 (no element near
 inversion).  At h = 1/512 the local residuals cannot be driven to 1e-14 (the line search stalls at
 the rounding floor of the stiffness, E = 210), so both sides stop at 1e-12 relative / 1e-13
@@ -73,9 +74,10 @@ def _local_condition(lp, res, points):
     return abs(lmax / lmin)
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_full_size_neohooke_sampled_local_corrections_and_tangent(nls, precision):
-    p = I.neohooke_c3()
+@pytest.mark.parametrize("workload,precision", [("c3", "fp64"), ("c3", "fp32"), ("c5", "fp32")])
+def test_full_size_neohooke_sampled_local_corrections_and_tangent(nls, workload, precision):
+    # c5: the 2048 x 2048 workload (8.4M dofs, 4096 subdomains) on its local path only
+    p = I.neohooke_c3() if workload == "c3" else I.neohooke_c5()
     tight = dict(inner_rtol=1e-12, inner_atol=1e-13)
     s = nls.make_solver(p, coupling="one", precision=precision, autotune=1, **tight)
     rng = np.random.default_rng(2410)
