@@ -160,3 +160,10 @@ def test_lambda_mode_validation(nls):
         s2.set_lambda_mode(7)
     s2.set_lambda_mode(nls.LAMBDA_PLANE_STRESS)
     s2.set_lambda_mode(nls.LAMBDA_PRINTED)
+    # a new mode after setup invalidates it (the coarse basis and the local operators depend on it):
+    # the next solve is refused before any device work
+    s3 = nls.make_solver(I.neohooke_problem(8, I.brick_partition(8, 2, 2, 1), 4, 1, traction_max=1.0),
+                         setup="host")
+    s3.set_lambda_mode(nls.LAMBDA_PLANE_STRESS)
+    with pytest.raises(nls.NLSError, match="setup"):
+        s3.solve()
