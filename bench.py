@@ -352,6 +352,94 @@ def run_beam(args):
     print(json.dumps(line), flush=True)
 
 
+def run_c5_local(args):
+    """The 2048 x 2048 Neo-Hooke workload's local path: one F_1 evaluation (Eq. 5) per step, i.e.
+    every subdomain's local Newton solve (Eq. 4) batched in one launch plus the refactorization at
+    its converged state, from a smooth bending state u_y = -0.02 x^2 at the first load step's
+    traction.  The two-level solve of this workload is not run: its coarse band is beyond the
+    coarse factorization."""
+    import torch
+    from paper_2410_24138_gb300 import build, inputs as I, nls
+    torch.cuda.set_device(0)
+    build.build()
+    p = I.neohooke_c5()
+    stream = torch.cuda.current_stream()
+    s = nls.Solver(device=0, stream=stream.cuda_stream)
+    s.set_problem(p)
+    s.set_coarse(nls.COARSE_NONE)
+    # per-kernel statistics on (set before setup): CUDA events around the few launches of an
+    # evaluation, whose one local Newton launch takes a quarter of a second
+    s.set_options(coupling=nls.COUPLING["one"], local_precision=nls.PREC_FP32_IR,
+                  coarse_precision=nls.PREC_FP32_IR, autotune=1, profile_kernels=1)
+    t0 = time.perf_counter()
+    s.setup()
+    setup_s = time.perf_counter() - t0
+    sizes = s.sizes()
+    load = 0.2
+    u = np.zeros(p.n_nodes * 2)
+    u[1::2] = -0.02 * p.xy[:, 0] ** 2  # zero on the clamped edge x = 0
+    ud = torch.from_numpy(u).cuda()
+    flush = torch.zeros(64 * 1024 * 1024, dtype=torch.float64, device="cuda")
+
+    def device_step():
+        flush.add_(1.0)  # 512 MB written between steps
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, its, st = s.eval_Fx(ud, load)
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1), int(its.sum()), int((st != 0).sum())
+
+    for _ in range(args.warmup):
+        device_step()
+    torch.cuda.synchronize()
+    s.reset_kernel_stats()
+    clocks = ClockSampler(0)
+    clocks.start()
+    res = [device_step() for _ in range(args.steps)]
+    clk = clocks.stop()
+    kst = s.kernel_stats()  # the timed region's launches
+    total_ms = sum(r[0] for r in res)
+    steps_total = sum(r[1] for r in res)
+    value = steps_total / (total_ms * 1e-3)
+    # end to end through the C ABI with host arrays: u in, F_1 and the per-subdomain counts out
+    e2e_ms = []
+    for _ in range(args.steps):
+        flush.add_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Fx, its, _ = s.eval_Fx(u, load)
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    launches = sum(v[0] for k, v in kst.items() if not k.startswith("phase:"))
+    newton = [k for k in kst if k.startswith("k_local_newton")]
+    peaks, peak_kind = measured_peaks()
+    roof = (roofline_for(newton[0], kst[newton[0]][0], kst[newton[0]][1], sizes, peaks, peak_kind,
+                         steps_per_launch=res[0][1]) if newton else None)
+    if roof:
+        roof["traffic"] = None  # the kernel's DRAM capture is of the 512 x 512 workload, not this one
+    line = {
+        "metric": "subdomain Newton steps/s of one batched F_1 evaluation (local path only)", "value": value,
+        "unit": "subdomain Newton steps/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64+f32", "data": "synthetic",
+        "config": {"workload": "Neo-Hooke 2048x2048 Q1 (8.4M dofs), 4096 uneven subdomains, overlap 2: local path "
+                               "only (one-level F_1 at load factor 0.2 from a bending state; the coarse problem "
+                               "is not built)",
+                   "precision": "FP32 local band factors + FP64 iterative refinement; FP64 residuals",
+                   "l2": "512 MB buffer written between steps; working set > L2", "setup_s": setup_s,
+                   "n_dofs": sizes.n_dofs, "n_sub": sizes.n_sub, "max_local_dofs": sizes.max_local_dofs,
+                   "max_half_band": sizes.max_half_band},
+        "local_newton_steps_per_evaluation": res[0][1], "local_failures": res[0][2],
+        "roofline": roof, "tuning": s.tuning(), "gpu_launches": launches,
+        "kernels_ms": {k: [v[0], round(v[1], 3)] for k, v in kst.items() if not k.startswith("phase:")},
+        "e2e": {"value": res[0][1] * len(e2e_ms) / (sum(e2e_ms) * 1e-3), "unit": "subdomain Newton steps/s",
+                "h2d_bytes_per_step": int(u.nbytes), "d2h_bytes_per_step": int(Fx.nbytes + 2 * 4 * p.n_sub)},
+        "clocks": clk, "cpu_baseline": None,
+    }
+    s.close()
+    print(json.dumps(line), flush=True)
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -591,7 +679,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "beam"])
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "beam", "c5-local"])
     ap.add_argument("--beam-m", type=int, default=240, help="beam cells across its unit width (5m along it)")
     ap.add_argument("--beam-px", type=int, default=8, help="bricks across the beam")
     ap.add_argument("--beam-py", type=int, default=32, help="bricks along the beam")
@@ -611,6 +699,8 @@ def main():
         run_c4(args)
     elif args.workload == "beam":
         run_beam(args)
+    elif args.workload == "c5-local":
+        run_c5_local(args)
     else:
         run_gpu(args)
 

@@ -82,8 +82,9 @@ typedef struct nls_options {
                                  [64, 256] and at least 32 + the largest half bandwidth (raised to
                                  that if smaller); 0 = library choice (or the autotuner's) */
   int32_t verbose;
-  int32_t profile_kernels;    /* 1: time every kernel launch with CUDA events on the context's
-                                 stream and accumulate per-kernel totals (nls_get_kernel_stats) */
+  int32_t profile_kernels;    /* 1: time every kernel launch of nls_solve, nls_eval_Fx and
+                                 nls_apply_tangent with CUDA events on the context's stream and
+                                 accumulate per-kernel totals (nls_get_kernel_stats) */
   int32_t cuda_graphs;        /* 1 (default): each GMRES iteration body (tangent application,
                                  two Gram-Schmidt passes, norm, copy of the Hessenberg column) is
                                  captured once per Krylov index into a CUDA graph and replayed;

@@ -2331,6 +2331,7 @@ int eval_F(Context& c, const double* u, double* F, int is_dev, double load) {
 
 int eval_Fx(Context& c, const double* u, double* Fx, int is_dev, double load, int32_t* its, int32_t* st) {
   Dev& D = *c.dev;
+  D.prof = c.opt.profile_kernels != 0;
   try {
     CK(cudaMemcpyAsync(D.u, u, sizeof(double) * c.N, is_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, D.s));
     FxInfo fi = evaluate_Fx(c, D.u, load, nullptr, nullptr);
@@ -2352,6 +2353,7 @@ int apply_tangent(Context& c, const double* v, double* y, int is_dev) {
     c.last_error = "nls_apply_tangent needs a preceding nls_eval_Fx";
     return NLS_E_ARG;
   }
+  D.prof = c.opt.profile_kernels != 0;
   try {
     CK(cudaMemcpyAsync(D.t1, v, sizeof(double) * c.N, is_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, D.s));
     LAUNCH(D, k_mask, grid_for(c.N), 256, 0, c.N, D.free_dof, D.t1);
