@@ -6,7 +6,7 @@ CPU-baseline leg.
 Section 2 of the paper uses the reduced GDSW space of Dohrmann and Widlund with
 option 2.2 (inverse Euclidean distance weights on the interface), changed so that
 interface edges ending at a Dirichlet boundary also get inverse-distance values
-instead of the constant one.  Written out (the readings are listed in the design notes):
+instead of the constant one.  Written out, with the readings where the paper is silent:
 
 * S(x) = set of non-overlapping subdomains whose elements touch node x.
   Interface = nodes with |S(x)| >= 2.  Interface nodes are grouped by (S, free or

@@ -4,7 +4,7 @@ Test infrastructure: imported only by the tests, the smoke check and the benchma
 CPU-baseline leg.
 
 Section 2 of the paper asks for an element-based overlapping partition built on the
-dual graph of the mesh.  The reading used here (written out in the design notes):
+dual graph of the mesh.  The paper does not spell out the construction; this oracle reads it as:
 
 * Omega_i' = Omega_i grown by ``overlap`` layers; one layer adds every element that
   shares at least one node with the current element set.

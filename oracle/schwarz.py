@@ -20,7 +20,7 @@ The method follows Section 2 of the paper:
   every outer iterate u;
 * the stopping test of the outer loop uses the original residual, ||F(u)||_2 < tol.
 
-Readings where the paper is silent (all listed in the design notes): local and coarse
+Readings where the paper is silent: local and coarse
 Newton stop at ||r|| <= max(1e-11, 1e-5 ||r_0||) (Section 3 tolerances), at most 50
 iterations, Armijo backtracking with halving (at most 10 trial steps, sufficient decrease
 1e-4 alpha); GMRES(50) with modified Gram-Schmidt and Givens rotations, zero initial guess,

@@ -1,6 +1,6 @@
 """Parity of the sm_103a path (through the C ABI) with the FP64 oracle.
 
-Tolerances (derived in the design notes):
+Tolerances (each derived from the arithmetic of the two sides):
 * F(u) of Eq. 3: both sides evaluate the same element formulas in FP64 and only the
   summation order differs -> 1e-13 relative to max |F|.
 * the coarse basis: FP64 energy-minimising extension, band LU without pivoting against a
@@ -9,7 +9,7 @@ Tolerances (derived in the design notes):
   1e-9 relative.  The FP32-factor path refines to the same FP64 residual -> same bound.
 * the tangent (Eqs. 6, 12): FP64 factors 1e-9; FP32 factors refined to 1e-10 -> 1e-7.
 * converged solutions: 1e-8 (FP64 path) and 1e-6 (FP32 + refinement) relative l2, the
-  bounds the workload statement sets; both sides are driven to ||F|| < 1e-12 first so that
+  bounds the solver is specified to meet; both sides are driven to ||F|| < 1e-12 first so that
   the bound measures the method, not the stopping test.
 """
 import numpy as np
