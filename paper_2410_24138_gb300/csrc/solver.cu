@@ -2527,7 +2527,14 @@ int local_corrections_noalloc(Context& c, const double* x, double* Fx, int32_t* 
   }
   try {
     CK(cudaSetDevice(c.device));
-    D.prof = false;  // per-launch event timing would create events: keep this path allocation free
+    // per-launch event timing would create events: keep this path allocation free (the flag is
+    // restored on return, so the context's profiling option is untouched)
+    struct ProfScope {
+      Dev& d;
+      bool saved;
+      ~ProfScope() { d.prof = saved; }
+    } prof_scope{D, D.prof};
+    D.prof = false;
     void* base = nullptr;
     CK(noalloc_scratch_address(c.device, &base));
     unsigned char* sc = (unsigned char*)base;
@@ -2541,6 +2548,8 @@ int local_corrections_noalloc(Context& c, const double* x, double* Fx, int32_t* 
     A.its = its_out ? its_out : (int32_t*)(sc + o_its);
     A.status = status_out ? status_out : (int32_t*)(sc + o_st);
     A.queue = (int32_t*)(sc + o_q);
+    A.chord = nullptr;  // no chord steps here: the context's counters stay as they are
+    A.reuse = 0;
     A.x = x;
     A.out = Fx;
     A.load = load;

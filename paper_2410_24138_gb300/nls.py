@@ -204,6 +204,7 @@ class Solver:
         self.lib = load()
         self.h = _P()
         self._check(self.lib.nls_create(ctypes.byref(self.h), device, stream), "nls_create")
+        self.device = device
         self.ndof = 1
         self.n_nodes = 0
         self.n_sub = 0
@@ -376,8 +377,34 @@ class Solver:
     def reset_kernel_stats(self):
         self._check(self.lib.nls_reset_kernel_stats(self.h), "nls_reset_kernel_stats")
 
+    def _device_tensor(self, t, name: str, dtype_name: str, numel: int, optional: bool = False):
+        """Check that t is a contiguous CUDA tensor on this context's device with the given dtype
+        and length: the allocation-free call hands raw device pointers to the kernel, so a host
+        array, a short tensor or a wrong element type must be refused here, before any launch."""
+        if t is None:
+            if optional:
+                return
+            raise ValueError(f"{name} is required")
+        if isinstance(t, np.ndarray) or not getattr(t, "is_cuda", False):
+            raise ValueError(f"{name} must be a CUDA torch tensor (got {type(t).__name__})")
+        if t.device.index != self.device:
+            raise ValueError(f"{name} is on cuda:{t.device.index}, the context on cuda:{self.device}")
+        if str(t.dtype) != "torch." + dtype_name:
+            raise ValueError(f"{name} must be {dtype_name} (got {t.dtype})")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        if t.numel() != numel:
+            raise ValueError(f"{name} must have {numel} entries (got {t.numel()})")
+
     def local_corrections_noalloc(self, x, Fx, its=None, status=None, load: float = 1.0):
-        """One-level corrections into the caller's device tensor Fx, using no allocation (see nls.h)."""
+        """One-level corrections into the caller's device tensor Fx, using no allocation (see nls.h).
+        x, Fx: float64 CUDA tensors of n_dofs entries; its, status (optional): int32 CUDA tensors of
+        n_sub entries, all on the context's device; ValueError otherwise (nothing is launched)."""
+        n = self.n_nodes * self.ndof
+        self._device_tensor(x, "x", "float64", n)
+        self._device_tensor(Fx, "Fx", "float64", n)
+        self._device_tensor(its, "its", "int32", self.n_sub, optional=True)
+        self._device_tensor(status, "status", "int32", self.n_sub, optional=True)
         self._check(self.lib.nls_local_corrections_noalloc(self.h, _ptr(x), _ptr(Fx), _ptr(its), _ptr(status), load),
                     "nls_local_corrections_noalloc")
         return Fx

@@ -167,3 +167,18 @@ def test_lambda_mode_validation(nls):
     s3.set_lambda_mode(nls.LAMBDA_PLANE_STRESS)
     with pytest.raises(nls.NLSError, match="setup"):
         s3.solve()
+
+
+def test_noalloc_binding_refuses_host_arrays_before_any_launch(nls):
+    """The allocation-free call passes raw device pointers to its kernel: the binding must refuse
+    host arrays and CPU tensors with a ValueError, without calling into the library."""
+    torch = pytest.importorskip("torch")
+    p = I.diffusion_problem(16, I.box_partition(16, 2, 2), 4, 1)
+    s = nls.make_solver(p, coupling="one", setup="host")
+    n = p.n_nodes
+    for x, out in ((np.zeros(n), np.zeros(n)),
+                   (torch.zeros(n, dtype=torch.float64), torch.zeros(n, dtype=torch.float64)),
+                   (torch.zeros(n, dtype=torch.float32), torch.zeros(n, dtype=torch.float32))):
+        with pytest.raises(ValueError):
+            s.local_corrections_noalloc(x, out)
+    s.close()
