@@ -1,19 +1,22 @@
 """Benchmark: time to ||F(u)||_2 < 1e-8 and subdomain Newton steps/s, FP64 plain vs chosen form.
 
-Workload (default): nonlinear diffusion -div((1 + u^2) grad u) = 1 on the unit square,
-1024 x 1024 P1 cells (~1.05M dofs), 1024 subdomains from the seeded uneven brick partition
-(+-15 % per side, seed 2410), overlap 2, RGDSW coarse space, hybrid two-level coupling
-(Eq. 11), zero initial guess.  One step = one complete solve from u = 0 to ||F|| < 1e-8:
-coarse Newton, one persistent batched local-Newton launch per outer iteration, exact
-tangent inside GMRES, outer Newton update -- every step of the hot path on the device.
-The chosen form uses FP32 local band factors with FP64 iterative refinement; the plain
-form factors in FP64.  Setup (maps, coarse basis) runs once before the timed region and is
-reported separately.
+Workload (default): compressible Neo-Hooke (Eq. 2, plane, E = 210, nu = 0.3) on 2048 x 2048 Q1
+cells (8.4M dofs), left edge clamped, vertical dead-load traction on the right edge ramped over
+5 load steps, 4096 subdomains from the seeded uneven brick partition (+-15 % per side, seed
+2410), overlap 2, RGDSW coarse space (23,376 coarse dofs), hybrid two-level coupling (Eq. 11),
+zero initial guess.  One step = one complete solve from u = 0 through the 5 load steps to
+||F|| < 1e-8: coarse Newton, one persistent batched local-Newton launch per outer iteration,
+exact tangent inside GMRES, outer Newton update -- every step of the hot path on the device.
+The chosen form uses FP32 local band factors and FP32 tiled coarse factors (tensor-core trailing
+products) with FP64 iterative refinement; the plain form factors in FP64.  Setup (maps, coarse
+basis) runs once before the timed region and is reported separately.  ``--workload c2`` runs the
+1024 x 1024 nonlinear diffusion problem (Eq. 1) instead.
 
-The line printed by rank 0 is the JSON contract of this repository (metric, value = whole-
-job subdomain Newton steps/s, roofline of the dominant kernel, e2e through host buffers,
-cpu_baseline = the FP64 oracle on a bounded sample).  ``--impl reference`` times the oracle
-itself on the host cores.
+The line printed by rank 0 is the JSON contract of this repository: value = whole-job full
+subdomain Newton steps per second (a step = one local Newton iteration with Jacobian assembly,
+band factorization, solve and line search; chord steps on stored factors are reported apart),
+roofline of the dominant kernel, e2e through host buffers, err_vs_oracle, and cpu_baseline = the
+FP64 oracle on a bounded sample on every host core.  ``--impl reference`` times the oracle itself.
 """
 from __future__ import annotations
 
@@ -45,58 +48,100 @@ def workload(name: str):
         return I.neohooke_c3(), "Neo-Hooke 512x512 Q1 (0.5M dofs), 256 uneven subdomains, overlap 2, 5 load steps"
     if name == "c4":
         return I.diffusion_c4(1), "log-normal diffusion 512x512 P1 (263k dofs), 256 uneven subdomains, overlap 2"
+    if name == "c5":
+        return I.neohooke_c5(), ("Neo-Hooke 2048x2048 Q1 (8.4M dofs), 4096 uneven subdomains, overlap 2, "
+                                 "5 load steps")
     raise SystemExit(f"unknown workload {name}")
 
 
+DEFAULT_STEPS = {"c1": 10, "c2": 10, "c3": 5, "c4": 10, "c5": 3, "beam": 1}
+WORKLOAD_NAME = ["c5"]  # the workload of this run (the key of the ncu traffic table)
+
+
 # ----------------------------------------------------------------------------------------------
-# CPU baseline: the oracle, as it stands, on a bounded sample of the same workload
+# CPU baseline: the oracle, as it stands, on a bounded sample of the same workload, on every core
 # ----------------------------------------------------------------------------------------------
-def oracle_sample(name: str, budget_s: float = 20.0):
-    """Local Newton solves of the first outer iteration (u = 0, one-level corrections) for as
-    many subdomains as fit in ``budget_s`` seconds; returns (steps/s, steps, subdomains, seconds)."""
+def sample_state(p) -> np.ndarray:
+    """The point at which the CPU baseline solves local problems: u = 0 for Eq. 1 (the source acts
+    everywhere), and for Eq. 2 the smooth bending state u_y = -0.02 x^2 (zero on the clamped edge),
+    so that every subdomain has a nonlinear local problem to solve, not only those at the loaded
+    edge."""
+    u = np.zeros(p.n_nodes * p.ndof)
+    if p.ndof == 2:
+        u[1::2] = -0.02 * p.xy[:, 0] ** 2
+    return u
+
+
+def _oracle_worker(task):
+    """One process of the CPU baseline: local Newton solves of the first load step at the sample
+    state for its subdomains until ``budget_s`` seconds of solving; returns (steps, subdomains, s)."""
+    name, subs, budget_s = task
     from oracle import schwarz as S
     p, _ = workload(name)
-    rng = np.random.default_rng(0)
-    order = rng.permutation(p.n_sub).tolist()
     load = 1.0 / max(1, p.load_steps)
-    u = np.zeros(p.n_nodes * p.ndof)
+    u = sample_state(p)
     steps, done, dt = 0, 0, 0.0
-    for c0 in range(0, p.n_sub, 32):
-        sw = S.Schwarz(p, S.Options(coupling=S.ONE_LEVEL), with_coarse=False, which=order[c0:c0 + 32])
+    for c0 in range(0, len(subs), 16):  # chunks amortise the oracle's per-construction mesh pass
+        sw = S.Schwarz(p, S.Options(coupling=S.ONE_LEVEL), with_coarse=False, which=subs[c0:c0 + 16])
         t0 = time.perf_counter()
         for lp in sw.locals:
-            w, its, status, _, _ = lp.solve_newton(u, u[lp.sub.dofs], sw.opts, load)
+            _, its, _, _, _ = lp.solve_newton(u, u[lp.sub.dofs], sw.opts, load)
             steps += its
             done += 1
         dt += time.perf_counter() - t0
         if dt > budget_s:
             break
-    return steps / dt, steps, done, dt
+    return steps, done, dt
+
+
+def oracle_sample(name: str, budget_s: float = 20.0, cores: int = 0):
+    """The oracle's local solves on ``cores`` processes (0: every host core), each over its own
+    seeded random share of the subdomains for about ``budget_s`` seconds of solving.  Returns
+    (steps/s summed over the processes, steps, subdomains, seconds per process, processes)."""
+    import multiprocessing as mp
+    p, _ = workload(name)
+    cores = cores or os.cpu_count() or 1
+    order = np.random.default_rng(0).permutation(p.n_sub).tolist()
+    tasks = [(name, order[k::cores], budget_s) for k in range(cores)]
+    saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in saved:
+        os.environ[k] = "1"  # one thread per process: the processes are the parallelism
+    try:
+        with mp.get_context("spawn").Pool(cores) as pool:
+            res = pool.map(_oracle_worker, tasks)
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    rate = sum(st / dt for st, _, dt in res if dt > 0)
+    return rate, sum(r[0] for r in res), sum(r[1] for r in res), max(r[2] for r in res), cores
 
 
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    rates = []
     for _ in range(args.warmup):
-        oracle_sample(args.workload, budget_s=2.0)
-    total_steps, total_time, subs = 0, 0.0, 0
+        oracle_sample(args.workload, budget_s=1.0)
+    rates, total_steps, total_time, subs, cores = [], 0, 0.0, 0, 1
     for _ in range(args.steps):
-        r, st, sd, dt = oracle_sample(args.workload, budget_s=args.ref_budget)
+        r, st, sd, dt, cores = oracle_sample(args.workload, budget_s=args.ref_budget)
         rates.append(r)
         total_steps += st
         total_time += dt
         subs += sd
-    value = total_steps / total_time
+    value = statistics.mean(rates)
     _, desc = workload(args.workload)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_time / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": desc},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{subs} subdomain local Newton solves (first outer iteration, u = 0) over "
-                                       f"{args.steps} steps, {total_steps} subdomain Newton steps"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{subs} subdomain local Newton solves at the first load step's sample "
+                                       f"state (u = 0 for Eq. 1, bending u_y = -0.02 x^2 for Eq. 2) on {cores} "
+                                       f"processes over {args.steps} steps, {total_steps} subdomain Newton steps"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -352,94 +397,6 @@ def run_beam(args):
     print(json.dumps(line), flush=True)
 
 
-def run_c5_local(args):
-    """The 2048 x 2048 Neo-Hooke workload's local path: one F_1 evaluation (Eq. 5) per step, i.e.
-    every subdomain's local Newton solve (Eq. 4) batched in one launch plus the refactorization at
-    its converged state, from a smooth bending state u_y = -0.02 x^2 at the first load step's
-    traction.  The two-level solve of this workload is not run: its coarse band is beyond the
-    coarse factorization."""
-    import torch
-    from paper_2410_24138_gb300 import build, inputs as I, nls
-    torch.cuda.set_device(0)
-    build.build()
-    p = I.neohooke_c5()
-    stream = torch.cuda.current_stream()
-    s = nls.Solver(device=0, stream=stream.cuda_stream)
-    s.set_problem(p)
-    s.set_coarse(nls.COARSE_NONE)
-    # per-kernel statistics on (set before setup): CUDA events around the few launches of an
-    # evaluation, whose one local Newton launch takes a quarter of a second
-    s.set_options(coupling=nls.COUPLING["one"], local_precision=nls.PREC_FP32_IR,
-                  coarse_precision=nls.PREC_FP32_IR, autotune=1, profile_kernels=1)
-    t0 = time.perf_counter()
-    s.setup()
-    setup_s = time.perf_counter() - t0
-    sizes = s.sizes()
-    load = 0.2
-    u = np.zeros(p.n_nodes * 2)
-    u[1::2] = -0.02 * p.xy[:, 0] ** 2  # zero on the clamped edge x = 0
-    ud = torch.from_numpy(u).cuda()
-    flush = torch.zeros(64 * 1024 * 1024, dtype=torch.float64, device="cuda")
-
-    def device_step():
-        flush.add_(1.0)  # 512 MB written between steps
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        _, its, st = s.eval_Fx(ud, load)
-        e1.record(stream)
-        e1.synchronize()
-        return e0.elapsed_time(e1), int(its.sum()), int((st != 0).sum())
-
-    for _ in range(args.warmup):
-        device_step()
-    torch.cuda.synchronize()
-    s.reset_kernel_stats()
-    clocks = ClockSampler(0)
-    clocks.start()
-    res = [device_step() for _ in range(args.steps)]
-    clk = clocks.stop()
-    kst = s.kernel_stats()  # the timed region's launches
-    total_ms = sum(r[0] for r in res)
-    steps_total = sum(r[1] for r in res)
-    value = steps_total / (total_ms * 1e-3)
-    # end to end through the C ABI with host arrays: u in, F_1 and the per-subdomain counts out
-    e2e_ms = []
-    for _ in range(args.steps):
-        flush.add_(1.0)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        Fx, its, _ = s.eval_Fx(u, load)
-        e2e_ms.append((time.perf_counter() - t0) * 1e3)
-    launches = sum(v[0] for k, v in kst.items() if not k.startswith("phase:"))
-    newton = [k for k in kst if k.startswith("k_local_newton")]
-    peaks, peak_kind = measured_peaks()
-    roof = (roofline_for(newton[0], kst[newton[0]][0], kst[newton[0]][1], sizes, peaks, peak_kind,
-                         steps_per_launch=res[0][1]) if newton else None)
-    if roof:
-        roof["traffic"] = None  # the kernel's DRAM capture is of the 512 x 512 workload, not this one
-    line = {
-        "metric": "subdomain Newton steps/s of one batched F_1 evaluation (local path only)", "value": value,
-        "unit": "subdomain Newton steps/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64+f32", "data": "synthetic",
-        "config": {"workload": "Neo-Hooke 2048x2048 Q1 (8.4M dofs), 4096 uneven subdomains, overlap 2: local path "
-                               "only (one-level F_1 at load factor 0.2 from a bending state; the coarse problem "
-                               "is not built)",
-                   "precision": "FP32 local band factors + FP64 iterative refinement; FP64 residuals",
-                   "l2": "512 MB buffer written between steps; working set > L2", "setup_s": setup_s,
-                   "n_dofs": sizes.n_dofs, "n_sub": sizes.n_sub, "max_local_dofs": sizes.max_local_dofs,
-                   "max_half_band": sizes.max_half_band},
-        "local_newton_steps_per_evaluation": res[0][1], "local_failures": res[0][2],
-        "roofline": roof, "tuning": s.tuning(), "gpu_launches": launches,
-        "kernels_ms": {k: [v[0], round(v[1], 3)] for k, v in kst.items() if not k.startswith("phase:")},
-        "e2e": {"value": res[0][1] * len(e2e_ms) / (sum(e2e_ms) * 1e-3), "unit": "subdomain Newton steps/s",
-                "h2d_bytes_per_step": int(u.nbytes), "d2h_bytes_per_step": int(Fx.nbytes + 2 * 4 * p.n_sub)},
-        "clocks": clk, "cpu_baseline": None,
-    }
-    s.close()
-    print(json.dumps(line), flush=True)
-
-
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -478,6 +435,38 @@ def replica_throughput(torch, dist, world, total_ms, units, device):
     return st_t.item() / (ms_t.item() * 1e-3), ms_t.item(), st_t.item()
 
 
+def err_vs_oracle(p, u: np.ndarray, samples: int = 6) -> dict:
+    """Error of a converged solution against the FP64 oracle, computed outside the timed region.
+    Always: the oracle's own FP64 evaluation of ||F(u)||_2 at the final load.  Diffusion meshes up
+    to about 1M dofs: the relative l2 distance to the oracle's plain global Newton solution of
+    F(u) = 0 (sparse direct FP64 solves, driven to ||F|| < 1e-11).  Larger or elasticity meshes:
+    for seeded sampled subdomains, the oracle's local solve of Eq. 4 at the returned u (tight
+    tolerances); a solution of F(u) = 0 is a fixed point of every local solve, so the relative
+    change of R_i u bounds how far u is from the oracle's local solutions."""
+    from oracle import fem, schwarz as S
+    F = fem.global_residual(fem.Model(p), u, 1.0)
+    out = {"oracle_residual": float(np.linalg.norm(F))}
+    t0 = time.perf_counter()
+    if p.law == 1 and p.n_nodes * p.ndof <= 1_100_000:
+        us, _ = S.plain_newton(p, tol=1e-11, load_steps=p.load_steps)
+        out.update(kind="global: the oracle's plain Newton solution (sparse direct FP64) on the same mesh",
+                   rel_l2=float(np.linalg.norm(u - us) / np.linalg.norm(us)))
+    else:
+        rng = np.random.default_rng(2410)
+        pick = sorted({0, p.n_sub // 2, p.n_sub - 1, *rng.choice(p.n_sub, samples - 3, replace=False).tolist()})
+        opts = S.Options(coupling=S.ONE_LEVEL, inner_rtol=1e-12, inner_atol=1e-13)
+        sw = S.Schwarz(p, opts, with_coarse=False, which=pick)
+        errs = []
+        for lp in sw.locals:
+            ru = u[lp.sub.dofs]
+            w, _, _, _, _ = lp.solve_newton(u, ru, opts, 1.0)
+            errs.append(float(np.linalg.norm(w - ru) / max(np.linalg.norm(ru), 1e-300)))
+        out.update(kind="sampled: the oracle's local solves (Eq. 4) at the returned u; relative change of R_i u",
+                   subdomains=pick, rel_l2_max=max(errs), rel_l2=errs)
+    out["oracle_s"] = time.perf_counter() - t0
+    return out
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -491,17 +480,18 @@ def run_gpu(args):
     torch.cuda.set_device(local)
     build.build()
     p, desc = workload(args.workload)
+    steps = args.steps
     stream = torch.cuda.current_stream().cuda_stream
     flush_buf = torch.zeros(64 * 1024 * 1024, dtype=torch.float64, device="cuda")
+    coupling = "hybrid" if p.n_sub > 1 else "one"
 
-    def make(precision, profile=0):
+    def make(precision):
         s = nls.Solver(device=local, stream=stream)
         s.set_problem(p)
-        s.set_coarse(nls.COARSE_RGDSW)
-        s.set_options(coupling=nls.COUPLING["hybrid"], load_steps=p.load_steps,
-                      local_precision=nls.PREC_FP32_IR if precision == "fp32" else nls.PREC_FP64,
-                      coarse_precision=nls.PREC_FP32_IR if precision == "fp32" else nls.PREC_FP64,
-                      profile_kernels=profile, autotune=1)
+        s.set_coarse(nls.COARSE_RGDSW if coupling != "one" else nls.COARSE_NONE)
+        prec = nls.PREC_FP32_IR if precision == "fp32" else nls.PREC_FP64
+        s.set_options(coupling=nls.COUPLING[coupling], load_steps=p.load_steps, local_precision=prec,
+                      coarse_precision=prec, autotune=1)
         t0 = time.perf_counter()
         s.setup()
         return s, time.perf_counter() - t0
@@ -509,7 +499,6 @@ def run_gpu(args):
     chosen, setup_s = make("fp32")
     sizes = chosen.sizes()
     n_dofs = sizes.n_dofs
-    # warm-up (also compiles nothing: the library is prebuilt)
     timed_solves(torch, chosen, n_dofs, args.warmup, flush_buf)
     if world > 1:
         dist.barrier()
@@ -517,49 +506,54 @@ def run_gpu(args):
     clocks = ClockSampler(local)
     clocks.start()
     t_wall0 = time.perf_counter()
-    times, reps = timed_solves(torch, chosen, n_dofs, args.steps, flush_buf)
+    times, reps = timed_solves(torch, chosen, n_dofs, steps, flush_buf)
     torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_wall0
     clk = clocks.stop()
     if world > 1:
         dist.barrier()
     total_ms = sum(times)
-    # the metric counts every local Newton iteration (residual, solve, line search), with or
-    # without a fresh factorization; the chord steps (stored factors) are also reported apart
-    steps_local = sum(r.subdomain_newton_steps for r in reps)
-    value, _, _ = replica_throughput(torch, dist, world, total_ms, steps_local, "cuda")
+    # the metric counts full local Newton steps (Jacobian assembly, band factorization, solve,
+    # line search); steps taken with stored factors (chord steps) are reported apart
+    full_steps = sum(r.subdomain_newton_steps - r.local_chord_steps for r in reps)
+    value, _, _ = replica_throughput(torch, dist, world, total_ms, full_steps, "cuda")
     rep0 = reps[-1]
+    u_final = None
 
-    # per-kernel timing of one more solve (CUDA events on the launching stream)
-    prof, _ = make("fp32", profile=1)
-    timed_solves(torch, prof, n_dofs, 1, flush_buf)
-    prof.reset_kernel_stats()
-    ptimes, preps = timed_solves(torch, prof, n_dofs, 1, flush_buf)
-    kstats_all = prof.kernel_stats()
+    # per-kernel timing of one more solve on the same context (CUDA events on the launching
+    # stream; graphs are off while profiling), outside the timed region
+    chosen.set_options(profile_kernels=1)
+    chosen.reset_kernel_stats()
+    ptimes, preps = timed_solves(torch, chosen, n_dofs, 1, flush_buf)
+    kstats_all = chosen.kernel_stats()
+    chosen.set_options(profile_kernels=0)
     phases = {k[6:]: round(v[1], 3) for k, v in kstats_all.items() if k.startswith("phase:")}
     kstats = {k: v for k, v in kstats_all.items() if not k.startswith("phase:")}
-    prof.close()
-
-    # plain FP64 form on the same mesh
-    plain, plain_setup = make("fp64")
-    timed_solves(torch, plain, n_dofs, 1, flush_buf)
-    p_times, p_reps = timed_solves(torch, plain, n_dofs, max(1, min(args.steps, 3)), flush_buf)
-    plain_rate = sum(r.subdomain_newton_steps for r in p_reps) / (sum(p_times) * 1e-3)
-    plain.close()
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
     host_u = torch.zeros(n_dofs, dtype=torch.float64).pin_memory()
     e2e_steps, e2e_ms = 0, 0.0
-    for _ in range(args.steps):
+    for _ in range(steps):
         flush_buf.add_(1.0)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         hu = host_u.numpy()
         hu[:] = 0.0
-        _, rep = chosen.solve(hu)
+        hu, rep = chosen.solve(hu)
         e2e_ms += (time.perf_counter() - t0) * 1e3
-        e2e_steps += rep.subdomain_newton_steps
+        e2e_steps += rep.subdomain_newton_steps - rep.local_chord_steps
     e2e_value = e2e_steps / (e2e_ms * 1e-3)
+    u_final = np.array(hu, copy=True)
+    tuning = chosen.tuning()
+    chosen.close()
+
+    # plain FP64 form on the same mesh
+    plain, plain_setup = make("fp64")
+    timed_solves(torch, plain, n_dofs, 1, flush_buf)
+    p_times, p_reps = timed_solves(torch, plain, n_dofs, max(1, min(steps, 2)), flush_buf)
+    plain_full = sum(r.subdomain_newton_steps - r.local_chord_steps for r in p_reps)
+    plain_rate = plain_full / (sum(p_times) * 1e-3)
+    plain.close()
 
     # roofline of the dominant kernel
     peaks, peak_kind = measured_peaks()
@@ -570,21 +564,27 @@ def run_gpu(args):
                         / max(1, preps[-1].outer_iterations))
     roof = roofline_for(dom_name, dom_launches, dom_ms, sizes, peaks, peak_kind, steps_per_launch)
     roof_top = [roofline_for(k, v[0], v[1], sizes, peaks, peak_kind, steps_per_launch)
-                for k, v in sorted(kstats.items(), key=lambda kv: -kv[1][1])[:3]]
-    tuning = chosen.tuning()
+                for k, v in sorted(kstats.items(), key=lambda kv: -kv[1][1])[:4]]
+    coarse_tc = {k: v for k, v in kstats.items() if k.startswith("k_tlu") or k.startswith("k_tile")}
+    roof_tensor = [roofline_for(k, v[0], v[1], sizes, peaks, peak_kind) for k, v in kstats.items()
+                   if k.startswith("k_tlu_update_tc") or k.startswith("k_tile_solve_products")]
 
     if rank == 0:
+        err = err_vs_oracle(p, u_final) if not args.no_oracle_err else None
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
-            r, st, sd, dt = oracle_sample(args.workload, budget_s=args.ref_budget)
-            cpu = {"value": r, "unit": UNIT, "cores": 1, "kind": "oracle",
-                   "sample": f"{sd} subdomain local Newton solves of the first outer iteration (u = 0), "
-                             f"{st} subdomain Newton steps in {dt:.1f} s, single-threaded numpy/scipy"}
+            r, st, sd, dt, cores = oracle_sample(args.workload, budget_s=args.ref_budget)
+            cpu = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle",
+                   "sample": f"{sd} subdomain local Newton solves at the first load step's sample state (u = 0 "
+                             f"for Eq. 1, bending u_y = -0.02 x^2 for Eq. 2), {st} subdomain Newton steps, {cores} "
+                             f"processes of {dt:.1f} s each (numpy/scipy FP64, one thread per process)"}
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
-            "config": {"workload": desc, "coupling": "hybrid", "precision": "FP32 local and coarse band factors + FP64 iterative refinement; FP64 residuals, GMRES, coarse matrix",
+            "config": {"workload": desc, "coupling": coupling,
+                       "precision": "FP32 local band factors and FP32 tiled coarse factors + FP64 iterative "
+                                    "refinement; FP64 residuals, GMRES, coarse matrix",
                        "l2": "512 MB buffer written between steps; working set > L2",
                        "parallelism": "replicas" if world > 1 else "single GPU", "setup_s": setup_s,
                        "n_dofs": n_dofs, "n_sub": sizes.n_sub, "coarse_dofs": sizes.n_coarse_dofs,
@@ -592,21 +592,27 @@ def run_gpu(args):
                        "coarse_half_band": sizes.coarse_half_band},
             "time_to_solution_s": {"chosen": statistics.median(times) * 1e-3,
                                    "plain_fp64": statistics.median(p_times) * 1e-3},
-            "subdomain_newton_steps_per_s": {"chosen": value / world, "plain_fp64": plain_rate},
+            "full_newton_steps_per_s": {"chosen": value / world, "plain_fp64": plain_rate},
             "speedup_chosen_vs_plain": statistics.median(p_times) / statistics.median(times),
             "iterations": {"outer": rep0.outer_iterations, "gmres": rep0.gmres_iterations,
-                           "subdomain_newton_steps": rep0.subdomain_newton_steps,
-                           "of_which_chord_steps": rep0.local_chord_steps,
+                           "full_newton_steps": rep0.subdomain_newton_steps - rep0.local_chord_steps,
+                           "chord_steps": rep0.local_chord_steps,
                            "coarse_newton_steps": rep0.coarse_newton_steps,
                            "final_residual": rep0.final_residual, "local_failures": rep0.local_failures},
+            "plain_iterations": {"outer": p_reps[-1].outer_iterations, "gmres": p_reps[-1].gmres_iterations,
+                                 "full_newton_steps": p_reps[-1].subdomain_newton_steps - p_reps[-1].local_chord_steps,
+                                 "final_residual": p_reps[-1].final_residual},
             "phases_s": {"inner": rep0.time_inner_s, "coarse": rep0.time_coarse_s, "gmres": rep0.time_gmres_s,
                          "other": rep0.time_other_s},
             "local_newton_phases_cta_ms": phases,
             "kernels_ms": {k: [v[0], round(v[1], 3), round(100.0 * v[1] / total_prof_ms, 1)] for k, v in
-                           sorted(kstats.items(), key=lambda kv: -kv[1][1])[:8]},
+                           sorted(kstats.items(), key=lambda kv: -kv[1][1])[:10]},
+            "coarse_factor_kernels_ms": {k: [v[0], round(v[1], 3)] for k, v in coarse_tc.items()},
             "roofline": roof,
-            "roofline_top3": roof_top,
+            "roofline_top": roof_top,
+            "roofline_tensor": roof_tensor,
             "tuning": tuning,
+            "err_vs_oracle": err,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * n_dofs, "d2h_bytes_per_step": 8 * n_dofs},
             "gpu_launches": int(sum(r.kernel_launches for r in reps)),
             "clocks": clk,
@@ -629,16 +635,10 @@ def fp32_peak_tflops(peaks):
     return SMS * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
 
 
-# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch, from the ncu
-# captures summarised in profiles/: the first launch of a solve of the 1024 x 1024 diffusion
-# workload, and for the Neo-Hooke kernel the mean over the 17 launches of one solve of the
-# 512 x 512 workload (its launches differ by load step); a kernel changed since its capture
-# has no entry.
-NCU_TRAFFIC_BYTES = {
-    "k_local_newton<diffusion, float, 128>": 7.337879e9 + 4.212179e9,
-    "k_local_newton<neohooke, float, 256>": 5.707471e9 + 2.054406e9,
-    "k_local_apply<float>": 2.434448e9 + 0.073884e9,
-}
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the default
+# workload, from the ncu captures summarised in profiles/ (keyed by workload and kernel); a kernel
+# changed since its capture has no entry.
+NCU_TRAFFIC_BYTES = {}
 
 
 def roofline_for(name, launches, ms, sizes, peaks, peak_kind, steps_per_launch=None):
@@ -652,20 +652,38 @@ def roofline_for(name, launches, ms, sizes, peaks, peak_kind, steps_per_launch=N
         peak = fp32_peak_tflops(peaks)
         ach = flops / avg_s / 1e12
         return {"kernel": name, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                "frac": ach / peak, "traffic": NCU_TRAFFIC_BYTES.get(name), "algorithmic_flops_per_launch": flops,
+                "frac": ach / peak, "traffic": NCU_TRAFFIC_BYTES.get((WORKLOAD_NAME[0], name)), "algorithmic_flops_per_launch": flops,
                 "avg_launch_ms": avg_s * 1e3,
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock"}
     if "local_apply" in name:
         fb = sizes.factor_bytes
-        # one pass over the packed solve operands, the local Jacobian (value + column index), the
-        # table gather of the input vector and the owned scatter of the output
-        alg = (sizes.total_solve_entries * fb + sizes.total_local_nnz * 12 + sizes.total_table_dofs * 12
-               + sizes.n_dofs * 8)
+        # algorithmic bytes of one tangent application: every subdomain's band factors read once
+        # (sum_i n_i (2 b_i + 1) entries), its local Jacobian (value + column index, 12 bytes per
+        # nonzero) and three global vectors (input, the term added, output)
+        alg = sizes.total_factor_entries * fb + sizes.total_local_nnz * 12 + 3 * sizes.n_dofs * 8
+        packed = sizes.total_solve_entries * fb
         peak = peaks["hbm_gbs"]
         return {"kernel": name, "bound": "hbm", "achieved": alg / avg_s / 1e9, "peak": peak, "unit": "GB/s",
-                "frac": alg / avg_s / 1e9 / peak, "traffic": NCU_TRAFFIC_BYTES.get(name),
+                "frac": alg / avg_s / 1e9 / peak, "traffic": NCU_TRAFFIC_BYTES.get((WORKLOAD_NAME[0], name)),
                 "algorithmic_bytes_per_launch": alg,
+                "stored_operand_bytes_per_launch": packed + sizes.total_local_nnz * 12 + 3 * sizes.n_dofs * 8,
+                "operand_format_overhead": packed / max(1, sizes.total_factor_entries * fb),
                 "avg_launch_ms": avg_s * 1e3, "peak_source": peak_kind}
+    if name.startswith("k_tlu_update_tc") or name.startswith("k_tile_solve_products"):
+        # tensor-core tile products: three TF32 MMA passes (hi*hi, hi*lo, lo*hi) of 128 x 128 x 128
+        # per tile; peak = the measured BF16 peak times the nominal TF32 / BF16 ratio (1.1 / 2.25)
+        NT, TB = -(-sizes.n_coarse_dofs // 128), max(1, -(-sizes.coarse_half_band // 128))
+        if name.startswith("k_tlu_update_tc"):
+            tiles = sum(min(TB, NT - 1 - k) ** 2 for k in range(NT - 1)) / max(1, NT - 1)
+        else:
+            tiles = sum(1 for t in range(NT) for k in range(1, TB + 1) if t - k >= 0) + \
+                sum(1 for t in range(NT) for k in range(1, TB + 1) if t + k < NT)
+        flops = 3 * 2 * 128 ** 3 * tiles
+        peak = peaks["bf16_tflops"] * 1.1 / 2.25
+        ach = flops / avg_s / 1e12
+        return {"kernel": name, "bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": None, "tf32_flops_per_launch": flops, "avg_launch_ms": avg_s * 1e3,
+                "peak_source": f"{peak_kind} bf16 x nominal tf32/bf16 (1.1/2.25)"}
     if "multidot" in name or "multiaxpy" in name or "spmv" in name or "p0" in name:
         return {"kernel": name, "bound": "hbm", "achieved": None, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": None, "traffic": None, "avg_launch_ms": avg_s * 1e3, "peak_source": peak_kind}
@@ -676,10 +694,10 @@ def roofline_for(name, launches, ms, sizes, peaks, peak_kind, steps_per_launch=N
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=0, help="timed steps (0: the workload's default)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "beam", "c5-local"])
+    ap.add_argument("--workload", default="c5", choices=["c1", "c2", "c3", "c4", "c5", "beam"])
     ap.add_argument("--beam-m", type=int, default=240, help="beam cells across its unit width (5m along it)")
     ap.add_argument("--beam-px", type=int, default=8, help="bricks across the beam")
     ap.add_argument("--beam-py", type=int, default=32, help="bricks along the beam")
@@ -690,17 +708,19 @@ def main():
     ap.add_argument("--c4-sweeps", type=int, default=6)
     ap.add_argument("--ref-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-oracle-err", action="store_true", help="skip the error report against the oracle")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("at least 3 warm-up steps are required")
+    if not args.steps:
+        args.steps = DEFAULT_STEPS.get(args.workload, 3)
+    WORKLOAD_NAME[0] = args.workload
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "c4":
         run_c4(args)
     elif args.workload == "beam":
         run_beam(args)
-    elif args.workload == "c5-local":
-        run_c5_local(args)
     else:
         run_gpu(args)
 

@@ -85,11 +85,14 @@ typedef struct nls_options {
   int32_t profile_kernels;    /* 1: time every kernel launch of nls_solve, nls_eval_Fx and
                                  nls_apply_tangent with CUDA events on the context's stream and
                                  accumulate per-kernel totals (nls_get_kernel_stats) */
-  int32_t cuda_graphs;        /* 1 (default): each GMRES iteration body (tangent application,
-                                 two Gram-Schmidt passes, norm, copy of the Hessenberg column) is
-                                 captured once per Krylov index into a CUDA graph and replayed;
-                                 0: plain stream launches.  Graphs are not used while
-                                 profile_kernels is set.  Results are identical either way. */
+  int32_t cuda_graphs;        /* 1 (default): a GMRES cycle (up to gmres_restart iterations, each a
+                                 tangent application, two Gram-Schmidt passes, the norm and a Givens
+                                 step on the device) is one CUDA graph of conditional nodes,
+                                 captured once and replayed; the Givens step stops the cycle on the
+                                 device, so the host reads its state once per cycle.  0: plain
+                                 stream launches and a host check after every iteration.  Graphs are
+                                 not used while profile_kernels is set.  Results are identical
+                                 either way. */
   int32_t coarse_reuse;       /* 1 (default): the coarse Newton iteration of Eq. 9 starts every
                                  outer step after the first of an nls_solve with the
                                  factorization (and explicit inverse) of the previous tangent
@@ -124,7 +127,20 @@ typedef struct nls_options {
   int32_t coarse_rebuild;     /* 1: inside nls_solve the RGDSW basis is rebuilt at every outer iterate
                                  u from DF(u) (the energy-minimising extension of the same interface
                                  values); 0 (default): built once at setup from DF(u^(0)). */
+  int32_t coarse_factor;      /* factorization of the coarse matrix A_0 (Eq. 9), fixed at nls_setup:
+                                 NLS_COARSE_FACTOR_AUTO (default): the one-CTA band LU when the half
+                                 bandwidth of A_0 is at most 128, the tiled one beyond;
+                                 NLS_COARSE_FACTOR_BAND: the band LU in one CTA (half bandwidth of
+                                 A_0 at most 128); NLS_COARSE_FACTOR_TILES: a band LU without pivoting
+                                 cut into square tiles and spread over many CTAs, with the trailing
+                                 tile products of the FP32 form on the tensor cores (TF32 split into
+                                 high and low parts, FP32 accumulation) -- for half bandwidths up to
+                                 480.  Every coarse solve is refined in FP64 against A_0 either way. */
 } nls_options;
+
+#define NLS_COARSE_FACTOR_AUTO 0
+#define NLS_COARSE_FACTOR_BAND 1
+#define NLS_COARSE_FACTOR_TILES 2
 
 /* Per-solve report. */
 typedef struct nls_report {
@@ -272,7 +288,7 @@ typedef struct nls_tuning {
   int32_t newton_threads, apply_threads;
   int32_t newton_tuned, apply_tuned;
   double newton_ms[2];        /* measured launch times of the 128- and 256-thread variants (0: not tried) */
-  int32_t graphs_captured;    /* GMRES iteration graphs currently instantiated */
+  int32_t graphs_captured;    /* GMRES cycle graphs currently instantiated (0 or 1) */
   int32_t coarse_threads;     /* CTA size of the coarse band factorization (autotuned when enabled) */
 } nls_tuning;
 int nls_get_tuning(const nls_ctx* ctx, nls_tuning* out);
@@ -292,6 +308,27 @@ int nls_get_owners(const nls_ctx* ctx, int32_t* owners_out);
 int nls_get_coarse_nodes(const nls_ctx* ctx, int32_t* first_node_out);
 /* The coarse basis P_0 as a dense column-major [n_dofs x n_coarse_dofs] host array. */
 int nls_get_coarse_basis(const nls_ctx* ctx, double* P0_out);
+
+/* The coarse matrix A_0 = P_0^T DF(u_0) P_0 of Eq. 9 formed by the last tangent phase (or coarse
+ * Newton step) in FP64 band storage: A0_out [n_coarse_dofs x (2 coarse_half_band + 1)], entry
+ * (i, i - b0 + d) at i (2 b0 + 1) + d. */
+int nls_get_coarse_matrix(const nls_ctx* ctx, double* A0_out);
+
+/* The coarse factorization and solve of Eq. 9 applied to a given band matrix (parity hook and
+ * utility).  band [n x (2b + 1)] (host, FP64, entry (i, i - b + d) at i (2b + 1) + d; entries
+ * outside the matrix are ignored) is factored without pivoting by `method`
+ * (NLS_COARSE_FACTOR_BAND, _TILES, or _AUTO as in nls_options.coarse_factor) in `precision`
+ * (NLS_PREC_FP64, or NLS_PREC_FP32_IR: FP32 factors, each solve refined in FP64 against the band
+ * until ||rhs - A x|| <= 1e-10 ||rhs||, at most 5 sweeps), then A x = rhs is solved; x [n] and
+ * rhs [n] are host arrays.  factors_out [n x (2b + 1)] (may be NULL) receives the factors in the
+ * band layout: d < b the multipliers of the unit lower factor L, d = b the reciprocal pivots
+ * 1 / U_ii, d > b the entries of U.  Runs on `device`'s legacy default stream with its own
+ * memory, freed before returning.  NLS_E_PIVOT for a zero or non-finite pivot,
+ * NLS_E_UNSUPPORTED beyond the half bandwidths the methods take (BAND 128, and a window of
+ * (b + 10) rows that fits in shared memory: about 160 in FP32, 110 in FP64; TILES 480) or when
+ * the solve vector (n values) does not fit in shared memory. */
+int nls_band_solve(int device, int32_t n, int32_t b, const double* band, const double* rhs, double* x,
+                   int32_t precision, int32_t method, double* factors_out);
 
 /* F(u) of Eq. 3 (Dirichlet rows zero) at load factor `load`; u, F of length n_dofs. */
 int nls_eval_F(nls_ctx* ctx, const double* u, double* F, int is_device, double load);
@@ -362,6 +399,16 @@ int nls_guess_gradient(nls_guess_net* net, int32_t B, const float* X, const floa
                        float* loss);
 /* Network output (FP32 inference) for normalised inputs X [B x 391] into Y [B x 1024]. */
 int nls_guess_forward(nls_guess_net* net, int32_t B, const float* X, float* Y);
+/* Test hooks of the input and output maps (context with an attached network; x [n_dofs] host):
+ * the raw inputs of every subdomain at x and load factor `load` (before normalisation) into
+ * features_out [n_sub x 391] (FP32); the proposal decoded from given network outputs
+ * Y [n_sub x 1024] (normalised units, FP32) at x into guess_out [total_local_dofs] (the local
+ * unknowns of every subdomain, concatenated in subdomain order as nls_get_local_states); and the
+ * smoothing of given starts w [total_local_dofs] at x into w_out [total_local_dofs], with the
+ * attached network's smoothing parameters. */
+int nls_guess_features(nls_ctx* ctx, const double* x, double load, float* features_out);
+int nls_guess_decode(nls_ctx* ctx, const double* x, double load, const float* Y, double* guess_out);
+int nls_guess_smooth(nls_ctx* ctx, const double* x, double load, const double* w, double* w_out);
 /* Guesses proposed and accepted by the local solves since the last call (then reset). */
 int nls_guess_counts(nls_ctx* ctx, int64_t* proposed, int64_t* accepted);
 /* Smoothing of proposed starts (see above): sweeps in [0, 64], omega in (0, 1].  Needs an

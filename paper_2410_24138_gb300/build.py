@@ -21,7 +21,7 @@ GENCODE = "-gencode=arch=compute_103a,code=sm_103a"
 CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 NVCC = os.path.join(CUDA_HOME, "bin", "nvcc") if os.path.exists(os.path.join(CUDA_HOME, "bin", "nvcc")) else "nvcc"
 
-SOURCES = ["api.cpp", "setup.cpp", "solver.cu", "guess.cu"]
+SOURCES = ["api.cpp", "setup.cpp", "solver.cu", "guess.cu", "coarse_tlu.cu"]
 
 
 def _compile(src: str, objdir: str, verbose: bool) -> str:

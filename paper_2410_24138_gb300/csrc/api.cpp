@@ -52,6 +52,7 @@ void nls_options_default(nls_options* o) {
   o->l2_prefetch = 4;
   o->outer_backtrack = 0;
   o->coarse_rebuild = 0;
+  o->coarse_factor = NLS_COARSE_FACTOR_AUTO;
   o->verbose = 0;
 }
 
@@ -256,9 +257,12 @@ int nls_set_options(nls_ctx* ctx, const nls_options* o) {
   if (o->l2_prefetch < 0 || o->l2_prefetch > 64) return fail(ctx, NLS_E_ARG, "l2_prefetch must be in [0, 64]");
   if (o->outer_backtrack != 0 && o->outer_backtrack != 1) return fail(ctx, NLS_E_ARG, "outer_backtrack must be 0 or 1");
   if (o->coarse_rebuild != 0 && o->coarse_rebuild != 1) return fail(ctx, NLS_E_ARG, "coarse_rebuild must be 0 or 1");
+  if (o->coarse_factor < NLS_COARSE_FACTOR_AUTO || o->coarse_factor > NLS_COARSE_FACTOR_TILES)
+    return fail(ctx, NLS_E_ARG, "unknown coarse_factor");
   if (ctx->c.is_setup && (o->local_precision != ctx->c.opt.local_precision ||
-                          o->coarse_precision != ctx->c.opt.coarse_precision))
-    return fail(ctx, NLS_E_ARG, "the factor precisions are fixed by nls_setup; set them before it");
+                          o->coarse_precision != ctx->c.opt.coarse_precision ||
+                          o->coarse_factor != ctx->c.opt.coarse_factor))
+    return fail(ctx, NLS_E_ARG, "the factor precisions and the coarse factorization are fixed by nls_setup; set them before it");
   ctx->c.opt = *o;
   nls::options_changed(ctx->c);
   return NLS_OK;
@@ -390,6 +394,21 @@ int nls_guess_set_smoothing(nls_ctx* ctx, int32_t sweeps, double omega) {
   return nls::guess_set_smoothing(ctx->c, sweeps, omega);
 }
 
+int nls_guess_features(nls_ctx* ctx, const double* x, double load, float* features_out) {
+  if (!ctx || !ctx->c.is_setup || !x || !features_out) return NLS_E_ARG;
+  return nls::guess_features(ctx->c, x, load, features_out);
+}
+
+int nls_guess_decode(nls_ctx* ctx, const double* x, double load, const float* Y, double* guess_out) {
+  if (!ctx || !ctx->c.is_setup || !x || !Y || !guess_out) return NLS_E_ARG;
+  return nls::guess_decode(ctx->c, x, load, Y, guess_out);
+}
+
+int nls_guess_smooth(nls_ctx* ctx, const double* x, double load, const double* w, double* w_out) {
+  if (!ctx || !ctx->c.is_setup || !x || !w || !w_out) return NLS_E_ARG;
+  return nls::guess_smooth(ctx->c, x, load, w, w_out);
+}
+
 int nls_guess_counts(nls_ctx* ctx, int64_t* proposed, int64_t* accepted) {
   if (!ctx) return NLS_E_ARG;
   return nls::guess_counts(ctx->c, proposed, accepted);
@@ -441,6 +460,16 @@ int nls_get_coarse_nodes(const nls_ctx* ctx, int32_t* first) {
 int nls_get_coarse_basis(const nls_ctx* ctx, double* P0) {
   if (!ctx || !ctx->c.is_setup || !P0) return NLS_E_ARG;
   return nls::get_coarse_basis(ctx->c, P0);
+}
+
+int nls_get_coarse_matrix(const nls_ctx* ctx, double* A0) {
+  if (!ctx || !ctx->c.is_setup || !A0) return NLS_E_ARG;
+  return nls::get_coarse_matrix(ctx->c, A0);
+}
+
+int nls_band_solve(int device, int32_t n, int32_t b, const double* band, const double* rhs, double* x,
+                   int32_t precision, int32_t method, double* factors_out) {
+  return nls::band_solve(device, n, b, band, rhs, x, precision, method, factors_out);
 }
 
 int nls_eval_F(nls_ctx* ctx, const double* u, double* F, int is_dev, double load) {

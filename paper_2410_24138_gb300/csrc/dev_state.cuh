@@ -1,6 +1,7 @@
 // Device-side state of one solver context and the launch / error helpers shared by the
 // translation units that launch kernels (solver.cu, guess.cu).
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <stdexcept>
@@ -13,6 +14,10 @@ namespace nls {
 
 struct CudaFailure : std::runtime_error {
   explicit CudaFailure(const std::string& s) : std::runtime_error(s) {}
+};
+// A kernel's bounded wait gave up (NLS_E_DEVICE_TIMEOUT); the context stays usable.
+struct DeviceTimeout : std::runtime_error {
+  explicit DeviceTimeout(const std::string& s) : std::runtime_error(s) {}
 };
 
 #define CK(call)                                                                                  \
@@ -34,6 +39,32 @@ struct CudaFailure : std::runtime_error {
     (D).launches += 1;                                                     \
     CK(cudaGetLastError());                                                \
   } while (0)
+
+// Status words of the local and coarse solves (per subdomain, and of the coarse factorization).
+// ST_TIMEOUT: a bounded device-side wait gave up (the kernel returned without finishing).
+enum LocalStatus { ST_OK = 0, ST_MAXIT = 1, ST_LS = 2, ST_NONFINITE = 3, ST_PIVOT = 4, ST_TIMEOUT = 9 };
+
+// State of one GMRES cycle on the device (32 bytes).
+struct GmresState {
+  int j;          // iterations done in the current cycle
+  int done;       // 1: converged (|g_j| <= target), breakdown or a non-finite norm
+  int limit;      // iterations allowed in this cycle
+  int pad;
+  double target;  // the cycle stops once |g_j| <= target
+  double res;     // |g_j| after the last iteration (the residual norm of the least-squares problem)
+};
+
+// Tiled band LU of the coarse matrix A_0 (coarse_tlu.cu): square tiles of TS x TS, tile row i
+// holding tiles j = i - TB .. i + TB (SW = 2 TB + 1 slots; slots outside the matrix unused).
+struct TileLU {
+  int TS = 0, NT = 0, TB = 0, SW = 0;
+  bool f32 = true;
+  void* T = nullptr;   // tiles: slot (i, j - i + TB), TS x TS values; j <= i row-major, j > i transposed
+  void* DG = nullptr;  // factored diagonal tiles (unit L below the diagonal, U on and above it)
+  CUtensorMap map;     // FP32 tiles as a 2D tensor of rows of TS values (TMA, 32 x TS boxes)
+  bool solve_tiles = false;  // FP32: inverted diagonal tiles and solve products for the cluster solve
+  int64_t launches_per_factor = 0;
+};
 
 // ------------------------------------------------------------------------------------------
 // device state
@@ -83,14 +114,18 @@ struct Dev {
   int32_t *cj_ptr = nullptr, *a0_ptr = nullptr;
   void* A0f = nullptr;
   void* A0dinv = nullptr;
+  TileLU* tlu = nullptr;  // tiled coarse factorization (when in use)
   int32_t* cstatus = nullptr;
   // vectors
   double* ut = nullptr;  // trial point of the outer backtracking
   double *u = nullptr, *x = nullptr, *u0 = nullptr, *Fx = nullptr, *F = nullptr, *t1 = nullptr, *t2 = nullptr,
          *w0 = nullptr, *gx = nullptr;
-  double *c = nullptr, *ct = nullptr, *dc = nullptr, *g = nullptr, *gt = nullptr, *cres = nullptr;
+  double *c = nullptr, *ct = nullptr, *dc = nullptr, *g = nullptr, *gt = nullptr, *cres = nullptr, *tg = nullptr;
   void* cy = nullptr;
   double *V = nullptr, *partial = nullptr, *scal = nullptr, *coef = nullptr;
+  // GMRES least-squares state on the device: R (m x m), rotations, rotated right-hand side, state
+  double *gR = nullptr, *gcs = nullptr, *gsn = nullptr, *gg = nullptr;
+  GmresState* gst = nullptr;
   int* bad = nullptr;
   unsigned long long* phase = nullptr;  // k_local_newton phase clocks (profiling)
   void* ainv = nullptr;                 // explicit A_0^-1 (transposed, factor precision) for the tangent phase

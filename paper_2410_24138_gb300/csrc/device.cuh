@@ -177,6 +177,50 @@ __device__ inline void nh_jacobian(const double* geo, const double ud[8], double
   }
 }
 
+// The Gauss-point state of Eq. 2 that the tangent needs (c = mu - lambda ln J, weight, F^-1),
+// computed once per element; nh_tangent_rows then forms the two rows of one node at a time, so
+// that the 64 FP64 entries of the element tangent are never live at once.
+struct NHGauss {
+  double c[4], w[4], i00[4], i01[4], i10[4], i11[4];
+};
+
+__device__ inline void nh_gauss(const double* geo, const double u[8], double mu, double lam, NHGauss& G) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const NHPoint<double> p = nh_point<double>(geo + q * 10, u, mu, lam);
+    G.c[q] = p.c;
+    G.w[q] = p.w;
+    G.i00[q] = p.i00;
+    G.i01[q] = p.i01;
+    G.i10[q] = p.i10;
+    G.i11[q] = p.i11;
+  }
+}
+
+// Rows (a, 0) and (a, 1) of the element tangent K of Eq. 2 (the same entries as nh_jacobian):
+// R[i * 8 + 2 b + k] = K_{(a,i),(b,k)}.
+__device__ inline void nh_tangent_rows(const double* geo, const NHGauss& G, double mu, double lam, int a, double R[16]) {
+#pragma unroll
+  for (int k = 0; k < 16; ++k) R[k] = 0.0;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const double* g = geo + q * 10;
+    const double bxa = g[2 * a], bya = g[2 * a + 1];
+    const double p0a = bxa * G.i00[q] + bya * G.i10[q], p1a = bxa * G.i01[q] + bya * G.i11[q];
+    const double w = G.w[q], c = G.c[q];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const double bx = g[2 * b], by = g[2 * b + 1];
+      const double p0b = bx * G.i00[q] + by * G.i10[q], p1b = bx * G.i01[q] + by * G.i11[q];
+      const double gg = mu * (bxa * bx + bya * by);
+      R[2 * b + 0] += w * (gg + lam * p0a * p0b + c * p0a * p0b);
+      R[2 * b + 1] += w * (lam * p0a * p1b + c * p1a * p0b);
+      R[8 + 2 * b + 0] += w * (lam * p1a * p0b + c * p0a * p1b);
+      R[8 + 2 * b + 1] += w * (gg + lam * p1a * p1b + c * p1a * p1b);
+    }
+  }
+}
+
 // ------------------------------------------------------------------------------------------
 // Band LU without pivoting.  Rows of the matrix come from a CSR block (columns are table dof
 // indices; only columns < n belong to the local matrix) or from a dense band array.
@@ -565,15 +609,18 @@ __host__ __device__ constexpr int64_t packed_block_entries(int b) {
   return 2 * (int64_t)SolveBlock<FT>::BS * SolveBlock<FT>::BS + 2 * (int64_t)b * SolveBlock<FT>::BS;
 }
 
+// Blocks t = first + wid, first + wid + stride, ... are packed by warp `wid` (< nwarps); one CTA
+// packing everything passes first = 0, stride = nwarps, several CTAs pass their own offsets.
 template <typename FT>
-__device__ void band_pack_solve(int n, int b, const FT* __restrict__ F, FT* __restrict__ P, FT* tmp, int nwarps) {
+__device__ void band_pack_solve_range(int n, int b, const FT* __restrict__ F, FT* __restrict__ P, FT* tmp, int nwarps,
+                                      int first, int stride) {
   constexpr int BS = SolveBlock<FT>::BS;
   const int W = 2 * b + 1, lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int nblk = (n + BS - 1) / BS;
   const int64_t PB = packed_block_entries<FT>(b);
   if (wid < nwarps) {
     FT* M = tmp + wid * BS * (BS + 1);
-    for (int t = wid; t < nblk; t += nwarps) {
+    for (int t = first + wid; t < nblk; t += stride) {
       const int k0 = t * BS, bs = min(BS, n - k0);
       FT* out = P + (int64_t)t * PB;
       // lower: M[i][j] = L[k0+i][k0+j] (j < i), unit diagonal
@@ -633,6 +680,11 @@ __device__ void band_pack_solve(int n, int b, const FT* __restrict__ F, FT* __re
     }
   }
   __syncthreads();
+}
+
+template <typename FT>
+__device__ void band_pack_solve(int n, int b, const FT* __restrict__ F, FT* __restrict__ P, FT* tmp, int nwarps) {
+  band_pack_solve_range<FT>(n, b, F, P, tmp, nwarps, 0, nwarps);
 }
 
 // Triangular solves with the packed operands, in place on y[0..n) (shared memory): warp 0

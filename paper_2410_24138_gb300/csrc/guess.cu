@@ -73,7 +73,7 @@ struct GuessCtx {
   int32_t *side_n0 = nullptr, *side_n1 = nullptr, *kelem = nullptr, *felem = nullptr;
   float *side_w = nullptr, *box = nullptr;  // box: Lx, Ly
   // per local unknown (concatenated as the local states): (s, t) in the ring box
-  float2* st = nullptr;
+  double2* st = nullptr;
   // per canonical point of every subdomain: 4 local-unknown positions (-1 = ring) and weights
   int4* cidx = nullptr;
   float2* cw = nullptr;
@@ -370,7 +370,7 @@ struct GeoArgs {
   const SubMeta* meta;
   const int32_t *side_n0, *side_n1, *kelem, *felem;
   const float *side_w, *box;
-  const float2* st;
+  const double2* st;
   const int4* cidx;
   const float2* cw;
   const double* kcoef;
@@ -437,7 +437,7 @@ __global__ void k_guess_decode(GeoArgs G, int nsub, const float* Y, float tscale
   const double* S = G.side + (int64_t)sub * 4 * kSide;
   const float* Ys = Y + (int64_t)sub * kNO;
   for (int a = threadIdx.x; a < m.n; a += blockDim.x) {
-    const float2 p = G.st[m.vec_off + a];
+    const double2 p = G.st[m.vec_off + a];
     guess[m.vec_off + a] = coons_eval(S, p.x, p.y) + corr_eval(Ys, p.x, p.y, tscale);
   }
 }
@@ -461,7 +461,7 @@ __global__ void k_guess_harvest(GeoArgs G, int nsub, const double* w, float* dX,
 #pragma unroll
     for (int c = 0; c < 4; ++c)
       if (ids[c] >= 0) {
-        const float2 p = G.st[m.vec_off + ids[c]];
+        const double2 p = G.st[m.vec_off + ids[c]];
         v += wts[c] * (w[m.vec_off + ids[c]] - coons_eval(S, p.x, p.y));
       }
     T[q] = (float)v;
@@ -590,7 +590,7 @@ void build_geometry(Context& c, GuessCtx& G) {
   std::vector<int32_t> n0((size_t)nsub * 4 * kSide), n1((size_t)nsub * 4 * kSide), kel((size_t)nsub * kKS * kKS),
       fel(nsub);
   std::vector<float> sw((size_t)nsub * 4 * kSide), box(2 * (size_t)nsub);
-  std::vector<float2> st(s.total_n);
+  std::vector<double2> st(s.total_n);
   const std::vector<double> diag = jacobi_diagonal(c);
   std::vector<int4> cidx((size_t)nsub * kNO);
   std::vector<float2> cw((size_t)nsub * kNO);
@@ -645,7 +645,7 @@ void build_geometry(Context& c, GuessCtx& G) {
     }
     for (int a = 0; a < m.n; ++a) {
       const int32_t v = s.tnode_gid[m.tnode_off + a];
-      st[m.vec_off + a] = make_float2((float)((gi[v] - i0) / (double)(i1 - i0)), (float)((gj[v] - j0) / (double)(j1 - j0)));
+      st[m.vec_off + a] = make_double2((gi[v] - i0) / (double)(i1 - i0), (gj[v] - j0) / (double)(j1 - j0));
     }
     for (int b = 0; b < kGrid; ++b)
       for (int a = 0; a < kGrid; ++a) {
@@ -732,6 +732,63 @@ GuessProposal guess_propose(Context& c, const double* x, double load) {
   out.sweeps = G->sweeps;
   out.omega = G->omega;
   return out;
+}
+
+// Smoothing parameters of the attached guess (diagonal, sweeps, omega) without a proposal.
+GuessProposal guess_smoothing(Context& c) {
+  GuessProposal out;
+  GuessCtx* G = c.dev ? (GuessCtx*)c.dev->guess : nullptr;
+  if (!G) return out;
+  out.diag = G->diag;
+  out.sweeps = G->sweeps;
+  out.omega = G->omega;
+  return out;
+}
+
+// Test hooks: the raw features at x (host) into out [nsub x 391], and the decode of given network
+// outputs Y [nsub x 1024] (normalised units) at x into out [total local unknowns].
+int guess_features(Context& c, const double* x, double load, float* out) {
+  GuessCtx* G = c.dev ? (GuessCtx*)c.dev->guess : nullptr;
+  if (!G) {
+    c.last_error = "the learned-guess hooks need an attached network";
+    return NLS_E_ARG;
+  }
+  Dev& D = *c.dev;
+  try {
+    CK(cudaMemcpyAsync(D.x, x, sizeof(double) * c.N, cudaMemcpyHostToDevice, D.s));
+    GeoArgs a = geo_args(c, *G, D.x, load);
+    LAUNCH(D, k_guess_features, G->nsub, 128, 0, a, G->nsub);
+    CK(cudaMemcpyAsync(out, G->raw, sizeof(float) * (size_t)G->nsub * kNF, cudaMemcpyDeviceToHost, D.s));
+    CK(cudaStreamSynchronize(D.s));
+  } catch (const std::exception& ex) {
+    c.last_error = ex.what();
+    return NLS_E_CUDA;
+  }
+  return NLS_OK;
+}
+
+int guess_decode(Context& c, const double* x, double load, const float* Y, double* out) {
+  GuessCtx* G = c.dev ? (GuessCtx*)c.dev->guess : nullptr;
+  if (!G || !G->net) {
+    c.last_error = "the learned-guess hooks need an attached network";
+    return NLS_E_ARG;
+  }
+  Dev& D = *c.dev;
+  GuessNet& N = *G->net;
+  try {
+    N.ensure_batch(G->nsub);
+    CK(cudaMemcpyAsync(D.x, x, sizeof(double) * c.N, cudaMemcpyHostToDevice, D.s));
+    CK(cudaMemcpyAsync(N.Y, Y, sizeof(float) * (size_t)G->nsub * kNO, cudaMemcpyHostToDevice, D.s));
+    GeoArgs a = geo_args(c, *G, D.x, load);
+    LAUNCH(D, k_guess_features, G->nsub, 128, 0, a, G->nsub);
+    LAUNCH(D, k_guess_decode, G->nsub, 128, 0, a, G->nsub, N.Y, N.tscale, G->guess);
+    CK(cudaMemcpyAsync(out, G->guess, sizeof(double) * c.ov.total_n, cudaMemcpyDeviceToHost, D.s));
+    CK(cudaStreamSynchronize(D.s));
+  } catch (const std::exception& ex) {
+    c.last_error = ex.what();
+    return NLS_E_CUDA;
+  }
+  return NLS_OK;
 }
 
 int guess_set_smoothing(Context& c, int32_t sweeps, double omega) {

@@ -156,6 +156,9 @@ int eval_Fx(Context& c, const double* u, double* Fx, int is_dev, double load, in
 int apply_tangent(Context& c, const double* v, double* y, int is_dev);
 int get_local_states(Context& c, double* w, int is_dev);
 int get_coarse_basis(const Context& c, double* P0);
+int get_coarse_matrix(const Context& c, double* A0);
+int band_solve(int device, int32_t n, int32_t b, const double* band, const double* rhs, double* x, int32_t precision,
+               int32_t method, double* factors_out);
 int kernel_stats(const Context& c, int32_t cap, nls_kernel_stat* out, int32_t* n_out);
 void reset_kernel_stats(Context& c);
 int get_tuning(const Context& c, nls_tuning* out);
@@ -173,6 +176,10 @@ struct GuessProposal {
   double omega = 0.8;
 };
 GuessProposal guess_propose(Context& c, const double* x, double load);
+GuessProposal guess_smoothing(Context& c);
+int guess_features(Context& c, const double* x, double load, float* out);
+int guess_decode(Context& c, const double* x, double load, const float* Y, double* out);
+int guess_smooth(Context& c, const double* x, double load, const double* w, double* out);
 int guess_set_smoothing(Context& c, int32_t sweeps, double omega);
 void guess_after_local(Context& c, const double* x, double load, bool proposed);
 void guess_free(Context& c);

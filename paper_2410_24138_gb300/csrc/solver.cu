@@ -36,6 +36,12 @@
 
 namespace nls {
 
+// coarse_tlu.cu
+void tlu_prepare(Context& c, bool f32);
+void tlu_factor(Context& c);
+void tlu_free(Context& c);
+bool tlu_solve(Context& c, const double* rhs, double* z, int accumulate, const int* skip, int* reset);
+
 namespace {
 
 
@@ -45,7 +51,6 @@ constexpr int kVecThreads = 256;
 constexpr int kVecWarps = kVecBlocks * (kVecThreads / 32);
 constexpr int kMaxGmresVecs = 128;
 
-enum LocalStatus { ST_OK = 0, ST_MAXIT = 1, ST_LS = 2, ST_NONFINITE = 3, ST_PIVOT = 4 };
 
 // ------------------------------------------------------------------------------------------
 // argument blocks
@@ -230,8 +235,10 @@ __device__ bool local_residual(const LocalArgs& A, const SubMeta& m, const doubl
 
 // Local Jacobian into the CSR block of the subdomain (rows per m.nrows) and, when `band` is
 // given, also into the band rows of the local matrix (row-major, 2 b + 1 per row, local
-// unknowns only) that the in-place band LU then factors.
-template <int LAW, typename JT, typename FT = double>
+// unknowns only) that the in-place band LU then factors.  Element tangents are formed in FP64
+// for both forms: the CSR block, against which the FP32 factors are refined, is the exact
+// Jacobian; only the band copy that is factored is rounded to the factors' precision.
+template <int LAW, typename FT = double>
 __device__ void local_jacobian(const LocalArgs& A, const SubMeta& m, const double* xt, double* csr,
                                FT* band = nullptr) {
   const int nen = A.nen, nd = A.ndof, ned = nen * nd, ned2 = ned * ned;
@@ -283,30 +290,32 @@ __device__ void local_jacobian(const LocalArgs& A, const SubMeta& m, const doubl
           ue[2 * a] = xt[2 * lc[a]];
           ue[2 * a + 1] = xt[2 * lc[a] + 1];
         }
-        JT K[64];
-        dev::nh_jacobian<JT>(geo, ue, A.mu, A.lam, K);
-        {
-          double oc[64];
+        dev::NHGauss G;
+        dev::nh_gauss(geo, ue, A.mu, A.lam, G);
+#pragma unroll 1
+        for (int a = 0; a < 4; ++a) {
+          double R[16];
+          dev::nh_tangent_rows(geo, G, A.mu, A.lam, a, R);
+          const int32_t* epa = ep + 16 * a;  // rows (a, 0) and (a, 1): 16 consecutive targets
+          double oc[16];
 #pragma unroll
-          for (int q = 0; q < 64; ++q) oc[q] = (ep[q] >= 0) ? csr[ep[q]] : 0.0;
+          for (int q = 0; q < 16; ++q) oc[q] = (epa[q] >= 0) ? csr[epa[q]] : 0.0;
 #pragma unroll
-          for (int q = 0; q < 64; ++q)
-            if (ep[q] >= 0) csr[ep[q]] = oc[q] + (double)K[q];
-        }
-        if (band) {
-#pragma unroll
-          for (int a = 0; a < 4; ++a)
+          for (int q = 0; q < 16; ++q)
+            if (epa[q] >= 0) csr[epa[q]] = oc[q] + R[q];
+          if (band && lc[a] < m.nV) {
 #pragma unroll
             for (int b = 0; b < 4; ++b)
-              if (lc[a] < m.nV && lc[b] < m.nV) {
+              if (lc[b] < m.nV) {
 #pragma unroll
                 for (int da = 0; da < 2; ++da)
 #pragma unroll
                   for (int db = 0; db < 2; ++db) {
                     const int row = 2 * lc[a] + da, col = 2 * lc[b] + db;
-                    band[(int64_t)row * W + (col - row + m.b)] += (FT)K[(2 * a + da) * 8 + 2 * b + db];
+                    band[(int64_t)row * W + (col - row + m.b)] += (FT)R[da * 8 + 2 * b + db];
                   }
               }
+          }
         }
       }
     }
@@ -352,6 +361,42 @@ __device__ int local_solve(const LocalArgs& A, const SubMeta& m, const int32_t* 
   return sweeps;
 }
 
+// Damped Jacobi sweeps on a proposed local start (in xt's local unknowns): they remove the
+// pointwise part of the proposal's error, w <- w - omega r(w) / (d (1 + w^2)) on all entries at
+// once, d the diagonal of the Jacobian's leading term.  Leaves the residual of the result in racc
+// and returns false if an evaluation was not finite.
+template <int LAW>
+__device__ bool smooth_proposal(const LocalArgs& A, const SubMeta& m, double* xt, double* racc) {
+  bool okg = local_residual<LAW>(A, m, xt, racc);
+  for (int sw = 0; sw < A.guess_sweeps && okg; ++sw) {
+    for (int a = threadIdx.x; a < m.n; a += blockDim.x) {
+      const double q = (LAW == NLS_LAW_DIFFUSION) ? 1.0 + xt[a] * xt[a] : 1.0;
+      xt[a] -= A.guess_omega * racc[a] / (A.guess_diag[m.vec_off + a] * q);
+    }
+    __syncthreads();
+    okg = local_residual<LAW>(A, m, xt, racc);
+  }
+  return okg;
+}
+
+// Test hook: the smoothing of given starts (A.guess, concatenated local vectors) at the point A.x,
+// one CTA per subdomain, into A.out (concatenated local vectors).
+template <int LAW>
+__global__ void __launch_bounds__(256) k_guess_smooth(LocalArgs A) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  double* xt = (double*)smem;
+  double* racc = xt + A.max_nt;
+  const int sub = blockIdx.x, nd = A.ndof;
+  const SubMeta m = A.meta[sub];
+  for (int t = threadIdx.x; t < m.nt; t += blockDim.x)
+    xt[t] = A.x[(int64_t)A.tnode_gid[m.tnode_off + t / nd] * nd + t % nd];
+  __syncthreads();
+  for (int a = threadIdx.x; a < m.n; a += blockDim.x) xt[a] = A.guess[m.vec_off + a];
+  __syncthreads();
+  smooth_proposal<LAW>(A, m, xt, racc);
+  for (int a = threadIdx.x; a < m.n; a += blockDim.x) A.out[m.vec_off + a] = xt[a];
+}
+
 // ------------------------------------------------------------------------------------------
 // k_local_newton: the batched local corrections T_i of Eq. 4
 // ------------------------------------------------------------------------------------------
@@ -369,7 +414,6 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 128 ? 4 : 1)) k_local_newton(Lo
   FT* rp = (FT*)(smem + P.rp);
   int* flag = (int*)(smem + P.flag);
   __shared__ int s_item;
-  using JT = typename std::conditional<LAW == NLS_LAW_DIFFUSION, double, FT>::type;
   const int tid = threadIdx.x, nd = A.ndof;
   constexpr int BSI = dev::SolveBlock<FT>::BS;
   const int inv_warps = min((int)(blockDim.x >> 5), (int)((P.rp - P.win) / (sizeof(FT) * BSI * (BSI + 1))));
@@ -421,16 +465,7 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 128 ? 4 : 1)) k_local_newton(Lo
         xt[a] = A.guess[m.vec_off + a];
       }
       __syncthreads();
-      bool okg = local_residual<LAW>(A, m, xt, racc);
-      // damped Jacobi on the local problem removes the pointwise part of the proposal's error
-      for (int sw = 0; sw < A.guess_sweeps && okg; ++sw) {
-        for (int a = tid; a < n; a += blockDim.x) {
-          const double q = (LAW == NLS_LAW_DIFFUSION) ? 1.0 + xt[a] * xt[a] : 1.0;
-          xt[a] -= A.guess_omega * racc[a] / (A.guess_diag[m.vec_off + a] * q);
-        }
-        __syncthreads();
-        okg = local_residual<LAW>(A, m, xt, racc);
-      }
+      bool okg = smooth_proposal<LAW>(A, m, xt, racc);
       double lg = 0.0;
       for (int a = tid; a < n; a += blockDim.x) lg += racc[a] * racc[a];
       double rng = sqrt(dev::block_sum(lg, red));
@@ -458,7 +493,7 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 128 ? 4 : 1)) k_local_newton(Lo
         break;
       }
       if (!stored) {
-        local_jacobian<LAW, JT, FT>(A, m, xt, csr, F);
+        local_jacobian<LAW, FT>(A, m, xt, csr, F);
         mark(1);
         if (dev::band_lu_inplace<FT>(n, m.b, F, win, rp, flag)) {
           status = ST_PIVOT;
@@ -509,7 +544,7 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 128 ? 4 : 1)) k_local_newton(Lo
       rn = rtn;
     }
     if (A.want_tangent && status != ST_NONFINITE && status != ST_PIVOT) {
-      local_jacobian<LAW, JT, FT>(A, m, xt, csr, F);
+      local_jacobian<LAW, FT>(A, m, xt, csr, F);
       mark(5);
       if (dev::band_lu_inplace<FT>(n, m.b, F, win, rp, flag)) status = ST_PIVOT;
       else dev::band_pack_solve<FT>(n, m.b, F, Dv, win, inv_warps);
@@ -594,7 +629,7 @@ __global__ void __launch_bounds__(256) k_harmonic(LocalArgs A) {
   double* F = (double*)A.factor + m.factor_off;
   for (int t = tid; t < m.nt; t += blockDim.x) xt[t] = A.x[(int64_t)A.tnode_gid[m.tnode_off + t / nd] * nd + t % nd];
   __syncthreads();
-  local_jacobian<LAW, double>(A, m, xt, csr);
+  local_jacobian<LAW>(A, m, xt, csr);
   if (n == 0 || nc == 0) return;
   dev::RowSource src{rowptr, colidx, csr};
   if (dev::band_lu<double>(n, m.b, src, F, win, rp, flag)) {
@@ -617,7 +652,7 @@ __global__ void __launch_bounds__(256) k_harmonic(LocalArgs A) {
   }
 }
 
-template <int LAW, typename JT>
+template <int LAW>
 __global__ void __launch_bounds__(256) k_galerkin(LocalArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
   const SmemPlan P = smem_plan<double>(A.max_n, A.max_nt, A.max_b, false);
@@ -632,7 +667,7 @@ __global__ void __launch_bounds__(256) k_galerkin(LocalArgs A) {
   double* csr = A.csr + m.nnz_off;
   for (int t = tid; t < m.nt; t += blockDim.x) xt[t] = A.x[(int64_t)A.tnode_gid[m.tnode_off + t / nd] * nd + t % nd];
   __syncthreads();
-  local_jacobian<LAW, JT>(A, m, xt, csr);
+  local_jacobian<LAW>(A, m, xt, csr);
   if (nc == 0) return;
   // Y = K^(j) Phi_j
   for (int64_t idx = tid; idx < (int64_t)m.nt * nc; idx += blockDim.x) {
@@ -699,7 +734,7 @@ __global__ void __launch_bounds__(1024) k_coarse_factor(int N0, int b0, const do
 // they are applied (coarse_solve): the FP64 residual of one vector costs N0 (2 b0 + 1)
 // multiply-adds, that of every column of the inverse N0 times as many.
 template <typename FT>
-__global__ void __launch_bounds__(256) k_coarse_inverse(int N0, int b0, const FT* Dinv, FT* AinvT, int l2d) {
+__global__ void __launch_bounds__(512) k_coarse_inverse(int N0, int b0, const FT* Dinv, FT* AinvT, int l2d) {
   extern __shared__ __align__(16) unsigned char smem[];
   FT* y = (FT*)smem;
   constexpr int BS = dev::SolveBlock<FT>::BS;
@@ -806,43 +841,22 @@ __global__ void __launch_bounds__(256) k_coarse_residual(int N0, int b0, const d
   }
 }
 
-// coarse solve z = A0^-1 g (global-memory vectors), FP64 refinement against the band A0
+// One coarse solve with the packed band factors in one CTA (the solve vector in shared memory):
+// z = (accumulate ? z : 0) + A_0^-1 rhs in the factors' precision.  With *skip set (a refinement
+// that has converged) the kernel does nothing; `reset`, if given, is cleared (the refinement flag
+// of the solve that starts here).  Needs blockDim.x >= 32 + b0.
 template <typename FT>
-__global__ void __launch_bounds__(256) k_coarse_solve(int N0, int b0, const double* A0, const FT* F, const FT* Dinv,
-                                                       const double* g, double* z, double* res, FT* y, double ir_rtol,
-                                                       int ir_max, int l2d) {
-  __shared__ double red[40];
-  const int W = 2 * b0 + 1;
-  double loc = 0.0;
-  for (int a = threadIdx.x; a < N0; a += blockDim.x) {
-    y[a] = (FT)g[a];
-    loc += g[a] * g[a];
-  }
-  const double gn = sqrt(dev::block_sum(loc, red));
-  dev::band_solve_packed<FT, true>(N0, b0, Dinv, y, l2d);
-  for (int a = threadIdx.x; a < N0; a += blockDim.x) z[a] = (double)y[a];
+__global__ void __launch_bounds__(512) k_coarse_band_solve(int N0, int b0, const FT* Dinv, const double* rhs,
+                                                             double* z, int accumulate, const int* skip, int* reset,
+                                                             int l2d) {
+  if (skip && *skip) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  FT* y = (FT*)smem;
+  if (reset && threadIdx.x == 0) *reset = 0;
+  for (int a = threadIdx.x; a < N0; a += blockDim.x) y[a] = (FT)rhs[a];
   __syncthreads();
-  if (sizeof(FT) == 4) {
-    for (int sw = 0; sw < ir_max; ++sw) {
-      double l2 = 0.0;
-      for (int a = threadIdx.x; a < N0; a += blockDim.x) {
-        double acc = g[a];
-        for (int d = 0; d < W; ++d) {
-          const int col = a - b0 + d;
-          if (col >= 0 && col < N0) acc -= A0[(int64_t)a * W + d] * z[col];
-        }
-        res[a] = acc;
-        l2 += acc * acc;
-      }
-      const double rn = sqrt(dev::block_sum(l2, red));
-      if (!(rn > ir_rtol * gn)) break;
-      for (int a = threadIdx.x; a < N0; a += blockDim.x) y[a] = (FT)res[a];
-      __syncthreads();
-      dev::band_solve_packed<FT, true>(N0, b0, Dinv, y, l2d);
-      for (int a = threadIdx.x; a < N0; a += blockDim.x) z[a] += (double)y[a];
-      __syncthreads();
-    }
-  }
+  dev::band_solve_packed<FT, true>(N0, b0, Dinv, y, l2d);
+  for (int a = threadIdx.x; a < N0; a += blockDim.x) z[a] = (accumulate ? z[a] : 0.0) + (double)y[a];
 }
 
 // ------------------------------------------------------------------------------------------
@@ -902,7 +916,7 @@ __global__ void k_node_residual(int64_t n_nodes, int nd, const int64_t* star_ptr
   }
 }
 
-template <int LAW, typename JT>
+template <int LAW>
 __global__ void k_global_jacobian(const int32_t* elems, int e0, int e1, const int32_t* conn, const double* geom,
                                   const double* kcoef, const double* x, const int32_t* epos, double* val, double mu,
                                   double lam) {
@@ -926,11 +940,16 @@ __global__ void k_global_jacobian(const int32_t* elems, int e0, int e1, const in
         ue[2 * a] = x[2 * (int64_t)c[a]];
         ue[2 * a + 1] = x[2 * (int64_t)c[a] + 1];
       }
-      JT K[64];
-      dev::nh_jacobian<JT>(geo, ue, mu, lam, K);
+      dev::NHGauss G;
+      dev::nh_gauss(geo, ue, mu, lam, G);
       const int32_t* ep = epos + (int64_t)e * 64;
+#pragma unroll 1
+      for (int a = 0; a < 4; ++a) {
+        double R[16];
+        dev::nh_tangent_rows(geo, G, mu, lam, a, R);
 #pragma unroll
-      for (int q = 0; q < 64; ++q) val[ep[q]] += (double)K[q];
+        for (int q = 0; q < 16; ++q) val[ep[16 * a + q]] += R[q];
+      }
     }
   }
 }
@@ -1029,6 +1048,73 @@ __global__ void k_scale_inv(int64_t n, const double* x, const double* nrm, doubl
 
 __global__ void k_sqrt_inplace(double* x) { *x = sqrt(*x); }
 
+// ---- GMRES least-squares state on the device (GmresState) --------------------------------------
+
+// A new cycle: g = (rn, 0, ..., 0).
+__global__ void k_gmres_start(int m, double rn, double target, int limit, double* g, GmresState* st) {
+  for (int i = threadIdx.x; i <= m; i += blockDim.x) g[i] = (i == 0) ? rn : 0.0;
+  if (threadIdx.x == 0) {
+    st->j = 0;
+    st->done = 0;
+    st->limit = limit;
+    st->target = target;
+    st->res = rn;
+  }
+}
+
+// After iteration j: the Hessenberg column h_i = scal[i] + scal[half + i] (the two Gram-Schmidt
+// passes, i <= j) and h_{j+1} = scal[kMaxGmresVecs]; apply the earlier rotations to it, form the
+// rotation that annihilates h_{j+1}, rotate g, keep the column of R (row-major, m x m); then
+// decide whether the cycle goes on, and (inside a graph) set `h`, the condition of the next
+// iteration's IF node.
+__global__ void k_gmres_givens(int j, int m, const double* scal, double* Rm, double* cs, double* sn, double* g,
+                               GmresState* st, cudaGraphConditionalHandle h, int use_handle) {
+  if (threadIdx.x != 0) return;
+  double col[kMaxGmresVecs / 2 + 1];
+  for (int i = 0; i <= j; ++i) col[i] = scal[i] + scal[kMaxGmresVecs / 2 + i];
+  const double hn = scal[kMaxGmresVecs];
+  for (int i = 0; i < j; ++i) {
+    const double t = cs[i] * col[i] + sn[i] * col[i + 1];
+    col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
+    col[i] = t;
+  }
+  const double d = hypot(col[j], hn);
+  cs[j] = col[j] / d;
+  sn[j] = hn / d;
+  col[j] = d;
+  g[j + 1] = -sn[j] * g[j];
+  g[j] = cs[j] * g[j];
+  for (int i = 0; i <= j; ++i) Rm[(size_t)i * m + j] = col[i];
+  const double res = fabs(g[j + 1]);
+  const int done = (!isfinite(hn) || res <= st->target || hn == 0.0) ? 1 : 0;
+  st->j = j + 1;
+  st->res = res;
+  st->done = done;
+  if (use_handle) cudaGraphSetConditional(h, (!done && j + 1 < st->limit) ? 1u : 0u);
+}
+
+// y = R^-1 g over the cycle's st->j iterations (back substitution) into coef.
+__global__ void k_gmres_lsq(int m, const double* Rm, const double* g, const GmresState* st, double* coef) {
+  if (threadIdx.x != 0) return;
+  const int n = st->j;
+  for (int i = n - 1; i >= 0; --i) {
+    double acc = g[i];
+    for (int k = i + 1; k < n; ++k) acc -= Rm[(size_t)i * m + k] * coef[k];
+    coef[i] = acc / Rm[(size_t)i * m + i];
+  }
+}
+
+// w += sign sum_{i < st->j} coef[i] V_i (the number of vectors read from the device)
+__global__ void k_multiaxpy_dev(int64_t n, const GmresState* st, const double* V, int64_t ld, const double* coef,
+                                double sign, double* w) {
+  const int nv = st->j;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int i = 0; i < nv; ++i) acc += coef[i] * V[(int64_t)i * ld + k];
+    w[k] += sign * acc;
+  }
+}
+
 }  // namespace
 
 
@@ -1056,6 +1142,20 @@ int apply_threads(const Context& c) {
 
 bool fp32_local(const Context& c) { return c.opt.local_precision == NLS_PREC_FP32_IR; }
 bool fp32_coarse(const Context& c) { return c.opt.coarse_precision == NLS_PREC_FP32_IR; }
+
+// Largest half bandwidth of A_0 the one-CTA band LU takes (its window sits in shared memory) and
+// that the coarse band solves take (warp 0 plus one thread per coupled row in a CTA of at most
+// 512 threads, which keeps 128 registers per thread for the double-buffered operands).
+constexpr int kMaxBandB0 = 128;
+constexpr int kMaxSolveB0 = 512 - 32;
+
+bool coarse_tiles(const Context& c) {
+  return c.opt.coarse_factor == NLS_COARSE_FACTOR_TILES ||
+         (c.opt.coarse_factor == NLS_COARSE_FACTOR_AUTO && c.cs.b0 > kMaxBandB0);
+}
+
+// CTA size of the one-CTA coarse band solves: warp 0 plus one thread per coupled row.
+int coarse_solve_threads(const Context& c) { return std::max(256, (32 + c.cs.b0 + 31) / 32 * 32); }
 
 LocalArgs make_args(const Context& c, const LocalSet& hs, const DeviceLocalSet& ds) {
   LocalArgs A;
@@ -1154,14 +1254,11 @@ void global_jacobian(Context& c, const double* x) {
   for (size_t k = 0; k + 1 < c.g_color_ptr.size(); ++k) {
     const int e0 = c.g_color_ptr[k], e1 = c.g_color_ptr[k + 1];
     if (c.law == NLS_LAW_DIFFUSION)
-      LAUNCH(D, (k_global_jacobian<NLS_LAW_DIFFUSION, double>), grid_for(e1 - e0), 256, 0, D.g_elem, e0, e1, D.conn,
-             D.geom, D.kcoef, x, D.g_epos, D.g_val, mu, lam);
-    else if (fp32_local(c))
-      LAUNCH(D, (k_global_jacobian<NLS_LAW_NEOHOOKE, float>), grid_for(e1 - e0), 256, 0, D.g_elem, e0, e1, D.conn,
-             D.geom, D.kcoef, x, D.g_epos, D.g_val, mu, lam);
+      LAUNCH(D, (k_global_jacobian<NLS_LAW_DIFFUSION>), grid_for(e1 - e0), 256, 0, D.g_elem, e0, e1, D.conn, D.geom,
+             D.kcoef, x, D.g_epos, D.g_val, mu, lam);
     else
-      LAUNCH(D, (k_global_jacobian<NLS_LAW_NEOHOOKE, double>), grid_for(e1 - e0), 256, 0, D.g_elem, e0, e1, D.conn,
-             D.geom, D.kcoef, x, D.g_epos, D.g_val, mu, lam);
+      LAUNCH(D, (k_global_jacobian<NLS_LAW_NEOHOOKE>), grid_for(e1 - e0), 256, 0, D.g_elem, e0, e1, D.conn, D.geom,
+             D.kcoef, x, D.g_epos, D.g_val, mu, lam);
   }
 }
 
@@ -1366,6 +1463,7 @@ bool coarse_status_ok(Dev& D) {
   int32_t st = 0;
   CK(cudaMemcpyAsync(&st, D.cstatus, sizeof(int32_t), cudaMemcpyDeviceToHost, D.s));
   sync(D);
+  if (st == ST_TIMEOUT) throw DeviceTimeout("a tile of the coarse factorization gave up waiting for its operands");
   return st == ST_OK;
 }
 
@@ -1382,9 +1480,8 @@ void coarse_assemble_launch(Context& c, const double* x) {
   A.x = x;
   const int T = 256;
   const size_t sm = smem_plan<double>(c.nov.max_n, c.nov.max_nt, c.nov.max_b, false).total;
-  if (c.law == NLS_LAW_DIFFUSION) LAUNCH(D, (k_galerkin<NLS_LAW_DIFFUSION, double>), c.nov.count, T, sm, A);
-  else if (fp32_local(c)) LAUNCH(D, (k_galerkin<NLS_LAW_NEOHOOKE, float>), c.nov.count, T, sm, A);
-  else LAUNCH(D, (k_galerkin<NLS_LAW_NEOHOOKE, double>), c.nov.count, T, sm, A);
+  if (c.law == NLS_LAW_DIFFUSION) LAUNCH(D, (k_galerkin<NLS_LAW_DIFFUSION>), c.nov.count, T, sm, A);
+  else LAUNCH(D, (k_galerkin<NLS_LAW_NEOHOOKE>), c.nov.count, T, sm, A);
   const int64_t ne = (int64_t)c.cs.N0 * (2 * c.cs.b0 + 1);
   LAUNCH(D, k_a0_gather, grid_for(ne), 256, 0, ne, D.a0_ptr, D.a0_src, D.blk, D.A0);
 }
@@ -1393,6 +1490,10 @@ void coarse_assemble_launch(Context& c, const double* x) {
 // solve operands; the status word is read by coarse_status_ok.
 void coarse_factor_launch(Context& c) {
   Dev& D = *c.dev;
+  if (D.tlu) {
+    tlu_factor(c);
+    return;
+  }
   const bool f32 = fp32_coarse(c);
   const size_t fsm = coarse_factor_smem(c, f32);
   auto factor = [&](int T) {
@@ -1449,14 +1550,28 @@ void coarse_solve(Context& c, const double* g, double* z) {
     }
     return;
   }
-  if (fp32_coarse(c))
-    LAUNCH(D, k_coarse_solve<float>, 1, 256, 0, c.cs.N0, c.cs.b0, D.A0, (const float*)D.A0f,
-           (const float*)D.A0dinv, g, z, D.cres, (float*)D.cy, c.opt.ir_rtol, c.opt.ir_max_sweeps,
-           c.opt.l2_prefetch);
-  else
-    LAUNCH(D, k_coarse_solve<double>, 1, 256, 0, c.cs.N0, c.cs.b0, D.A0, (const double*)D.A0f,
-           (const double*)D.A0dinv, g, z, D.cres, (double*)D.cy, c.opt.ir_rtol, c.opt.ir_max_sweeps,
-           c.opt.l2_prefetch);
+  // band factors: one solve in one CTA, then (FP32 factors) up to ir_max_sweeps refinement steps
+  // z += A_0^-1 (g - A_0 z) with the FP64 residual on every SM; the same fixed launch sequence
+  // as above, the steps after convergence returning at once
+  const int N0 = c.cs.N0;
+  const bool f32 = fp32_coarse(c);
+  const int T = coarse_solve_threads(c);
+  auto band_solve = [&](const double* rhs, int accumulate, const int* skip, int* reset) {
+    if (tlu_solve(c, rhs, z, accumulate, skip, reset)) return;  // tiled factors: the cluster solve
+    if (f32)
+      LAUNCH(D, k_coarse_band_solve<float>, 1, T, sizeof(float) * N0, N0, c.cs.b0, (const float*)D.A0dinv, rhs, z,
+             accumulate, skip, reset, c.opt.l2_prefetch);
+    else
+      LAUNCH(D, k_coarse_band_solve<double>, 1, T, sizeof(double) * N0, N0, c.cs.b0, (const double*)D.A0dinv, rhs, z,
+             accumulate, skip, reset, c.opt.l2_prefetch);
+  };
+  band_solve(g, 0, nullptr, D.cflag);
+  const int sweeps = f32 ? c.opt.ir_max_sweeps : 0;
+  for (int sw = 0; sw < sweeps; ++sw) {
+    LAUNCH(D, k_coarse_residual, (N0 + 7) / 8, 256, 0, N0, c.cs.b0, D.A0, g, z, D.cres, D.cpart,
+           (unsigned*)(D.cflag + 1), D.cflag, c.opt.ir_rtol);
+    band_solve(D.cres, 1, D.cflag, nullptr);
+  }
 }
 
 // x = u - P0 c
@@ -1690,6 +1805,11 @@ int device_setup(Context& c) {
     D.partial = D.alloc<double>((size_t)kVecWarps * (kMaxGmresVecs + 2));
     D.scal = D.alloc<double>(kMaxGmresVecs + 8);
     D.coef = D.alloc<double>(kMaxGmresVecs + 8);
+    D.gR = D.alloc<double>((size_t)D.m * D.m);
+    D.gcs = D.alloc<double>(D.m);
+    D.gsn = D.alloc<double>(D.m);
+    D.gg = D.alloc<double>(D.m + 1);
+    D.gst = (GmresState*)D.alloc<double>(4);
     D.bad = D.alloc<int>(4);
     D.phase = D.alloc<unsigned long long>(8);
     CK(cudaMemsetAsync(D.phase, 0, sizeof(unsigned long long) * 8, D.s));
@@ -1700,9 +1820,17 @@ int device_setup(Context& c) {
     auto need = [&](size_t b, const char* what) {
       if (b > lim) throw std::runtime_error(std::string(what) + " needs more shared memory than the device offers");
     };
-    if (c.ov.max_b > 128 || (c.coarse_kind == NLS_COARSE_RGDSW && c.cs.b0 > 128))
-      throw std::runtime_error("a band matrix has a half bandwidth above 128 (local " + std::to_string(c.ov.max_b) +
-                               ", coarse " + std::to_string(c.cs.b0) + "); the band factorisation supports 128");
+    if (c.ov.max_b > 128)
+      throw std::runtime_error("a local band matrix has a half bandwidth above 128 (" + std::to_string(c.ov.max_b) +
+                               "); the local band factorisation supports 128");
+    if (c.coarse_kind == NLS_COARSE_RGDSW && !coarse_tiles(c) && c.cs.b0 > kMaxBandB0)
+      throw std::runtime_error("the coarse matrix has a half bandwidth of " + std::to_string(c.cs.b0) +
+                               "; the one-CTA band factorisation supports " + std::to_string(kMaxBandB0) +
+                               " (the tiled one, coarse_factor = NLS_COARSE_FACTOR_TILES, up to " +
+                               std::to_string(kMaxSolveB0) + ")");
+    if (c.coarse_kind == NLS_COARSE_RGDSW && c.cs.b0 > kMaxSolveB0)
+      throw std::runtime_error("the coarse matrix has a half bandwidth of " + std::to_string(c.cs.b0) +
+                               "; the coarse solves support " + std::to_string(kMaxSolveB0));
     need(local_newton_smem<float>(c.ov), "local Newton (FP32 factors)");
     if (!fp32_local(c)) need(local_newton_smem<double>(c.ov), "local Newton (FP64 factors)");
     set_smem(k_local_newton<NLS_LAW_DIFFUSION, float, 128>, lim);
@@ -1714,18 +1842,20 @@ int device_setup(Context& c) {
     set_smem(k_local_newton<NLS_LAW_NEOHOOKE, float, 256>, lim);
     set_smem(k_local_newton<NLS_LAW_NEOHOOKE, double, 256>, lim);
     set_smem(k_local_apply<float>, lim);
+    set_smem(k_guess_smooth<NLS_LAW_DIFFUSION>, lim);
+    set_smem(k_guess_smooth<NLS_LAW_NEOHOOKE>, lim);
     set_smem(k_local_apply<double>, lim);
     set_smem(k_harmonic<NLS_LAW_DIFFUSION>, lim);
     set_smem(k_harmonic<NLS_LAW_NEOHOOKE>, lim);
-    set_smem(k_galerkin<NLS_LAW_DIFFUSION, double>, lim);
-    set_smem(k_galerkin<NLS_LAW_NEOHOOKE, float>, lim);
-    set_smem(k_galerkin<NLS_LAW_NEOHOOKE, double>, lim);
+    set_smem(k_galerkin<NLS_LAW_DIFFUSION>, lim);
+    set_smem(k_galerkin<NLS_LAW_NEOHOOKE>, lim);
     set_smem(k_coarse_factor<float>, lim);
     set_smem(k_coarse_factor<double>, lim);
     if (c.coarse_kind == NLS_COARSE_RGDSW) {
       Coarse& cs = c.cs;
       if (cs.N0 == 0) throw std::runtime_error("the partition has no coarse nodes (one subdomain?)");
-      need(coarse_factor_smem(c, fp32_coarse(c)), "coarse band factorization");
+      if (!coarse_tiles(c)) need(coarse_factor_smem(c, fp32_coarse(c)), "coarse band factorization");
+      need((fp32_coarse(c) ? sizeof(float) : sizeof(double)) * (size_t)cs.N0, "coarse band solve");
       upload_set(D, c.nov, D.nov, false, false);
       D.phi = D.upload(cs.phi_host);
       D.phi_off = D.upload(cs.phi_off);
@@ -1740,20 +1870,22 @@ int device_setup(Context& c) {
       if (fp32_coarse(c)) {
         D.A0f = D.alloc<float>((size_t)cs.N0 * (2 * cs.b0 + 1));
         D.A0dinv = D.alloc<float>(ndinv);
-        D.cy = D.alloc<float>(cs.N0);
       } else {
         D.A0f = D.alloc<double>((size_t)cs.N0 * (2 * cs.b0 + 1));
         D.A0dinv = D.alloc<double>(ndinv);
-        D.cy = D.alloc<double>(cs.N0);
       }
       D.cstatus = D.alloc<int32_t>(1);
+      // refinement of the coarse solves: per-CTA partial norms, converged flag and ticket counter
+      D.cpart = D.alloc<double>(2 * (size_t)((cs.N0 + 7) / 8));
+      D.cflag = D.alloc<int>(2);
+      CK(cudaMemsetAsync(D.cflag, 0, 2 * sizeof(int), D.s));
+      set_smem(k_coarse_band_solve<float>, lim);
+      set_smem(k_coarse_band_solve<double>, lim);
+      if (coarse_tiles(c)) tlu_prepare(c, fp32_coarse(c));
       if (cs.N0 <= kMaxInverseN0) {
         if (fp32_coarse(c)) D.ainv = D.alloc<float>((size_t)cs.N0 * cs.N0);
         else D.ainv = D.alloc<double>((size_t)cs.N0 * cs.N0);
         D.gpart = D.alloc<double>((size_t)cs.N0 * kGemvChunks);
-        D.cpart = D.alloc<double>(2 * (size_t)((cs.N0 + 7) / 8));
-        D.cflag = D.alloc<int>(2);
-        CK(cudaMemsetAsync(D.cflag, 0, 2 * sizeof(int), D.s));
         set_smem(k_coarse_inverse<float>, lim);
         set_smem(k_coarse_inverse<double>, lim);
       }
@@ -1770,11 +1902,15 @@ int device_setup(Context& c) {
       D.dc = D.alloc<double>(cs.N0);
       D.g = D.alloc<double>(cs.N0);
       D.gt = D.alloc<double>(cs.N0);
+      D.tg = D.alloc<double>(cs.N0);  // the tangent's coarse right-hand side (never swapped)
       D.cres = D.alloc<double>(cs.N0);
       coarse_extension(c);
     }
     sync(D);
     c.device_bytes = D.bytes;
+  } catch (const DeviceTimeout& ex) {
+    c.last_error = ex.what();
+    return NLS_E_DEVICE_TIMEOUT;
   } catch (const CudaFailure& ex) {
     c.last_error = ex.what();
     return NLS_E_CUDA;
@@ -1831,6 +1967,7 @@ void device_free(Context& c) {
   cudaSetDevice(c.device);
   if (D.s) cudaStreamSynchronize(D.s);
   guess_free(c);
+  tlu_free(c);
   D.reset_graphs();
   if (D.cap) cudaStreamDestroy(D.cap);
   if (D.s2) cudaStreamSynchronize(D.s2), cudaStreamDestroy(D.s2);
@@ -1924,9 +2061,15 @@ FxInfo evaluate_Fx(Context& c, const double* u, double load, double* t_inner, do
   // - one CTA per SM (none can share an SM with the factorization): the whole chain goes on
   //   the second stream, its assembly overlapping the start of the local solves, and the local
   //   Newton grid leaves one SM to the factorization.
+  // The tiled factorization spreads every step over many CTAs: it cannot live in the corner of the
+  // machine the local grid leaves, so it runs alone on the main stream, before the local solves.
   const bool two_level = cp != NLS_COUPLING_ONE;
-  const bool spare_sm = two_level && newton_ctas_per_sm(c) == 1;
-  if (two_level) {
+  const bool serial_coarse = two_level && D.tlu != nullptr;
+  const bool spare_sm = two_level && !serial_coarse && newton_ctas_per_sm(c) == 1;
+  if (serial_coarse) {
+    tangent_coarse_assemble(c);
+    tangent_coarse_factor(c);
+  } else if (two_level) {
     if (!spare_sm) tangent_coarse_assemble(c);
     if (!D.s2) {
       int least = 0, greatest = 0;
@@ -1974,7 +2117,7 @@ FxInfo evaluate_Fx(Context& c, const double* u, double load, double* t_inner, do
     // F_x += P0 T_0(u); the coarse part of the tangent at u_0 = u - P0 T_0(u) comes from the
     // second stream
     LAUNCH(D, k_p0_apply, grid_for(c.N), 256, 0, c.N, D.p0_rowptr, D.p0_col, D.p0_val, D.c, 1.0, D.Fx, 1.0, D.Fx);
-    CK(cudaStreamWaitEvent(D.s, D.ev_coarse, 0));
+    if (!serial_coarse) CK(cudaStreamWaitEvent(D.s, D.ev_coarse, 0));
     D.coarse_fact_valid = coarse_status_ok(D);
     if (!D.coarse_fact_valid) info.pivot_failure = true;
     D.ainv_valid = D.coarse_fact_valid && D.ainv != nullptr;
@@ -1997,8 +2140,8 @@ void tangent(Context& c, const double* v, double* y) {
   }
   // w0 = P0 A0^-1 P0^T DF(u0) v
   LAUNCH(D, k_spmv_free, grid_for(c.N), 256, 0, c.N, D.g_rowptr, D.g_col, D.g_val, D.free_dof, v, D.t1);
-  p0t(c, D.t1, D.gt);
-  coarse_solve(c, D.gt, D.dc);
+  p0t(c, D.t1, D.tg);
+  coarse_solve(c, D.tg, D.dc);
   LAUNCH(D, k_p0_apply, grid_for(c.N), 256, 0, c.N, D.p0_rowptr, D.p0_col, D.p0_val, D.dc, 0.0, nullptr, 1.0, D.w0);
   if (cp == NLS_COUPLING_ADD) {
     launch_local_apply(c, v, D.w0, y);
@@ -2014,57 +2157,93 @@ struct GmresResult {
   bool converged = false;
 };
 
-// GMRES(m), zero initial guess, classical Gram-Schmidt with one re-orthogonalisation
-// (device multi-dots), Givens rotations on the host.  Solution into D.gx.
-// Replays (capturing on first use) the graph of GMRES iteration body `j`.  The graphs hold
-// device pointers and kernel arguments, so they are keyed by everything those depend on: the
-// options, the coarse-solve form (explicit inverse or band factors) and the tangent CTA size.
-template <typename F>
-void run_iteration_graph(Context& c, int j, F&& body) {
+// GMRES(m), zero initial guess, classical Gram-Schmidt with one re-orthogonalisation (device
+// multi-dots), Givens rotations and the least-squares update on the device.  Solution into D.gx.
+//
+// A cycle of up to m iterations runs without the host: with CUDA graphs it is one graph of m
+// conditional (IF) nodes in a chain, node j holding iteration j's body (tangent application,
+// two Gram-Schmidt passes, norm, scaling, Givens step); the Givens kernel of iteration j sets the
+// shared condition to "continue" or "stop" (converged, breakdown, or the cycle's iteration limit),
+// so no body after the last useful one is launched.  The host reads the cycle's state once, then
+// the least-squares solve and the update run on the device.  The cycle graph holds device pointers
+// and kernel arguments, so it is keyed by everything those depend on: the options, the
+// coarse-solve form (explicit inverse or band factors), the tangent CTA size and the scratch
+// vectors.  Without graphs (profiling, or cuda_graphs = 0) the same kernels run on the stream and
+// the host reads the state after every iteration.
+std::string cycle_graph_key(Context& c) {
   Dev& D = *c.dev;
   std::string key((const char*)&c.opt, sizeof(c.opt));
   key += D.ainv_valid ? 'i' : 'b';
-  key += std::to_string(apply_threads(c));
+  key += std::to_string(apply_threads(c)) + "," + std::to_string(D.m) + ",";
   // scratch vectors the tangent writes (some are swapped by the coarse Newton iteration)
-  for (const void* p : {(const void*)D.t1, (const void*)D.t2, (const void*)D.w0, (const void*)D.gt,
-                        (const void*)D.dc, (const void*)D.gpart, (const void*)D.cres, (const void*)D.cy,
+  for (const void* p : {(const void*)D.t1, (const void*)D.t2, (const void*)D.w0, (const void*)D.tg,
+                        (const void*)D.dc, (const void*)D.gpart, (const void*)D.cres,
                         (const void*)D.cpart, (const void*)D.cflag})
     key += std::to_string((uintptr_t)p) + ",";
-  if (key != D.graph_key || (int)D.it_exec.size() != D.m) {
+  return key;
+}
+
+// Captures (first use) and launches the cycle graph; body(j, next, use) issues iteration j, whose
+// Givens step sets `next` (the condition of node j + 1) when `use` is set.  The kernels of every
+// body are counted apart, for the launch count once the cycle's length is known.
+template <typename F>
+void run_cycle_graph(Context& c, F&& body) {
+  Dev& D = *c.dev;
+  const std::string key = cycle_graph_key(c);
+  if (key != D.graph_key || D.it_exec.empty()) {
     D.reset_graphs();
     D.graph_key = key;
-    D.it_exec.assign(D.m, nullptr);
-    D.it_launches.assign(D.m, 0);
-  }
-  if (!D.it_exec[j]) {
     if (!D.cap) CK(cudaStreamCreateWithFlags(&D.cap, cudaStreamNonBlocking));
+    cudaGraph_t G = nullptr;
+    CK(cudaGraphCreate(&G, 0));
     const cudaStream_t saved = D.s;
     const int64_t l0 = D.launches;
-    cudaGraph_t g = nullptr;
-    CK(cudaStreamBeginCapture(D.cap, cudaStreamCaptureModeThreadLocal));
-    D.s = D.cap;
     try {
-      body();
+      // one condition per node (a handle belongs to one conditional node): node 0 runs by default,
+      // node j + 1 only when iteration j's Givens step sets its handle; all are reset at launch
+      std::vector<cudaGraphConditionalHandle> h(D.m);
+      for (int j = 0; j < D.m; ++j)
+        CK(cudaGraphConditionalHandleCreate(&h[j], G, j == 0 ? 1u : 0u, cudaGraphCondAssignDefault));
+      cudaGraphNode_t prev = nullptr;
+      D.it_launches.assign(D.m, 0);
+      for (int j = 0; j < D.m; ++j) {
+        cudaGraphNodeParams p = {};
+        p.type = cudaGraphNodeTypeConditional;
+        p.conditional.handle = h[j];
+        p.conditional.type = cudaGraphCondTypeIf;
+        p.conditional.size = 1;
+        cudaGraphNode_t node = nullptr;
+        CK(cudaGraphAddNode(&node, G, prev ? &prev : nullptr, nullptr, prev ? 1 : 0, &p));
+        cudaGraph_t bg = p.conditional.phGraph_out[0];
+        const int64_t lj = D.launches;
+        CK(cudaStreamBeginCaptureToGraph(D.cap, bg, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+        D.s = D.cap;
+        try {
+          body(j, j + 1 < D.m ? h[j + 1] : cudaGraphConditionalHandle{}, j + 1 < D.m ? 1 : 0);
+        } catch (...) {
+          cudaGraph_t tmp = nullptr;
+          cudaStreamEndCapture(D.cap, &tmp);
+          throw;
+        }
+        D.s = saved;
+        CK(cudaStreamEndCapture(D.cap, &bg));
+        D.it_launches[j] = D.launches - lj;
+        prev = node;
+      }
+      cudaGraphExec_t ex = nullptr;
+      CK(cudaGraphInstantiate(&ex, G, 0));
+      D.it_exec.assign(1, ex);
     } catch (...) {
-      cudaStreamEndCapture(D.cap, &g);
-      if (g) cudaGraphDestroy(g);
       D.s = saved;
       D.launches = l0;
+      cudaGraphDestroy(G);
+      D.reset_graphs();
       throw;
     }
-    const cudaError_t e = cudaStreamEndCapture(D.cap, &g);
-    D.s = saved;
-    CK(e);
-    cudaGraphExec_t ex = nullptr;
-    const cudaError_t ei = cudaGraphInstantiate(&ex, g, 0);
-    cudaGraphDestroy(g);
-    CK(ei);
-    D.it_exec[j] = ex;
-    D.it_launches[j] = D.launches - l0;
+    cudaGraphDestroy(G);
     D.launches = l0;
   }
-  CK(cudaGraphLaunch(D.it_exec[j], D.s));
-  D.launches += D.it_launches[j];
+  CK(cudaGraphLaunch(D.it_exec[0], D.s));
 }
 
 GmresResult gmres(Context& c, const double* b) {
@@ -2083,69 +2262,48 @@ GmresResult gmres(Context& c, const double* b) {
   double* r = D.t2;
   CK(cudaMemcpyAsync(r, b, sizeof(double) * N, cudaMemcpyDeviceToDevice, D.s));
   double rn = bn;
-  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), gv(m + 1), y(m);
   const double target = c.opt.gmres_rtol * bn;
+  // iteration j of a cycle: w = DF_x v_j, CGS2 against v_0 .. v_j, h_{j+1,j} = ||w||, v_{j+1} =
+  // w / h_{j+1,j}, Givens step (sets the graph condition when `use_handle`)
+  auto body = [&](int j, cudaGraphConditionalHandle h, int use_handle) {
+    double* vj = D.V + (size_t)j * N;
+    double* w = D.V + (size_t)(j + 1) * N;
+    tangent(c, vj, w);
+    for (int pass = 0; pass < 2; ++pass) {
+      LAUNCH(D, k_multidot_partial, kVecBlocks, kVecThreads, 0, N, j + 1, D.V, N, w, D.partial);
+      LAUNCH(D, k_partial_final, std::min(j + 1, 64), 256, 0, j + 1, D.partial, D.scal + pass * (kMaxGmresVecs / 2));
+      LAUNCH(D, k_multiaxpy, grid_for(N), 256, 0, N, j + 1, D.V, N, D.scal + pass * (kMaxGmresVecs / 2), -1.0, w);
+    }
+    LAUNCH(D, k_multidot_partial, kVecBlocks, kVecThreads, 0, N, 1, w, (int64_t)0, w, D.partial);
+    LAUNCH(D, k_partial_final, 1, 256, 0, 1, D.partial, D.scal + kMaxGmresVecs);
+    LAUNCH(D, k_sqrt_inplace, 1, 1, 0, D.scal + kMaxGmresVecs);
+    LAUNCH(D, k_scale_inv, grid_for(N), 256, 0, N, w, D.scal + kMaxGmresVecs, w);
+    LAUNCH(D, k_gmres_givens, 1, 32, 0, j, m, D.scal, D.gR, D.gcs, D.gsn, D.gg, D.gst, h, use_handle);
+  };
+  GmresState st;
   while (R.its < c.opt.gmres_maxit) {
-    // V0 = r / rn
     LAUNCH(D, k_axpby, grid_for(N), 256, 0, N, 1.0 / rn, r, 0.0, nullptr, D.V);
-    std::fill(H.begin(), H.end(), 0.0);
-    std::fill(gv.begin(), gv.end(), 0.0);
-    gv[0] = rn;
-    int j = 0;
-    bool done = false;
-    while (j < m && R.its < c.opt.gmres_maxit) {
-      double* vj = D.V + (size_t)j * N;
-      double* w = D.V + (size_t)(j + 1) * N;
-      auto body = [&]() {
-        tangent(c, vj, w);
-        // CGS2
-        for (int pass = 0; pass < 2; ++pass) {
-          LAUNCH(D, k_multidot_partial, kVecBlocks, kVecThreads, 0, N, j + 1, D.V, N, w, D.partial);
-          LAUNCH(D, k_partial_final, std::min(j + 1, 64), 256, 0, j + 1, D.partial,
-                 D.scal + pass * (kMaxGmresVecs / 2));
-          LAUNCH(D, k_multiaxpy, grid_for(N), 256, 0, N, j + 1, D.V, N, D.scal + pass * (kMaxGmresVecs / 2), -1.0, w);
-        }
-        LAUNCH(D, k_multidot_partial, kVecBlocks, kVecThreads, 0, N, 1, w, (int64_t)0, w, D.partial);
-        LAUNCH(D, k_partial_final, 1, 256, 0, 1, D.partial, D.scal + kMaxGmresVecs);
-        LAUNCH(D, k_sqrt_inplace, 1, 1, 0, D.scal + kMaxGmresVecs);
-        CK(cudaMemcpyAsync(D.h_scal, D.scal, sizeof(double) * (kMaxGmresVecs + 1), cudaMemcpyDeviceToHost, D.s));
-        LAUNCH(D, k_scale_inv, grid_for(N), 256, 0, N, w, D.scal + kMaxGmresVecs, w);
-      };
-      if (graphs) run_iteration_graph(c, j, body);
-      else body();
+    const int limit = std::min(m, c.opt.gmres_maxit - R.its);
+    LAUNCH(D, k_gmres_start, 1, 32, 0, m, rn, target, limit, D.gg, D.gst);
+    if (graphs) {
+      run_cycle_graph(c, body);
+      CK(cudaMemcpyAsync(&st, D.gst, sizeof(st), cudaMemcpyDeviceToHost, D.s));
       sync(D);
-      for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = D.h_scal[i] + D.h_scal[kMaxGmresVecs / 2 + i];
-      const double hn = D.h_scal[kMaxGmresVecs];
-      H[(size_t)(j + 1) * m + j] = hn;
-      for (int i = 0; i < j; ++i) {
-        const double t = cs[i] * H[(size_t)i * m + j] + sn[i] * H[(size_t)(i + 1) * m + j];
-        H[(size_t)(i + 1) * m + j] = -sn[i] * H[(size_t)i * m + j] + cs[i] * H[(size_t)(i + 1) * m + j];
-        H[(size_t)i * m + j] = t;
-      }
-      const double d = std::hypot(H[(size_t)j * m + j], H[(size_t)(j + 1) * m + j]);
-      cs[j] = H[(size_t)j * m + j] / d;
-      sn[j] = H[(size_t)(j + 1) * m + j] / d;
-      H[(size_t)j * m + j] = d;
-      H[(size_t)(j + 1) * m + j] = 0.0;
-      gv[j + 1] = -sn[j] * gv[j];
-      gv[j] = cs[j] * gv[j];
-      ++j;
-      ++R.its;
-      if (!std::isfinite(hn) || std::abs(gv[j]) <= target || hn == 0.0) {
-        done = true;
-        break;
+      for (int j = 0; j < st.j; ++j) D.launches += D.it_launches[j];
+    } else {
+      for (int j = 0; j < limit; ++j) {
+        body(j, cudaGraphConditionalHandle{}, 0);
+        CK(cudaMemcpyAsync(&st, D.gst, sizeof(st), cudaMemcpyDeviceToHost, D.s));
+        sync(D);
+        if (st.done || st.j >= limit) break;
       }
     }
-    for (int i = j - 1; i >= 0; --i) {
-      double acc = gv[i];
-      for (int k = i + 1; k < j; ++k) acc -= H[(size_t)i * m + k] * y[k];
-      y[i] = acc / H[(size_t)i * m + i];
-    }
-    CK(cudaMemcpyAsync(D.coef, y.data(), sizeof(double) * j, cudaMemcpyHostToDevice, D.s));
-    LAUNCH(D, k_multiaxpy, grid_for(N), 256, 0, N, j, D.V, N, D.coef, 1.0, D.gx);
-    sync(D);
-    R.relres = std::abs(gv[j]) / bn;
-    if (done && std::abs(gv[j]) <= target) {
+    // y = R^-1 g (back substitution) and x += V y, on the device
+    LAUNCH(D, k_gmres_lsq, 1, 32, 0, m, D.gR, D.gg, D.gst, D.coef);
+    LAUNCH(D, k_multiaxpy_dev, grid_for(N), 256, 0, N, D.gst, D.V, N, D.coef, 1.0, D.gx);
+    R.its += st.j;
+    R.relres = st.res / bn;
+    if (st.done && st.res <= target) {
       R.converged = true;
       break;
     }
@@ -2158,7 +2316,7 @@ GmresResult gmres(Context& c, const double* b) {
       R.converged = true;
       break;
     }
-    if (done) break;
+    if (st.done) break;
   }
   return R;
 }
@@ -2302,6 +2460,9 @@ int solve(Context& c, double* u_user, int u_dev, nls_report* rep) {
     rp.time_gmres_s = t_gmres;
     rp.time_other_s = std::max(0.0, wall - t_inner - t_coarse - t_gmres);
     D.prof_flush();
+  } catch (const DeviceTimeout& ex) {
+    c.last_error = ex.what();
+    status = NLS_E_DEVICE_TIMEOUT;
   } catch (const CudaFailure& ex) {
     c.last_error = ex.what();
     status = NLS_E_CUDA;
@@ -2340,6 +2501,9 @@ int eval_Fx(Context& c, const double* u, double* Fx, int is_dev, double load, in
     if (st) CK(cudaMemcpyAsync(st, D.ov.status, sizeof(int32_t) * c.ov.count, cudaMemcpyDeviceToHost, D.s));
     sync(D);
     if (fi.pivot_failure) return NLS_E_PIVOT;
+  } catch (const DeviceTimeout& ex) {
+    c.last_error = ex.what();
+    return NLS_E_DEVICE_TIMEOUT;
   } catch (const std::exception& ex) {
     c.last_error = ex.what();
     return NLS_E_CUDA;
@@ -2448,6 +2612,135 @@ int get_coarse_basis(const Context& c, double* P0) {
     return NLS_E_CUDA;
   }
   return NLS_OK;
+}
+
+int guess_smooth(Context& c, const double* x, double load, const double* w, double* out) {
+  if (!c.dev || !c.dev->guess) {
+    c.last_error = "the learned-guess hooks need an attached network";
+    return NLS_E_ARG;
+  }
+  Dev& D = *c.dev;
+  try {
+    const GuessProposal g = guess_smoothing(c);
+    CK(cudaMemcpyAsync(D.x, x, sizeof(double) * c.N, cudaMemcpyHostToDevice, D.s));
+    CK(cudaMemcpyAsync(D.ov.w, w, sizeof(double) * c.ov.total_n, cudaMemcpyHostToDevice, D.s));
+    LocalArgs A = make_args(c, c.ov, D.ov);
+    A.x = D.x;
+    A.load = load;
+    A.guess = D.ov.w;
+    A.guess_diag = g.diag;
+    A.guess_sweeps = g.sweeps;
+    A.guess_omega = g.omega;
+    A.out = D.ov.work;  // concatenated local vectors
+    const size_t sm = sizeof(double) * ((size_t)c.ov.max_nt + c.ov.max_n) + 16;
+    if (c.law == NLS_LAW_DIFFUSION) LAUNCH(D, k_guess_smooth<NLS_LAW_DIFFUSION>, c.ov.count, 128, sm, A);
+    else LAUNCH(D, k_guess_smooth<NLS_LAW_NEOHOOKE>, c.ov.count, 128, sm, A);
+    CK(cudaMemcpyAsync(out, D.ov.work, sizeof(double) * c.ov.total_n, cudaMemcpyDeviceToHost, D.s));
+    sync(D);
+  } catch (const std::exception& ex) {
+    c.last_error = ex.what();
+    return NLS_E_CUDA;
+  }
+  return NLS_OK;
+}
+
+int get_coarse_matrix(const Context& c, double* A0) {
+  if (c.coarse_kind != NLS_COARSE_RGDSW || !c.dev || !c.dev->A0) return NLS_E_ARG;
+  Dev& D = *c.dev;
+  try {
+    CK(cudaMemcpyAsync(A0, D.A0, sizeof(double) * (size_t)c.cs.N0 * (2 * c.cs.b0 + 1), cudaMemcpyDeviceToHost, D.s));
+    CK(cudaStreamSynchronize(D.s));
+  } catch (const std::exception&) {
+    return NLS_E_CUDA;
+  }
+  return NLS_OK;
+}
+
+// The coarse factorization and solve on a given band matrix (parity hook and utility): a context
+// with only the coarse problem, run on the legacy default stream and freed on return.
+int band_solve(int device, int32_t n, int32_t b, const double* band, const double* rhs, double* x, int32_t precision,
+               int32_t method, double* factors_out) {
+  if (n < 1 || b < 0 || !band || !rhs || !x) return NLS_E_ARG;
+  if ((precision != NLS_PREC_FP64 && precision != NLS_PREC_FP32_IR) || method < NLS_COARSE_FACTOR_AUTO ||
+      method > NLS_COARSE_FACTOR_TILES)
+    return NLS_E_ARG;
+  Context c;
+  c.device = device;
+  c.stream = nullptr;
+  nls_options_default(&c.opt);
+  c.opt.coarse_precision = precision;
+  c.opt.coarse_factor = method;
+  c.coarse_kind = NLS_COARSE_RGDSW;
+  c.cs.N0 = n;
+  c.cs.b0 = b;
+  int status = NLS_OK;
+  try {
+    if (b > kMaxSolveB0 || (!coarse_tiles(c) && b > kMaxBandB0)) return NLS_E_UNSUPPORTED;
+    CK(cudaSetDevice(device));
+    c.dev = new Dev();
+    Dev& D = *c.dev;
+    D.s = nullptr;
+    cudaDeviceProp prop;
+    CK(cudaGetDeviceProperties(&prop, device));
+    D.nsm = prop.multiProcessorCount;
+    D.smem_optin = prop.sharedMemPerBlockOptin;
+    const bool f32 = fp32_coarse(c);
+    const size_t fs = f32 ? sizeof(float) : sizeof(double);
+    if (fs * (size_t)n > D.smem_optin || (!coarse_tiles(c) && coarse_factor_smem(c, f32) > D.smem_optin)) {
+      device_free(c);
+      return NLS_E_UNSUPPORTED;  // the one-CTA window or the solve vector exceeds shared memory
+    }
+    const size_t nw = (size_t)n * (2 * b + 1);
+    D.A0 = D.alloc<double>(nw);
+    CK(cudaMemcpyAsync(D.A0, band, sizeof(double) * nw, cudaMemcpyHostToDevice, D.s));
+    const size_t ndinv = (size_t)packed_solve_entries(n, b);
+    if (f32) {
+      D.A0f = D.alloc<float>(nw);
+      D.A0dinv = D.alloc<float>(ndinv);
+    } else {
+      D.A0f = D.alloc<double>(nw);
+      D.A0dinv = D.alloc<double>(ndinv);
+    }
+    D.cstatus = D.alloc<int32_t>(1);
+    D.cpart = D.alloc<double>(2 * (size_t)((n + 7) / 8));
+    D.cflag = D.alloc<int>(2);
+    CK(cudaMemsetAsync(D.cflag, 0, 2 * sizeof(int), D.s));
+    D.cres = D.alloc<double>(n);
+    D.g = D.alloc<double>(n);
+    D.dc = D.alloc<double>(n);
+    CK(cudaMemcpyAsync(D.g, rhs, sizeof(double) * n, cudaMemcpyHostToDevice, D.s));
+    set_smem(k_coarse_factor<float>, D.smem_optin);
+    set_smem(k_coarse_factor<double>, D.smem_optin);
+    set_smem(k_coarse_band_solve<float>, D.smem_optin);
+    set_smem(k_coarse_band_solve<double>, D.smem_optin);
+    if (coarse_tiles(c)) tlu_prepare(c, f32);
+    coarse_factor_launch(c);
+    if (!coarse_status_ok(D)) {
+      status = NLS_E_PIVOT;
+    } else {
+      coarse_solve(c, D.g, D.dc);
+      CK(cudaMemcpyAsync(x, D.dc, sizeof(double) * n, cudaMemcpyDeviceToHost, D.s));
+    }
+    if (factors_out) {
+      std::vector<float> f(f32 ? nw : 0);
+      if (f32) CK(cudaMemcpyAsync(f.data(), D.A0f, sizeof(float) * nw, cudaMemcpyDeviceToHost, D.s));
+      else CK(cudaMemcpyAsync(factors_out, D.A0f, sizeof(double) * nw, cudaMemcpyDeviceToHost, D.s));
+      sync(D);
+      if (f32)
+        for (size_t k = 0; k < nw; ++k) factors_out[k] = (double)f[k];
+    }
+    sync(D);
+  } catch (const DeviceTimeout&) {
+    status = NLS_E_DEVICE_TIMEOUT;
+  } catch (const CudaFailure&) {
+    status = NLS_E_CUDA;
+  } catch (const std::bad_alloc&) {
+    status = NLS_E_NOMEM;
+  } catch (const std::exception&) {
+    status = NLS_E_ARG;
+  }
+  device_free(c);
+  return status;
 }
 
 // ------------------------------------------------------------------------------------------

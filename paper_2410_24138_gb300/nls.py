@@ -18,6 +18,7 @@ from .inputs import LAMBDA_PLANE_STRESS, LAMBDA_PRINTED, LAW_DIFFUSION, LAW_NEOH
 P1_TRI, Q1_QUAD = 1, 2
 COUPLING = {"one": 0, "add": 1, "hybrid": 2}
 PREC_FP64, PREC_FP32_IR = 0, 1
+COARSE_FACTOR_AUTO, COARSE_FACTOR_BAND, COARSE_FACTOR_TILES = 0, 1, 2
 COARSE_NONE, COARSE_RGDSW = 0, 1
 
 STATUS = {0: "ok", -1: "E_ARG", -2: "E_CUDA", -3: "E_NOMEM", -4: "E_UNSUPPORTED", -5: "E_LOCAL_NEWTON",
@@ -36,7 +37,7 @@ class Options(ctypes.Structure):
                 ("profile_kernels", ctypes.c_int32), ("cuda_graphs", ctypes.c_int32),
                 ("coarse_reuse", ctypes.c_int32), ("local_reuse", ctypes.c_int32), ("autotune", ctypes.c_int32),
                 ("l2_prefetch", ctypes.c_int32), ("outer_backtrack", ctypes.c_int32),
-                ("coarse_rebuild", ctypes.c_int32)]
+                ("coarse_rebuild", ctypes.c_int32), ("coarse_factor", ctypes.c_int32)]
 
 
 class Report(ctypes.Structure):
@@ -95,7 +96,8 @@ EXPORTS = ["nls_options_default", "nls_create", "nls_destroy", "nls_strerror", "
            "nls_guess_attach", "nls_guess_train", "nls_guess_pairs", "nls_guess_get_params", "nls_guess_set_params",
            "nls_guess_get_normalisation", "nls_guess_set_normalisation", "nls_guess_gradient", "nls_guess_forward",
            "nls_guess_counts", "nls_get_tuning", "nls_guess_set_smoothing", "nls_set_coefficients",
-           "nls_set_volume_force", "nls_set_lambda_mode"]
+           "nls_set_volume_force", "nls_set_lambda_mode", "nls_get_coarse_matrix", "nls_band_solve",
+           "nls_guess_features", "nls_guess_decode", "nls_guess_smooth"]
 
 _LIB = None
 _P = ctypes.c_void_p
@@ -140,6 +142,11 @@ def load() -> ctypes.CDLL:
         "nls_get_owners": (ctypes.c_int, [_P, _P]),
         "nls_get_coarse_nodes": (ctypes.c_int, [_P, _P]),
         "nls_get_coarse_basis": (ctypes.c_int, [_P, _P]),
+        "nls_get_coarse_matrix": (ctypes.c_int, [_P, _P]),
+        "nls_guess_features": (ctypes.c_int, [_P, _P, dbl, _P]),
+        "nls_guess_decode": (ctypes.c_int, [_P, _P, dbl, _P, _P]),
+        "nls_guess_smooth": (ctypes.c_int, [_P, _P, dbl, _P, _P]),
+        "nls_band_solve": (ctypes.c_int, [ctypes.c_int, i32, i32, _P, _P, _P, i32, i32, _P]),
         "nls_eval_F": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, dbl]),
         "nls_eval_Fx": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, dbl, _P, _P]),
         "nls_apply_tangent": (ctypes.c_int, [_P, _P, _P, ctypes.c_int]),
@@ -326,6 +333,13 @@ class Solver:
         out = np.zeros((s.n_coarse_dofs, s.n_dofs), dtype=np.float64)  # column-major N x N0
         self._check(self.lib.nls_get_coarse_basis(self.h, _ptr(out)), "nls_get_coarse_basis")
         return out.T
+
+    def coarse_matrix(self) -> np.ndarray:
+        """A_0 of the last tangent phase in band storage [n_coarse_dofs, 2 b0 + 1] (FP64)."""
+        s = self.sizes()
+        out = np.zeros((s.n_coarse_dofs, 2 * s.coarse_half_band + 1), dtype=np.float64)
+        self._check(self.lib.nls_get_coarse_matrix(self.h, _ptr(out)), "nls_get_coarse_matrix")
+        return out
 
     def eval_F(self, u, load: float = 1.0):
         F = np.zeros_like(u) if isinstance(u, np.ndarray) else u.new_zeros(u.shape)
@@ -516,10 +530,52 @@ def set_guess_smoothing(solver: "Solver", sweeps: int, omega: float = 0.8):
     solver._check(solver.lib.nls_guess_set_smoothing(solver.h, sweeps, omega), "nls_guess_set_smoothing")
 
 
+def guess_features(solver: "Solver", x: np.ndarray, load: float = 1.0) -> np.ndarray:
+    """Raw inputs [n_sub, 391] of every subdomain at x (test hook; needs an attached network)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    out = np.zeros((solver.n_sub, GUESS_FEATURES), dtype=np.float32)
+    solver._check(solver.lib.nls_guess_features(solver.h, _ptr(x), load, _ptr(out)), "nls_guess_features")
+    return out
+
+
+def guess_decode(solver: "Solver", x: np.ndarray, Y: np.ndarray, load: float = 1.0) -> np.ndarray:
+    """Proposal (concatenated local unknowns) decoded from network outputs Y [n_sub, 1024] at x."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    Y = np.ascontiguousarray(Y, dtype=np.float32)
+    out = np.zeros(solver.sizes().total_local_dofs)
+    solver._check(solver.lib.nls_guess_decode(solver.h, _ptr(x), load, _ptr(Y), _ptr(out)), "nls_guess_decode")
+    return out
+
+
+def guess_smooth(solver: "Solver", x: np.ndarray, w: np.ndarray, load: float = 1.0) -> np.ndarray:
+    """The smoothing of given starts w (concatenated local unknowns) at x."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    out = np.zeros_like(w)
+    solver._check(solver.lib.nls_guess_smooth(solver.h, _ptr(x), load, _ptr(w), _ptr(out)), "nls_guess_smooth")
+    return out
+
+
 def guess_counts(solver: "Solver"):
     p, a = ctypes.c_int64(), ctypes.c_int64()
     solver._check(solver.lib.nls_guess_counts(solver.h, ctypes.byref(p), ctypes.byref(a)), "nls_guess_counts")
     return p.value, a.value
+
+
+def band_solve(band: np.ndarray, rhs: np.ndarray, precision: int = PREC_FP32_IR, method: int = COARSE_FACTOR_TILES,
+               device: int = 0, want_factors: bool = False):
+    """Factor the band matrix band [n, 2b + 1] with the coarse factorization and solve band x = rhs
+    (include/nls.h nls_band_solve); returns x, or (x, factors in the same band layout)."""
+    lib = load()
+    band = np.ascontiguousarray(band, dtype=np.float64)
+    rhs = np.ascontiguousarray(rhs, dtype=np.float64)
+    n, w = band.shape
+    x = np.zeros(n)
+    fac = np.zeros_like(band) if want_factors else None
+    st = lib.nls_band_solve(device, n, (w - 1) // 2, _ptr(band), _ptr(rhs), _ptr(x), precision, method, _ptr(fac))
+    if st < 0:
+        raise NLSError(st, "nls_band_solve", "")
+    return (x, fac) if want_factors else x
 
 
 def make_solver(p: Problem, coupling: str = "hybrid", precision: str = "fp32", coarse: Optional[bool] = None,

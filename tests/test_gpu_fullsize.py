@@ -12,15 +12,15 @@ F_x, 1e-7 for the tangent (FP32 factors refined to 1e-10), and local iteration c
 one.
 
 The 512 x 512 Neo-Hooke workload (Eq. 2, Q1, 0.53M dofs, 256 uneven subdomains, overlap 2), and
-the local path of the 2048 x 2048 one (8.4M dofs, 4096 subdomains; its coarse problem is not
-built), are checked the same way on five subdomains, at the first load step's traction (load factor 0.2) and
-a smooth bending state u_y = -0.02 x^2 with a seeded perturbation of 1e-5 (no element near
-inversion).  At h = 1/512 the local residuals cannot be driven to 1e-14 (the line search stalls at
-the rounding floor of the stiffness, E = 210), so both sides stop at 1e-12 relative / 1e-13
-absolute; Newton's last step takes both far below that.  Both forms run: F_x within 1e-9 in both;
-the tangent within 1e-9 in the FP64 form, and in the FP32 form, whose local Jacobians come from FP32
-element tangents, within 8 u kappa_2(R_i J P_i) (u = 2^-24), the first-order effect of a perturbation of
-a few unit roundoffs per entry on the local solve (kappa from the oracle's local Jacobian by Lanczos).
+the local path of the 2048 x 2048 one (8.4M dofs, 4096 subdomains), are checked the same way on
+five subdomains, at the first load step's traction (load factor 0.2) and a smooth bending state
+u_y = -0.02 x^2 with a seeded perturbation of 1e-5 (no element near inversion).  At h = 1/512 the
+local residuals cannot be driven to 1e-14 (the line search stalls at the rounding floor of the
+stiffness, E = 210), so both sides stop at 1e-12 relative / 1e-13 absolute; Newton's last step
+takes both far below that.  Both forms run: F_x within 1e-9 in both; the tangent within 1e-9 in the
+FP64 form and 1e-7 in the FP32 form, whose FP32 factors are refined to 1e-10 against the local
+Jacobian assembled from FP64 element tangents -- the same bounds as for Eq. 1.  Every comparison
+is also made entry by entry in the max norm, at ten times the l2 bound.
 """
 import numpy as np
 import pytest
@@ -60,18 +60,10 @@ def test_full_size_sampled_local_corrections_and_tangent(nls, workload):
     for k, (lp, res) in enumerate(zip(sw.locals, sto["local"])):
         owned = lp.sub.dofs[lp.sub.owned]
         assert np.linalg.norm(Fx[owned] - Fo[owned]) <= 1e-9 * np.linalg.norm(Fo[owned])
+        assert np.abs(Fx[owned] - Fo[owned]).max() <= 1e-8 * np.abs(Fo[owned]).max()
         assert np.linalg.norm(y[owned] - yo[owned]) <= 1e-7 * np.linalg.norm(yo[owned])
+        assert np.abs(y[owned] - yo[owned]).max() <= 1e-6 * np.abs(yo[owned]).max()
         assert abs(int(its[pick[k]]) - res.its) <= 1
-
-
-
-def _local_condition(lp, res, points):
-    """2-norm condition number of the oracle's local Jacobian R_i J(w_i) P_i (symmetric for Eq. 2)."""
-    import scipy.sparse.linalg as spla
-    J = lp.jacobian_rows(lp.table(points, res.w))[:, lp.sub.tpos].tocsc()
-    lmax = spla.eigsh(J, k=1, which="LM", return_eigenvectors=False)[0]
-    lmin = spla.eigsh(J, k=1, sigma=0, which="LM", return_eigenvectors=False)[0]
-    return abs(lmax / lmin)
 
 
 @pytest.mark.parametrize("workload,precision", [("c3", "fp64"), ("c3", "fp32"), ("c5", "fp32")])
@@ -98,10 +90,8 @@ def test_full_size_neohooke_sampled_local_corrections_and_tangent(nls, workload,
         assert res.status == 0
         owned = lp.sub.dofs[lp.sub.owned]
         assert np.linalg.norm(Fx[owned] - Fo[owned]) <= 1e-9 * np.linalg.norm(Fo[owned])
+        assert np.abs(Fx[owned] - Fo[owned]).max() <= 1e-8 * np.abs(Fo[owned]).max()
         assert abs(int(its[pick[k]]) - res.its) <= 1
-        # FP64 form: 1e-9.  FP32 form: the local Jacobian is assembled from FP32 element tangents
-        # (each entry a short sum of products at four Gauss points, a relative rounding error of a
-        # few u = 2^-24; 8 u taken), and to first order the local solve amplifies a relative
-        # perturbation of the operator by kappa_2(R_i J P_i) (400 - 2300 for these subdomains)
-        tol = 1e-9 if precision == "fp64" else 8 * 2.0 ** -24 * _local_condition(lp, res, sto["points"])
+        tol = 1e-9 if precision == "fp64" else 1e-7
         assert np.linalg.norm(y[owned] - yo[owned]) <= tol * np.linalg.norm(yo[owned])
+        assert np.abs(y[owned] - yo[owned]).max() <= 10 * tol * np.abs(yo[owned]).max()

@@ -144,3 +144,57 @@ def test_trained_guess_gains_local_newton_steps(nls):
     net1 = _train(nls, range(1, 25), 1.0)
     plain1, guess1, _ = _steps(nls, net1, (1001, 1002), 1.0)
     assert guess1 <= plain1
+
+
+@pytest.fixture(scope="module")
+def guess_case(nls):
+    """A 64 x 64 log-normal-k diffusion problem (held-out field seed), 16 uneven subdomains, with
+    an attached network (the maps do not depend on its weights)."""
+    p = I.diffusion_c4(1001, n=64, per_side=4)
+    s = nls.make_solver(p, coupling="one", precision="fp32")
+    net = nls.GuessNet(h1=32, h2=32, seed=2)
+    nls.attach_guess(s, net, nls.GUESS_USE)
+    nls.set_guess_smoothing(s, 6, 0.8)
+    rng = np.random.default_rng(11)
+    x = np.where(fem.free_mask(p), 0.2 * rng.random(p.n_nodes), 0.0)
+    return p, s, net, x
+
+
+def test_feature_map_matches_oracle(nls, guess_case):
+    """Every one of the 391 raw inputs of every subdomain: FP32 storage of FP64 values whose
+    interpolation weights are themselves FP32, so within 1e-6 relative (+1e-7 of the field)."""
+    from oracle import decomposition as dec, guess as G
+    p, s, net, x = guess_case
+    F = nls.guess_features(s, x, 0.7)
+    subs, _ = dec.decompose(p)
+    for i, sub in enumerate(subs):
+        ref = G.features(p, sub.vnodes, x, 0.7)
+        np.testing.assert_allclose(F[i], ref, rtol=1e-6, atol=1e-7 * np.abs(x).max())
+
+
+def test_decode_matches_oracle(nls, guess_case):
+    """Coons patch of the side samples plus the bilinear 32 x 32 correction at every local unknown,
+    in FP64 on both sides from the same FP32 network outputs: 1e-12 of the largest value."""
+    from oracle import decomposition as dec, guess as G
+    p, s, net, x = guess_case
+    Y = np.random.default_rng(3).standard_normal((p.n_sub, nls.GUESS_OUTPUTS)).astype(np.float32)
+    tscale = net.normalisation()[2]
+    got = nls.guess_decode(s, x, Y, 0.7)
+    subs, _ = dec.decompose(p)
+    ref = np.concatenate([G.decode(p, sub.vnodes, x, Y[i].astype(np.float64), tscale) for i, sub in enumerate(subs)])
+    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+
+
+def test_smoothing_matches_oracle(nls, guess_case):
+    """Six damped Jacobi sweeps (omega 0.8) of the same starts on both sides, in FP64: only the
+    summation order of the local residuals differs (1e-12 of the largest value)."""
+    from oracle import guess as G, schwarz as S
+    p, s, net, x = guess_case
+    sw = S.Schwarz(p, S.Options(coupling=S.ONE_LEVEL), with_coarse=False)
+    rng = np.random.default_rng(5)
+    starts = [x[lp.sub.dofs] + 0.05 * rng.standard_normal(lp.sub.n) for lp in sw.locals]
+    got = nls.guess_smooth(s, x, np.concatenate(starts), 0.7)
+    ref = np.concatenate([G.smooth(lp, x, w0, 0.7, 6, 0.8, G.jacobi_diagonal(p, lp.sub.vnodes))
+                          for lp, w0 in zip(sw.locals, starts)])
+    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+    assert np.abs(got - np.concatenate(starts)).max() > 1e-3  # the sweeps did change the starts
