@@ -349,60 +349,81 @@ int nls_get_local_states(nls_ctx* ctx, double* w_out, int is_device);
 
 /* ---- learned initial guess (not in the paper) ------------------------------------------
  * A small fully connected network proposes the starting point of every local Newton solve
- * (Eq. 4).  Inputs (391 values per subdomain, structured P1 meshes of Eq. 1 only): the local
- * Dirichlet data on the ring of nodes around the box of local unknowns, sampled at 33 points
- * on each of its four sides, log k sampled on 16 x 16 points of the box, f, and the box width
- * and height.  Output: a 32 x 32 correction, on a canonical grid of the box, to the Coons
- * (bilinear transfinite) patch of the side data; the guess at a node is the patch plus the
- * bilinearly interpolated correction.  Layers: 391 -> h1 -> h2 -> 1024, tanh-form GELU.
- * Training: BF16 operands on the tensor cores with FP32 accumulation, FP32 master weights,
- * Adam, loss 1/(2B) sum ||y - t||^2 on normalised inputs and targets.  Inference: FP32.
+ * (Eq. 4), on structured meshes of the unit square (n x n cells, nodes numbered row by row).
+ * Box of a subdomain: the grid rectangle one node beyond its local unknowns, clamped to the mesh
+ * (for Eq. 1 the ring of Dirichlet data around the unknowns; a side on a Neumann edge of Eq. 2 is
+ * that edge).  Two kinds of network:
+ * - scalar (Eq. 1, P1 triangles): 391 inputs per subdomain -- x on the four sides of the box,
+ *   sampled at 33 points each, log k on 16 x 16 points of the box, the load factor times f, and
+ *   the box width and height; 1024 outputs.
+ * - displacement (Eq. 2, Q1 quadrilaterals): 267 inputs -- the 4 x 33 side samples of the first
+ *   and of the second displacement component, the load factor, the box width and height; 2048
+ *   outputs (1024 per component).
+ * Each 1024 outputs are a 32 x 32 correction, on a canonical grid of the box, to the Coons
+ * (bilinear transfinite) patch of one component's side data; the guess at a node is the patch
+ * plus the bilinearly interpolated correction.  Layers: n_in -> h1 -> h2 -> n_out, tanh-form
+ * GELU.  Training: BF16 operands on the tensor cores with FP32 accumulation, FP32 master
+ * weights, Adam, loss 1/(2B) sum ||y - t||^2 on normalised inputs and targets.  Inference: FP32.
  * Before the test, `sweeps` damped Jacobi steps w <- w - omega r(w) / d(w) on the local
  * problem remove the pointwise (high-frequency) part of the network's error, which otherwise
- * dominates the residual: d_a(w) = (1 + w_a^2) sum_{e owns a} k_e |grad phi_a|^2 |e|, the
- * diagonal of the Jacobian's leading term (defaults: 6 sweeps, omega = 0.8, the damping that
- * minimises the smoothing factor of Jacobi on the five-point stencil P1 yields here).
+ * dominates the residual.  Eq. 1: d_a(w) = (1 + w_a^2) sum_{e owns a} k_e |grad phi_a|^2 |e|,
+ * the diagonal of the Jacobian's leading term; Eq. 2: d the diagonal of the linear-elastic
+ * stiffness (the tangent at zero displacement).  Defaults: 6 sweeps, omega = 0.8, the damping
+ * that minimises the smoothing factor of Jacobi on the five-point stencil P1 yields here.
  * A guess is used only where its (smoothed) local residual is smaller than that of R_i x (the
  * start the method uses otherwise); the local stopping test stays relative to the residual at
  * R_i x, so convergence to tolerance does not depend on the network.
  * The network lives on one device; every array below is a host pointer. */
 typedef struct nls_guess_net nls_guess_net;
-#define NLS_GUESS_FEATURES 391
-#define NLS_GUESS_OUTPUTS 1024
+#define NLS_GUESS_FEATURES 391        /* inputs of the scalar kind */
+#define NLS_GUESS_OUTPUTS 1024        /* outputs of the scalar kind */
+#define NLS_GUESS_FEATURES_DISP 267   /* inputs of the displacement kind */
+#define NLS_GUESS_OUTPUTS_DISP 2048   /* outputs of the displacement kind */
+#define NLS_GUESS_KIND_SCALAR 0
+#define NLS_GUESS_KIND_DISPLACEMENT 1
 #define NLS_GUESS_USE 1      /* propose starting points in nls_solve / nls_eval_Fx */
 #define NLS_GUESS_HARVEST 2  /* record (features, converged local state) pairs after every local solve */
 #define NLS_GUESS_FIRST_OUTER 4  /* with NLS_GUESS_USE: propose only at the first outer iteration of each
                                     load step of nls_solve (later iterations start from R_i u) */
 
-/* Create a network with hidden widths h1, h2 (multiples of 16), weights drawn from splitmix64
- * `seed`, on `device`, with room for `capacity` training pairs. */
+/* Create a network of NLS_GUESS_KIND_* `kind` with hidden widths h1, h2 (multiples of 16),
+ * weights drawn from splitmix64 `seed`, on `device`, with room for `capacity` training pairs.
+ * nls_guess_create makes the scalar kind.  NLS_E_ARG on a bad kind, width or capacity. */
 int nls_guess_create(nls_guess_net** out, int device, int32_t h1, int32_t h2, uint64_t seed, int64_t capacity);
+int nls_guess_create_kind(nls_guess_net** out, int device, int32_t kind, int32_t h1, int32_t h2, uint64_t seed,
+                          int64_t capacity);
+/* The network's kind and its numbers of inputs and outputs (n_in, n_out below). */
+int nls_guess_dims(const nls_guess_net* net, int32_t* kind, int32_t* n_in, int32_t* n_out);
 void nls_guess_destroy(nls_guess_net* net);
-/* Attach a network to a context (after nls_setup) with NLS_GUESS_* mode bits, or detach (net NULL). */
+/* Attach a network to a context (after nls_setup) with NLS_GUESS_* mode bits, or detach (net NULL).
+ * NLS_E_ARG when the kind does not match the problem (scalar: Eq. 1 on P1 triangles;
+ * displacement: Eq. 2 on Q1 quadrilaterals); NLS_E_UNSUPPORTED when the mesh is not a structured
+ * grid of the unit square numbered row by row. */
 int nls_guess_attach(nls_ctx* ctx, nls_guess_net* net, int32_t mode);
 /* Train on the harvested pairs: `steps` Adam steps on random minibatches of `batch` pairs
  * (splitmix64 `seed`), learning rate lr.  loss_out[steps] (may be NULL) receives the losses. */
 int nls_guess_train(nls_guess_net* net, int32_t steps, int32_t batch, double lr, uint64_t seed, float* loss_out);
 /* Number of harvested pairs. */
 int nls_guess_pairs(const nls_guess_net* net, int64_t* n_out);
-/* Parameters as one FP32 array in the order W1 [h1 x 391], b1, W2 [h2 x h1], b2, W3 [1024 x h2],
+/* Parameters as one FP32 array in the order W1 [h1 x n_in], b1, W2 [h2 x h1], b2, W3 [n_out x h2],
  * b3 (row-major); *count receives the length.  set_params also resets the Adam state. */
 int nls_guess_get_params(const nls_guess_net* net, float* params, int64_t* count);
 int nls_guess_set_params(nls_guess_net* net, const float* params, int64_t count);
-/* Normalisation of inputs and targets: x_norm = (x - mean) / scale per input, t_norm = t / tscale. */
+/* Normalisation of inputs and targets: x_norm = (x - mean) / scale per input (mean, scale [n_in]),
+ * t_norm = t / tscale. */
 int nls_guess_get_normalisation(const nls_guess_net* net, float* mean, float* scale, float* tscale);
 int nls_guess_set_normalisation(nls_guess_net* net, const float* mean, const float* scale, float tscale);
-/* Gradient of the loss on a given batch of normalised inputs X [B x 391] and targets
- * T [B x 1024] (host arrays), in the parameter order above, with FP32 (precision 0) or BF16
+/* Gradient of the loss on a given batch of normalised inputs X [B x n_in] and targets
+ * T [B x n_out] (host arrays), in the parameter order above, with FP32 (precision 0) or BF16
  * (precision 1) GEMM operands; *loss receives the loss.  Test hook for the gradient checks. */
 int nls_guess_gradient(nls_guess_net* net, int32_t B, const float* X, const float* T, int32_t precision, float* grad,
                        float* loss);
-/* Network output (FP32 inference) for normalised inputs X [B x 391] into Y [B x 1024]. */
+/* Network output (FP32 inference) for normalised inputs X [B x n_in] into Y [B x n_out]. */
 int nls_guess_forward(nls_guess_net* net, int32_t B, const float* X, float* Y);
 /* Test hooks of the input and output maps (context with an attached network; x [n_dofs] host):
  * the raw inputs of every subdomain at x and load factor `load` (before normalisation) into
- * features_out [n_sub x 391] (FP32); the proposal decoded from given network outputs
- * Y [n_sub x 1024] (normalised units, FP32) at x into guess_out [total_local_dofs] (the local
+ * features_out [n_sub x n_in] (FP32); the proposal decoded from given network outputs
+ * Y [n_sub x n_out] (normalised units, FP32) at x into guess_out [total_local_dofs] (the local
  * unknowns of every subdomain, concatenated in subdomain order as nls_get_local_states); and the
  * smoothing of given starts w [total_local_dofs] at x into w_out [total_local_dofs], with the
  * attached network's smoothing parameters. */

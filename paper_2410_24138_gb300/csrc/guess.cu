@@ -1,19 +1,22 @@
 // Learned initial guess for the local Newton solves (not part of the paper's method; see
-// include/nls.h for the definition of inputs, outputs and the acceptance rule).
+// include/nls.h for the definition of inputs, outputs and the acceptance rule).  Two kinds of
+// network: scalar (Eq. 1 on P1 triangles) and displacement (Eq. 2 on Q1 quadrilaterals, two
+// components per node).
 //
 // Kernels:
-//   k_guess_features   per subdomain: the 4 x 33 side samples of the Dirichlet data on the
-//                      node ring around the box of local unknowns, log k on 16 x 16 points,
-//                      f, box width and height (raw values).
-//   k_guess_normalise  raw features -> network inputs ((x - mean) / scale).
+//   k_guess_features   per subdomain: the 4 x 33 side samples of each component of x on the
+//                      box one node beyond the local unknowns (clamped to the mesh); Eq. 1:
+//                      log k on 16 x 16 points and the load factor times f; Eq. 2: the load
+//                      factor; box width and height (raw values).
+//   k_normalise        raw features -> network inputs ((x - mean) / scale).
 //   k_gemm_bf16        C = A B with BF16 operands on the tensor cores (mma.sync m16n8k16,
 //                      FP32 accumulation); operands are read as FP32 and rounded to BF16 when
 //                      staged, so master weights and activations stay FP32.
 //   k_gemm_f32         the same product in FP32 (inference and the FP32 gradient check).
-//   k_guess_decode     guess at every local unknown = Coons patch of the side samples +
-//                      bilinear interpolation of the 32 x 32 correction.
+//   k_guess_decode     guess at every local unknown = Coons patch of its component's side
+//                      samples + bilinear interpolation of that component's 32 x 32 correction.
 //   k_guess_harvest    training pair: raw features + correction (w - Coons) of the converged
-//                      local state, sampled bilinearly on the canonical grid.
+//                      local state, per component, sampled bilinearly on the canonical grid.
 //   k_adam             one Adam step on the FP32 master parameters.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -31,15 +34,19 @@
 namespace nls {
 
 constexpr int kSide = 33, kKS = 16, kGrid = 32;
-constexpr int kNF = NLS_GUESS_FEATURES, kNO = NLS_GUESS_OUTPUTS;
-static_assert(4 * kSide + kKS * kKS + 3 == kNF, "feature layout");
-static_assert(kGrid * kGrid == kNO, "output layout");
+constexpr int kNF = NLS_GUESS_FEATURES, kNO = NLS_GUESS_OUTPUTS, kG2 = kGrid * kGrid;
+constexpr int kNF2 = NLS_GUESS_FEATURES_DISP, kNO2 = NLS_GUESS_OUTPUTS_DISP;
+static_assert(4 * kSide + kKS * kKS + 3 == kNF, "feature layout (Eq. 1)");
+static_assert(kG2 == kNO, "output layout (Eq. 1)");
+static_assert(2 * 4 * kSide + 3 == kNF2, "feature layout (Eq. 2)");
+static_assert(2 * kG2 == kNO2, "output layout (Eq. 2)");
 
 // ------------------------------------------------------------------------------------------
 // network state
 // ------------------------------------------------------------------------------------------
 struct GuessNet {
   int device = 0;
+  int kind = NLS_GUESS_KIND_SCALAR, nf = kNF, no = kNO;  // inputs and outputs per subdomain
   int h1 = 0, h2 = 0;
   int64_t capacity = 0, npairs = 0, nparam = 0;
   int64_t off[6] = {0};  // W1, b1, W2, b2, W3, b3
@@ -69,21 +76,23 @@ struct GuessCtx {
   GuessNet* net = nullptr;
   int mode = 0;
   int nsub = 0;
-  // per subdomain: side sample maps (node0, node1, weight), k sample elements, f element, box
+  int ndof = 1;  // components per node (the network's kind)
+  // per subdomain: side sample maps (node0, node1, weight), k sample elements and f element
+  // (Eq. 1), box
   int32_t *side_n0 = nullptr, *side_n1 = nullptr, *kelem = nullptr, *felem = nullptr;
   float *side_w = nullptr, *box = nullptr;  // box: Lx, Ly
-  // per local unknown (concatenated as the local states): (s, t) in the ring box
+  // per local unknown (concatenated as the local states): (s, t) of its node in the box
   double2* st = nullptr;
   // per canonical point of every subdomain: 4 local-unknown positions (-1 = ring) and weights
   int4* cidx = nullptr;
   float2* cw = nullptr;
   // buffers
   float *raw = nullptr, *xin = nullptr, *yout = nullptr;
-  double* side = nullptr;  // side samples [nsub][132] of the last feature pass
+  double* side = nullptr;  // side samples [nsub][ndof x 132] of the last feature pass
   double* guess = nullptr; // proposed local states (total local unknowns)
   int32_t* accepted = nullptr;
   double* fcell_dev = nullptr;
-  double* diag = nullptr;  // per local unknown: sum_e k_e |grad phi_a|^2 |e| (Jacobi smoothing)
+  double* diag = nullptr;  // per local unknown: the Jacobi smoothing's diagonal
   int sweeps = 6;
   double omega = 0.8;
   int64_t proposed_total = 0, accepted_total = 0;
@@ -300,30 +309,30 @@ __global__ void k_adam(int64_t n, float* p, const float* g, float* m, float* v, 
 }
 
 // minibatch: X = normalised raw features, T = raw targets / tscale
-__global__ void k_gather_batch(int B, const int32_t* idx, const float* dX, const float* dT, const float* mean,
-                               const float* scale, float tscale, float* X, float* T) {
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)B * (kNF + kNO);
+__global__ void k_gather_batch(int B, int nf, int no, const int32_t* idx, const float* dX, const float* dT,
+                               const float* mean, const float* scale, float tscale, float* X, float* T) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)B * (nf + no);
        e += (int64_t)gridDim.x * blockDim.x) {
-    const int r = (int)(e / (kNF + kNO)), c = (int)(e % (kNF + kNO));
+    const int r = (int)(e / (nf + no)), c = (int)(e % (nf + no));
     const int64_t src = idx[r];
-    if (c < kNF) X[(int64_t)r * kNF + c] = (dX[src * kNF + c] - mean[c]) / scale[c];
-    else T[(int64_t)r * kNO + (c - kNF)] = dT[src * kNO + (c - kNF)] / tscale;
+    if (c < nf) X[(int64_t)r * nf + c] = (dX[src * nf + c] - mean[c]) / scale[c];
+    else T[(int64_t)r * no + (c - nf)] = dT[src * no + (c - nf)] / tscale;
   }
 }
 
-__global__ void k_normalise(int B, const float* raw, const float* mean, const float* scale, float* X) {
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)B * kNF; e += (int64_t)gridDim.x * blockDim.x) {
-    const int c = (int)(e % kNF);
+__global__ void k_normalise(int B, int nf, const float* raw, const float* mean, const float* scale, float* X) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)B * nf; e += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(e % nf);
     X[e] = (raw[e] - mean[c]) / scale[c];
   }
 }
 
 // per-feature mean and standard deviation over the first n pairs (fixed-order sums)
-__global__ void k_feature_stats(int64_t n, const float* dX, float* mean, float* scale) {
+__global__ void k_feature_stats(int64_t n, int nf, const float* dX, float* mean, float* scale) {
   const int c = blockIdx.x;
   __shared__ double red[256];
   double s = 0.0;
-  for (int64_t r = threadIdx.x; r < n; r += blockDim.x) s += dX[r * kNF + c];
+  for (int64_t r = threadIdx.x; r < n; r += blockDim.x) s += dX[r * nf + c];
   red[threadIdx.x] = s;
   __syncthreads();
   for (int o = blockDim.x / 2; o > 0; o >>= 1) {
@@ -334,7 +343,7 @@ __global__ void k_feature_stats(int64_t n, const float* dX, float* mean, float* 
   __syncthreads();
   double q = 0.0;
   for (int64_t r = threadIdx.x; r < n; r += blockDim.x) {
-    const double d = dX[r * kNF + c] - mu;
+    const double d = dX[r * nf + c] - mu;
     q += d * d;
   }
   red[threadIdx.x] = q;
@@ -379,6 +388,7 @@ struct GeoArgs {
   double load;
   float* raw;
   double* side;
+  int ndof, nf;  // components per node, inputs per subdomain
 };
 
 __device__ inline double side_value(const double* S, int side, double u) {
@@ -409,36 +419,50 @@ __device__ inline double corr_eval(const float* Y, double s, double t, float tsc
   return v * tscale;
 }
 
+// Eq. 1: [side samples (132), log k (256), load f, box width, box height]; Eq. 2: [side samples of
+// component 0 (132), of component 1 (132), load, box width, box height].
 __global__ void k_guess_features(GeoArgs G, int nsub) {
   const int sub = blockIdx.x;
   if (sub >= nsub) return;
-  float* out = G.raw + (int64_t)sub * kNF;
-  double* S = G.side + (int64_t)sub * 4 * kSide;
-  for (int q = threadIdx.x; q < 4 * kSide; q += blockDim.x) {
-    const int64_t k = (int64_t)sub * 4 * kSide + q;
+  constexpr int NS = 4 * kSide;
+  const int nd = G.ndof;
+  float* out = G.raw + (int64_t)sub * G.nf;
+  double* S = G.side + (int64_t)sub * nd * NS;
+  for (int e = threadIdx.x; e < nd * NS; e += blockDim.x) {
+    const int c = e / NS, q = e % NS;
+    const int64_t k = (int64_t)sub * NS + q;
     const double w = G.side_w[k];
-    const double v = (1.0 - w) * G.x[G.side_n0[k]] + w * G.x[G.side_n1[k]];
-    S[q] = v;
-    out[q] = (float)v;
+    const double v = (1.0 - w) * G.x[(int64_t)G.side_n0[k] * nd + c] + w * G.x[(int64_t)G.side_n1[k] * nd + c];
+    S[e] = v;
+    out[e] = (float)v;
   }
-  for (int q = threadIdx.x; q < kKS * kKS; q += blockDim.x)
-    out[4 * kSide + q] = (float)log(G.kcoef[G.kelem[(int64_t)sub * kKS * kKS + q]]);
-  if (threadIdx.x == 0) {
-    out[4 * kSide + kKS * kKS] = (float)(G.load * G.fcell[G.felem[sub]]);
-    out[4 * kSide + kKS * kKS + 1] = G.box[2 * sub];
-    out[4 * kSide + kKS * kKS + 2] = G.box[2 * sub + 1];
+  if (nd == 1) {
+    for (int q = threadIdx.x; q < kKS * kKS; q += blockDim.x)
+      out[NS + q] = (float)log(G.kcoef[G.kelem[(int64_t)sub * kKS * kKS + q]]);
+    if (threadIdx.x == 0) {
+      out[NS + kKS * kKS] = (float)(G.load * G.fcell[G.felem[sub]]);
+      out[NS + kKS * kKS + 1] = G.box[2 * sub];
+      out[NS + kKS * kKS + 2] = G.box[2 * sub + 1];
+    }
+  } else if (threadIdx.x == 0) {
+    out[nd * NS] = (float)G.load;
+    out[nd * NS + 1] = G.box[2 * sub];
+    out[nd * NS + 2] = G.box[2 * sub + 1];
   }
 }
 
+// local unknown a is component a % ndof of its node (node-major, component-interleaved)
 __global__ void k_guess_decode(GeoArgs G, int nsub, const float* Y, float tscale, double* guess) {
   const int sub = blockIdx.x;
   if (sub >= nsub) return;
   const SubMeta m = G.meta[sub];
-  const double* S = G.side + (int64_t)sub * 4 * kSide;
-  const float* Ys = Y + (int64_t)sub * kNO;
+  const int nd = G.ndof;
+  const double* S = G.side + (int64_t)sub * nd * 4 * kSide;
+  const float* Ys = Y + (int64_t)sub * nd * kG2;
   for (int a = threadIdx.x; a < m.n; a += blockDim.x) {
+    const int c = a % nd;
     const double2 p = G.st[m.vec_off + a];
-    guess[m.vec_off + a] = coons_eval(S, p.x, p.y) + corr_eval(Ys, p.x, p.y, tscale);
+    guess[m.vec_off + a] = coons_eval(S + c * 4 * kSide, p.x, p.y) + corr_eval(Ys + c * kG2, p.x, p.y, tscale);
   }
 }
 
@@ -448,23 +472,26 @@ __global__ void k_guess_harvest(GeoArgs G, int nsub, const double* w, float* dX,
   const int sub = blockIdx.x;
   if (sub >= nsub) return;
   const SubMeta m = G.meta[sub];
-  const double* S = G.side + (int64_t)sub * 4 * kSide;
-  float* X = dX + (slot0 + sub) * kNF;
-  float* T = dT + (slot0 + sub) * kNO;
-  for (int q = threadIdx.x; q < kNF; q += blockDim.x) X[q] = G.raw[(int64_t)sub * kNF + q];
-  for (int q = threadIdx.x; q < kNO; q += blockDim.x) {
-    const int4 id = G.cidx[(int64_t)sub * kNO + q];
-    const float2 wt = G.cw[(int64_t)sub * kNO + q];
+  const int nd = G.ndof;
+  const double* S = G.side + (int64_t)sub * nd * 4 * kSide;
+  float* X = dX + (slot0 + sub) * G.nf;
+  float* T = dT + (slot0 + sub) * nd * kG2;
+  for (int q = threadIdx.x; q < G.nf; q += blockDim.x) X[q] = G.raw[(int64_t)sub * G.nf + q];
+  for (int e = threadIdx.x; e < nd * kG2; e += blockDim.x) {
+    const int comp = e / kG2, q = e % kG2;
+    const int4 id = G.cidx[(int64_t)sub * kG2 + q];
+    const float2 wt = G.cw[(int64_t)sub * kG2 + q];
     const int ids[4] = {id.x, id.y, id.z, id.w};
     const double wts[4] = {(1.0 - wt.x) * (1.0 - wt.y), wt.x * (1.0 - wt.y), (1.0 - wt.x) * wt.y, wt.x * wt.y};
     double v = 0.0;
 #pragma unroll
     for (int c = 0; c < 4; ++c)
       if (ids[c] >= 0) {
-        const double2 p = G.st[m.vec_off + ids[c]];
-        v += wts[c] * (w[m.vec_off + ids[c]] - coons_eval(S, p.x, p.y));
+        const int64_t l = m.vec_off + (int64_t)ids[c] * nd + comp;
+        const double2 p = G.st[l];
+        v += wts[c] * (w[l] - coons_eval(S + comp * 4 * kSide, p.x, p.y));
       }
-    T[q] = (float)v;
+    T[e] = (float)v;
   }
 }
 
@@ -473,16 +500,16 @@ __global__ void k_guess_harvest(GeoArgs G, int nsub, const double* w, float* dX,
 void GuessNet::ensure_batch(int B) {
   if (B <= bmax) return;
   bmax = B;
-  X = alloc<float>((size_t)B * kNF);
-  T = alloc<float>((size_t)B * kNO);
+  X = alloc<float>((size_t)B * nf);
+  T = alloc<float>((size_t)B * no);
   const int hm = std::max(h1, h2);
   Z1 = alloc<float>((size_t)B * h1);
   A1 = alloc<float>((size_t)B * h1);
   Z2 = alloc<float>((size_t)B * h2);
   A2 = alloc<float>((size_t)B * h2);
-  Y = alloc<float>((size_t)B * kNO);
-  dA = alloc<float>((size_t)B * std::max(hm, kNO));
-  dZ = alloc<float>((size_t)B * std::max(hm, kNO));
+  Y = alloc<float>((size_t)B * no);
+  dA = alloc<float>((size_t)B * std::max(hm, no));
+  dZ = alloc<float>((size_t)B * std::max(hm, no));
   lossbuf = alloc<float>(1024);
   idx = alloc<int32_t>(B);
 }
@@ -498,12 +525,12 @@ void net_forward(GuessNet& N, cudaStream_t s, int B, const float* X, bool bf16) 
   const float* W3 = N.p + N.off[4];
   const float* b3 = N.p + N.off[5];
   const int grid = 1216;
-  gemm(s, bf16, B, N.h1, kNF, X, kNF, 1, W1, 1, kNF, N.Z1, N.h1);
+  gemm(s, bf16, B, N.h1, N.nf, X, N.nf, 1, W1, 1, N.nf, N.Z1, N.h1);
   k_bias_act<<<grid, 256, 0, s>>>(B, N.h1, N.Z1, b1, N.A1, 1);
   gemm(s, bf16, B, N.h2, N.h1, N.A1, N.h1, 1, W2, 1, N.h1, N.Z2, N.h2);
   k_bias_act<<<grid, 256, 0, s>>>(B, N.h2, N.Z2, b2, N.A2, 1);
-  gemm(s, bf16, B, kNO, N.h2, N.A2, N.h2, 1, W3, 1, N.h2, N.Y, kNO);
-  k_bias_act<<<grid, 256, 0, s>>>(B, kNO, N.Y, b3, nullptr, 0);
+  gemm(s, bf16, B, N.no, N.h2, N.A2, N.h2, 1, W3, 1, N.h2, N.Y, N.no);
+  k_bias_act<<<grid, 256, 0, s>>>(B, N.no, N.Y, b3, nullptr, 0);
   CK(cudaGetLastError());
 }
 
@@ -513,11 +540,11 @@ float net_gradient(GuessNet& N, cudaStream_t s, int B, bool bf16) {
   const float* W2 = N.p + N.off[2];
   const float* W3 = N.p + N.off[4];
   const int nb = 256;
-  k_loss_grad<<<nb, 256, 0, s>>>((int64_t)B * kNO, B, N.Y, N.T, N.dZ, N.lossbuf);
+  k_loss_grad<<<nb, 256, 0, s>>>((int64_t)B * N.no, B, N.Y, N.T, N.dZ, N.lossbuf);
   // layer 3: dW3 = dY^T A2, db3 = colsum dY, dA2 = dY W3
-  gemm(s, bf16, kNO, N.h2, B, N.dZ, 1, kNO, N.A2, N.h2, 1, N.g + N.off[4], N.h2);
-  k_colsum<<<(kNO + 255) / 256, 256, 0, s>>>(B, kNO, N.dZ, N.g + N.off[5]);
-  gemm(s, bf16, B, N.h2, kNO, N.dZ, kNO, 1, W3, N.h2, 1, N.dA, N.h2);
+  gemm(s, bf16, N.no, N.h2, B, N.dZ, 1, N.no, N.A2, N.h2, 1, N.g + N.off[4], N.h2);
+  k_colsum<<<(N.no + 255) / 256, 256, 0, s>>>(B, N.no, N.dZ, N.g + N.off[5]);
+  gemm(s, bf16, B, N.h2, N.no, N.dZ, N.no, 1, W3, N.h2, 1, N.dA, N.h2);
   k_gelu_back<<<1216, 256, 0, s>>>((int64_t)B * N.h2, N.Z2, N.dA);
   // layer 2 (dZ2 in dA)
   gemm(s, bf16, N.h2, N.h1, B, N.dA, 1, N.h2, N.A1, N.h1, 1, N.g + N.off[2], N.h1);
@@ -525,7 +552,7 @@ float net_gradient(GuessNet& N, cudaStream_t s, int B, bool bf16) {
   gemm(s, bf16, B, N.h1, N.h2, N.dA, N.h2, 1, W2, N.h1, 1, N.dZ, N.h1);
   k_gelu_back<<<1216, 256, 0, s>>>((int64_t)B * N.h1, N.Z1, N.dZ);
   // layer 1 (dZ1 in dZ)
-  gemm(s, bf16, N.h1, kNF, B, N.dZ, 1, N.h1, N.X, kNF, 1, N.g + N.off[0], kNF);
+  gemm(s, bf16, N.h1, N.nf, B, N.dZ, 1, N.h1, N.X, N.nf, 1, N.g + N.off[0], N.nf);
   k_colsum<<<(N.h1 + 255) / 256, 256, 0, s>>>(B, N.h1, N.dZ, N.g + N.off[1]);
   CK(cudaGetLastError());
   std::vector<float> part(nb);
@@ -537,7 +564,7 @@ float net_gradient(GuessNet& N, cudaStream_t s, int B, bool bf16) {
 }
 
 // ------------------------------------------------------------------------------------------
-// host geometry of the attachment (structured P1 meshes)
+// host geometry of the attachment (structured P1 or Q1 meshes of the unit square)
 // ------------------------------------------------------------------------------------------
 // Leading-term Jacobian diagonal of every local unknown: sum over the subdomain's elements of
 // k_e |grad phi_a|^2 |e| (the smoothing of proposed starts divides by it times (1 + w_a^2)).
@@ -561,9 +588,45 @@ std::vector<double> jacobi_diagonal(const Context& c) {
   return diag;
 }
 
+// Eq. 2: diagonal of the linear-elastic Q1 stiffness (the tangent at zero displacement) at every
+// local unknown, sum over elements and Gauss points of w det(J) ((lambda + 2 mu) (dN_a/dX_c)^2 +
+// mu (dN_a/dX_c')^2) for component c (c' the other one).
+std::vector<double> elasticity_diagonal(const Context& c) {
+  const LocalSet& s = c.ov;
+  double mu = 0.0, lam = 0.0;
+  lame(c, mu, lam);
+  std::vector<double> diag(s.total_n, 0.0);
+  for (int sb = 0; sb < s.count; ++sb) {
+    const SubMeta& m = s.meta[sb];
+    for (int e = 0; e < m.ne; ++e) {
+      const int64_t ge = s.elem_gid[m.elem_off + e];
+      for (int q = 0; q < 4; ++q) {
+        const double* g = &c.geom[ge * c.geom_stride + q * 10];
+        for (int a = 0; a < 4; ++a) {
+          const int t = s.lconn[(m.elem_off + e) * 4 + a];
+          if (t >= m.nV) continue;
+          const double gx = g[2 * a], gy = g[2 * a + 1];
+          diag[m.vec_off + 2 * t] += g[8] * ((lam + 2.0 * mu) * gx * gx + mu * gy * gy);
+          diag[m.vec_off + 2 * t + 1] += g[8] * ((lam + 2.0 * mu) * gy * gy + mu * gx * gx);
+        }
+      }
+    }
+    for (int a = 0; a < m.n; ++a)
+      if (!(diag[m.vec_off + a] > 0.0)) throw std::runtime_error("learned guess: zero Jacobi diagonal");
+  }
+  return diag;
+}
+
+// The scalar kind needs Eq. 1 on P1 triangles, the displacement kind Eq. 2 on Q1 quadrilaterals.
+bool guess_kind_matches(const Context& c, int kind) {
+  if (kind == NLS_GUESS_KIND_SCALAR) return c.elem_type == NLS_P1_TRI && c.ndof == 1;
+  return kind == NLS_GUESS_KIND_DISPLACEMENT && c.elem_type == NLS_Q1_QUAD && c.ndof == 2 &&
+         c.law == NLS_LAW_NEOHOOKE;
+}
+
 void build_geometry(Context& c, GuessCtx& G) {
-  if (c.elem_type != NLS_P1_TRI || c.ndof != 1)
-    throw std::runtime_error("the learned guess supports the P1 diffusion problem on structured meshes");
+  const int nd = c.ndof;
+  G.ndof = nd;
   // grid indices from coordinates
   double xmin = 1e300, xmax = -1e300, ymin = 1e300, ymax = -1e300;
   for (int64_t v = 0; v < c.n_nodes; ++v) {
@@ -587,13 +650,14 @@ void build_geometry(Context& c, GuessCtx& G) {
   auto node = [&](int i, int j) { return (int32_t)(j * side + i); };
   const LocalSet& s = c.ov;
   const int nsub = s.count;
-  std::vector<int32_t> n0((size_t)nsub * 4 * kSide), n1((size_t)nsub * 4 * kSide), kel((size_t)nsub * kKS * kKS),
-      fel(nsub);
+  const bool scalar = nd == 1;
+  std::vector<int32_t> n0((size_t)nsub * 4 * kSide), n1((size_t)nsub * 4 * kSide),
+      kel(scalar ? (size_t)nsub * kKS * kKS : 0), fel(scalar ? nsub : 0);
   std::vector<float> sw((size_t)nsub * 4 * kSide), box(2 * (size_t)nsub);
   std::vector<double2> st(s.total_n);
-  const std::vector<double> diag = jacobi_diagonal(c);
-  std::vector<int4> cidx((size_t)nsub * kNO);
-  std::vector<float2> cw((size_t)nsub * kNO);
+  const std::vector<double> diag = scalar ? jacobi_diagonal(c) : elasticity_diagonal(c);
+  std::vector<int4> cidx((size_t)nsub * kG2);
+  std::vector<float2> cw((size_t)nsub * kG2);
   for (int sb = 0; sb < nsub; ++sb) {
     const SubMeta& m = s.meta[sb];
     int ia = INT32_MAX, ib = -1, ja = INT32_MAX, jb = -1;
@@ -606,8 +670,9 @@ void build_geometry(Context& c, GuessCtx& G) {
       jb = std::max(jb, gj[v]);
       local[v] = a;
     }
-    // ring box [ia-1, ib+1] x [ja-1, jb+1] (inside the mesh: local unknowns are never on the boundary)
-    const int i0 = ia - 1, i1 = ib + 1, j0 = ja - 1, j1 = jb + 1;
+    // box [ia-1, ib+1] x [ja-1, jb+1] clamped to the mesh (the clamp acts only where local
+    // unknowns reach a Neumann edge)
+    const int i0 = std::max(ia - 1, 0), i1 = std::min(ib + 1, nn), j0 = std::max(ja - 1, 0), j1 = std::min(jb + 1, nn);
     const double Lx = (i1 - i0) * hx, Ly = (j1 - j0) * hy;
     box[2 * sb] = (float)Lx;
     box[2 * sb + 1] = (float)Ly;
@@ -631,7 +696,7 @@ void build_geometry(Context& c, GuessCtx& G) {
       n1[base + 3 * kSide + q] = node(i1, jj + 1);
       sw[base + 3 * kSide + q] = (float)wj;
     }
-    for (int b = 0; b < kKS; ++b)
+    for (int b = 0; b < (scalar ? kKS : 0); ++b)
       for (int a = 0; a < kKS; ++a) {
         const double fx = i0 + (a + 0.5) / kKS * (i1 - i0), fy = j0 + (b + 0.5) / kKS * (j1 - j0);
         const int ci = std::min((int)fx, nn - 1), cj = std::min((int)fy, nn - 1);
@@ -639,12 +704,12 @@ void build_geometry(Context& c, GuessCtx& G) {
         const bool lower = (fx - ci) >= (fy - cj);
         kel[(size_t)sb * kKS * kKS + b * kKS + a] = 2 * (cj * nn + ci) + (lower ? 0 : 1);
       }
-    {
+    if (scalar) {
       const int ci = std::min((i0 + i1) / 2, nn - 1), cj = std::min((j0 + j1) / 2, nn - 1);
       fel[sb] = 2 * (cj * nn + ci);
     }
     for (int a = 0; a < m.n; ++a) {
-      const int32_t v = s.tnode_gid[m.tnode_off + a];
+      const int32_t v = s.tnode_gid[m.tnode_off + a / nd];
       st[m.vec_off + a] = make_double2((gi[v] - i0) / (double)(i1 - i0), (gj[v] - j0) / (double)(j1 - j0));
     }
     for (int b = 0; b < kGrid; ++b)
@@ -655,8 +720,8 @@ void build_geometry(Context& c, GuessCtx& G) {
           auto it = local.find(node(i, j));
           return it == local.end() ? -1 : it->second;
         };
-        cidx[(size_t)sb * kNO + b * kGrid + a] = make_int4(lid(ii, jj), lid(ii + 1, jj), lid(ii, jj + 1), lid(ii + 1, jj + 1));
-        cw[(size_t)sb * kNO + b * kGrid + a] = make_float2((float)(fx - ii), (float)(fy - jj));
+        cidx[(size_t)sb * kG2 + b * kGrid + a] = make_int4(lid(ii, jj), lid(ii + 1, jj), lid(ii, jj + 1), lid(ii + 1, jj + 1));
+        cw[(size_t)sb * kG2 + b * kGrid + a] = make_float2((float)(fx - ii), (float)(fy - jj));
       }
   }
   Dev& D = *c.dev;
@@ -671,9 +736,9 @@ void build_geometry(Context& c, GuessCtx& G) {
   G.cidx = G.upload(D, cidx);
   G.cw = G.upload(D, cw);
   G.diag = G.upload(D, diag);
-  G.raw = G.alloc<float>((size_t)nsub * kNF);
-  G.xin = G.alloc<float>((size_t)nsub * kNF);
-  G.side = G.alloc<double>((size_t)nsub * 4 * kSide);
+  G.raw = G.alloc<float>((size_t)nsub * G.net->nf);
+  G.xin = G.alloc<float>((size_t)nsub * G.net->nf);
+  G.side = G.alloc<double>((size_t)nsub * nd * 4 * kSide);
   G.guess = G.alloc<double>(s.total_n);
   G.accepted = G.alloc<int32_t>(nsub);
   std::vector<double> fcell(c.n_elems, 1.0);
@@ -702,6 +767,8 @@ GeoArgs geo_args(Context& c, GuessCtx& G, const double* x, double load) {
   a.load = load;
   a.raw = G.raw;
   a.side = G.side;
+  a.ndof = G.ndof;
+  a.nf = G.net->nf;
   return a;
 }
 
@@ -720,7 +787,7 @@ GuessProposal guess_propose(Context& c, const double* x, double load) {
   N.ensure_batch(G->nsub);
   GeoArgs a = geo_args(c, *G, x, load);
   LAUNCH(D, k_guess_features, G->nsub, 128, 0, a, G->nsub);
-  LAUNCH(D, k_normalise, 1216, 256, 0, G->nsub, G->raw, N.mean, N.scale, G->xin);
+  LAUNCH(D, k_normalise, 1216, 256, 0, G->nsub, N.nf, G->raw, N.mean, N.scale, G->xin);
   net_forward(N, D.s, G->nsub, G->xin, false);
   D.launches += 6;
   LAUNCH(D, k_guess_decode, G->nsub, 128, 0, a, G->nsub, N.Y, N.tscale, G->guess);
@@ -745,8 +812,8 @@ GuessProposal guess_smoothing(Context& c) {
   return out;
 }
 
-// Test hooks: the raw features at x (host) into out [nsub x 391], and the decode of given network
-// outputs Y [nsub x 1024] (normalised units) at x into out [total local unknowns].
+// Test hooks: the raw features at x (host) into out [nsub x nf], and the decode of given network
+// outputs Y [nsub x no] (normalised units) at x into out [total local unknowns].
 int guess_features(Context& c, const double* x, double load, float* out) {
   GuessCtx* G = c.dev ? (GuessCtx*)c.dev->guess : nullptr;
   if (!G) {
@@ -758,7 +825,7 @@ int guess_features(Context& c, const double* x, double load, float* out) {
     CK(cudaMemcpyAsync(D.x, x, sizeof(double) * c.N, cudaMemcpyHostToDevice, D.s));
     GeoArgs a = geo_args(c, *G, D.x, load);
     LAUNCH(D, k_guess_features, G->nsub, 128, 0, a, G->nsub);
-    CK(cudaMemcpyAsync(out, G->raw, sizeof(float) * (size_t)G->nsub * kNF, cudaMemcpyDeviceToHost, D.s));
+    CK(cudaMemcpyAsync(out, G->raw, sizeof(float) * (size_t)G->nsub * G->net->nf, cudaMemcpyDeviceToHost, D.s));
     CK(cudaStreamSynchronize(D.s));
   } catch (const std::exception& ex) {
     c.last_error = ex.what();
@@ -778,7 +845,7 @@ int guess_decode(Context& c, const double* x, double load, const float* Y, doubl
   try {
     N.ensure_batch(G->nsub);
     CK(cudaMemcpyAsync(D.x, x, sizeof(double) * c.N, cudaMemcpyHostToDevice, D.s));
-    CK(cudaMemcpyAsync(N.Y, Y, sizeof(float) * (size_t)G->nsub * kNO, cudaMemcpyHostToDevice, D.s));
+    CK(cudaMemcpyAsync(N.Y, Y, sizeof(float) * (size_t)G->nsub * N.no, cudaMemcpyHostToDevice, D.s));
     GeoArgs a = geo_args(c, *G, D.x, load);
     LAUNCH(D, k_guess_features, G->nsub, 128, 0, a, G->nsub);
     LAUNCH(D, k_guess_decode, G->nsub, 128, 0, a, G->nsub, N.Y, N.tscale, G->guess);
@@ -860,17 +927,26 @@ struct nls_guess_net {
 extern "C" {
 
 int nls_guess_create(nls_guess_net** out, int device, int32_t h1, int32_t h2, uint64_t seed, int64_t capacity) {
+  return nls_guess_create_kind(out, device, NLS_GUESS_KIND_SCALAR, h1, h2, seed, capacity);
+}
+
+int nls_guess_create_kind(nls_guess_net** out, int device, int32_t kind, int32_t h1, int32_t h2, uint64_t seed,
+                          int64_t capacity) {
   if (!out || h1 <= 0 || h2 <= 0 || h1 % 16 || h2 % 16 || capacity < 0) return NLS_E_ARG;
+  if (kind != NLS_GUESS_KIND_SCALAR && kind != NLS_GUESS_KIND_DISPLACEMENT) return NLS_E_ARG;
   nls_guess_net* w = new (std::nothrow) nls_guess_net();
   if (!w) return NLS_E_NOMEM;
   GuessNet& N = w->n;
   try {
     CK(cudaSetDevice(device));
     N.device = device;
+    N.kind = kind;
+    N.nf = kind == NLS_GUESS_KIND_SCALAR ? nls::kNF : nls::kNF2;
+    N.no = kind == NLS_GUESS_KIND_SCALAR ? nls::kNO : nls::kNO2;
     N.h1 = h1;
     N.h2 = h2;
     N.capacity = capacity;
-    const int64_t sz[6] = {(int64_t)h1 * nls::kNF, h1, (int64_t)h2 * h1, h2, (int64_t)nls::kNO * h2, nls::kNO};
+    const int64_t sz[6] = {(int64_t)h1 * N.nf, h1, (int64_t)h2 * h1, h2, (int64_t)N.no * h2, N.no};
     int64_t o = 0;
     for (int k = 0; k < 6; ++k) {
       N.off[k] = o;
@@ -879,7 +955,7 @@ int nls_guess_create(nls_guess_net** out, int device, int32_t h1, int32_t h2, ui
     N.nparam = o;
     std::vector<float> p(o, 0.f);
     nls::SplitMix rng{seed};
-    const int fan_in[3] = {nls::kNF, h1, h2};
+    const int fan_in[3] = {N.nf, h1, h2};
     for (int l = 0; l < 3; ++l) {
       const double sd = 1.0 / std::sqrt((double)fan_in[l]);
       for (int64_t e = 0; e < sz[2 * l]; ++e) p[N.off[2 * l] + e] = (float)(sd * rng.normal());
@@ -891,13 +967,13 @@ int nls_guess_create(nls_guess_net** out, int device, int32_t h1, int32_t h2, ui
     CK(cudaMemcpy(N.p, p.data(), o * sizeof(float), cudaMemcpyHostToDevice));
     CK(cudaMemset(N.m, 0, o * sizeof(float)));
     CK(cudaMemset(N.v, 0, o * sizeof(float)));
-    N.mean = N.alloc<float>(nls::kNF);
-    N.scale = N.alloc<float>(nls::kNF);
-    std::vector<float> zero(nls::kNF, 0.f), one(nls::kNF, 1.f);
-    CK(cudaMemcpy(N.mean, zero.data(), nls::kNF * sizeof(float), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(N.scale, one.data(), nls::kNF * sizeof(float), cudaMemcpyHostToDevice));
-    N.dX = N.alloc<float>((size_t)capacity * nls::kNF);
-    N.dT = N.alloc<float>((size_t)capacity * nls::kNO);
+    N.mean = N.alloc<float>(N.nf);
+    N.scale = N.alloc<float>(N.nf);
+    std::vector<float> zero(N.nf, 0.f), one(N.nf, 1.f);
+    CK(cudaMemcpy(N.mean, zero.data(), N.nf * sizeof(float), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(N.scale, one.data(), N.nf * sizeof(float), cudaMemcpyHostToDevice));
+    N.dX = N.alloc<float>((size_t)capacity * N.nf);
+    N.dT = N.alloc<float>((size_t)capacity * N.no);
   } catch (const std::exception&) {
     for (void* q : N.allocs) cudaFree(q);
     delete w;
@@ -913,6 +989,14 @@ void nls_guess_destroy(nls_guess_net* w) {
   cudaDeviceSynchronize();
   for (void* q : w->n.allocs) cudaFree(q);
   delete w;
+}
+
+int nls_guess_dims(const nls_guess_net* w, int32_t* kind, int32_t* n_in, int32_t* n_out) {
+  if (!w) return NLS_E_ARG;
+  if (kind) *kind = w->n.kind;
+  if (n_in) *n_in = w->n.nf;
+  if (n_out) *n_out = w->n.no;
+  return NLS_OK;
 }
 
 int nls_guess_pairs(const nls_guess_net* w, int64_t* n) {
@@ -945,8 +1029,8 @@ int nls_guess_get_normalisation(const nls_guess_net* w, float* mean, float* scal
   if (!w) return NLS_E_ARG;
   const GuessNet& N = w->n;
   if (cudaSetDevice(N.device) != cudaSuccess) return NLS_E_CUDA;
-  if (mean) cudaMemcpy(mean, N.mean, nls::kNF * sizeof(float), cudaMemcpyDeviceToHost);
-  if (scale) cudaMemcpy(scale, N.scale, nls::kNF * sizeof(float), cudaMemcpyDeviceToHost);
+  if (mean) cudaMemcpy(mean, N.mean, N.nf * sizeof(float), cudaMemcpyDeviceToHost);
+  if (scale) cudaMemcpy(scale, N.scale, N.nf * sizeof(float), cudaMemcpyDeviceToHost);
   if (tscale) *tscale = N.tscale;
   return cudaDeviceSynchronize() == cudaSuccess ? NLS_OK : NLS_E_CUDA;
 }
@@ -955,8 +1039,8 @@ int nls_guess_set_normalisation(nls_guess_net* w, const float* mean, const float
   if (!w || !mean || !scale || !(tscale > 0.f)) return NLS_E_ARG;
   GuessNet& N = w->n;
   if (cudaSetDevice(N.device) != cudaSuccess) return NLS_E_CUDA;
-  cudaMemcpy(N.mean, mean, nls::kNF * sizeof(float), cudaMemcpyHostToDevice);
-  cudaMemcpy(N.scale, scale, nls::kNF * sizeof(float), cudaMemcpyHostToDevice);
+  cudaMemcpy(N.mean, mean, N.nf * sizeof(float), cudaMemcpyHostToDevice);
+  cudaMemcpy(N.scale, scale, N.nf * sizeof(float), cudaMemcpyHostToDevice);
   N.tscale = tscale;
   return cudaDeviceSynchronize() == cudaSuccess ? NLS_OK : NLS_E_CUDA;
 }
@@ -968,8 +1052,8 @@ int nls_guess_gradient(nls_guess_net* w, int32_t B, const float* X, const float*
   try {
     CK(cudaSetDevice(N.device));
     N.ensure_batch(B);
-    CK(cudaMemcpy(N.X, X, (size_t)B * nls::kNF * sizeof(float), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(N.T, T, (size_t)B * nls::kNO * sizeof(float), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(N.X, X, (size_t)B * N.nf * sizeof(float), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(N.T, T, (size_t)B * N.no * sizeof(float), cudaMemcpyHostToDevice));
     const float L = nls::net_gradient(N, 0, B, precision == 1);
     CK(cudaMemcpy(grad, N.g, N.nparam * sizeof(float), cudaMemcpyDeviceToHost));
     if (loss) *loss = L;
@@ -985,9 +1069,9 @@ int nls_guess_forward(nls_guess_net* w, int32_t B, const float* X, float* Y) {
   try {
     CK(cudaSetDevice(N.device));
     N.ensure_batch(B);
-    CK(cudaMemcpy(N.X, X, (size_t)B * nls::kNF * sizeof(float), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(N.X, X, (size_t)B * N.nf * sizeof(float), cudaMemcpyHostToDevice));
     nls::net_forward(N, 0, B, N.X, false);
-    CK(cudaMemcpy(Y, N.Y, (size_t)B * nls::kNO * sizeof(float), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(Y, N.Y, (size_t)B * N.no * sizeof(float), cudaMemcpyDeviceToHost));
   } catch (const std::exception&) {
     return NLS_E_CUDA;
   }
@@ -1002,10 +1086,10 @@ int nls_guess_train(nls_guess_net* w, int32_t steps, int32_t batch, double lr, u
     CK(cudaSetDevice(N.device));
     N.ensure_batch(batch);
     // normalisation from the harvested pairs (inputs per feature, targets by their rms)
-    nls::k_feature_stats<<<nls::kNF, 256>>>(N.npairs, N.dX, N.mean, N.scale);
+    nls::k_feature_stats<<<N.nf, 256>>>(N.npairs, N.nf, N.dX, N.mean, N.scale);
     double* rms = nullptr;
     CK(cudaMalloc(&rms, sizeof(double)));
-    nls::k_target_rms<<<1, 256>>>(N.npairs * nls::kNO, N.dT, rms);
+    nls::k_target_rms<<<1, 256>>>(N.npairs * N.no, N.dT, rms);
     double hr = 1.0;
     CK(cudaMemcpy(&hr, rms, sizeof(double), cudaMemcpyDeviceToHost));
     cudaFree(rms);
@@ -1015,7 +1099,7 @@ int nls_guess_train(nls_guess_net* w, int32_t steps, int32_t batch, double lr, u
     for (int st = 0; st < steps; ++st) {
       for (int r = 0; r < batch; ++r) idx[r] = (int32_t)(rng.next() % (uint64_t)N.npairs);
       CK(cudaMemcpy(N.idx, idx.data(), batch * sizeof(int32_t), cudaMemcpyHostToDevice));
-      nls::k_gather_batch<<<1216, 256>>>(batch, N.idx, N.dX, N.dT, N.mean, N.scale, N.tscale, N.X, N.T);
+      nls::k_gather_batch<<<1216, 256>>>(batch, N.nf, N.no, N.idx, N.dX, N.dT, N.mean, N.scale, N.tscale, N.X, N.T);
       const float L = nls::net_gradient(N, 0, batch, true);
       N.adam_t += 1;
       const float b1 = 0.9f, b2 = 0.999f;
@@ -1048,6 +1132,11 @@ int guess_attach(Context& c, nls_guess_net* w, int32_t mode) {
     if (!w || mode == 0) return NLS_OK;
     if (w->n.device != c.device) {
       c.last_error = "network and context live on different devices";
+      return NLS_E_ARG;
+    }
+    if (!guess_kind_matches(c, w->n.kind)) {
+      c.last_error = "the network's kind does not match the problem (scalar: Eq. 1 on P1 triangles; "
+                     "displacement: Eq. 2 on Q1 quadrilaterals)";
       return NLS_E_ARG;
     }
     GuessCtx* G = new GuessCtx();

@@ -97,7 +97,7 @@ EXPORTS = ["nls_options_default", "nls_create", "nls_destroy", "nls_strerror", "
            "nls_guess_get_normalisation", "nls_guess_set_normalisation", "nls_guess_gradient", "nls_guess_forward",
            "nls_guess_counts", "nls_get_tuning", "nls_guess_set_smoothing", "nls_set_coefficients",
            "nls_set_volume_force", "nls_set_lambda_mode", "nls_get_coarse_matrix", "nls_band_solve",
-           "nls_guess_features", "nls_guess_decode", "nls_guess_smooth"]
+           "nls_guess_features", "nls_guess_decode", "nls_guess_smooth", "nls_guess_create_kind", "nls_guess_dims"]
 
 _LIB = None
 _P = ctypes.c_void_p
@@ -156,6 +156,9 @@ def load() -> ctypes.CDLL:
         "nls_reset_kernel_stats": (ctypes.c_int, [_P]),
         "nls_local_corrections_noalloc": (ctypes.c_int, [_P, _P, _P, _P, _P, dbl]),
         "nls_guess_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, i32, i32, ctypes.c_uint64, i64]),
+        "nls_guess_create_kind": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, i32, i32, i32, ctypes.c_uint64,
+                                                 i64]),
+        "nls_guess_dims": (ctypes.c_int, [_P, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)]),
         "nls_guess_destroy": (None, [_P]),
         "nls_guess_attach": (ctypes.c_int, [_P, _P, i32]),
         "nls_guess_train": (ctypes.c_int, [_P, i32, i32, dbl, ctypes.c_uint64, _P]),
@@ -430,19 +433,26 @@ class Solver:
 
 
 GUESS_USE, GUESS_HARVEST, GUESS_FIRST_OUTER = 1, 2, 4
-GUESS_FEATURES, GUESS_OUTPUTS = 391, 1024
+GUESS_FEATURES, GUESS_OUTPUTS = 391, 1024              # scalar kind (Eq. 1)
+GUESS_FEATURES_DISP, GUESS_OUTPUTS_DISP = 267, 2048    # displacement kind (Eq. 2)
+GUESS_KIND_SCALAR, GUESS_KIND_DISPLACEMENT = 0, 1
 
 
 class GuessNet:
     """The learned-initial-guess network (include/nls.h); host arrays are numpy float32."""
 
-    def __init__(self, h1: int = 512, h2: int = 512, seed: int = 1, capacity: int = 0, device: int = 0):
+    def __init__(self, h1: int = 512, h2: int = 512, seed: int = 1, capacity: int = 0, device: int = 0,
+                 kind: int = GUESS_KIND_SCALAR):
         self.lib = load()
         self.h = _P()
-        st = self.lib.nls_guess_create(ctypes.byref(self.h), device, h1, h2, seed, capacity)
+        st = self.lib.nls_guess_create_kind(ctypes.byref(self.h), device, kind, h1, h2, seed, capacity)
         if st < 0:
-            raise NLSError(st, "nls_guess_create", "")
+            raise NLSError(st, "nls_guess_create_kind", "")
         self.h1, self.h2 = h1, h2
+        k, ni, no = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        self._check(self.lib.nls_guess_dims(self.h, ctypes.byref(k), ctypes.byref(ni), ctypes.byref(no)),
+                    "nls_guess_dims")
+        self.kind, self.n_in, self.n_out = k.value, ni.value, no.value
 
     def close(self):
         if self.h:
@@ -476,8 +486,8 @@ class GuessNet:
         self._check(self.lib.nls_guess_set_params(self.h, _ptr(p), p.shape[0]), "nls_guess_set_params")
 
     def normalisation(self):
-        mean = np.zeros(GUESS_FEATURES, dtype=np.float32)
-        scale = np.zeros(GUESS_FEATURES, dtype=np.float32)
+        mean = np.zeros(self.n_in, dtype=np.float32)
+        scale = np.zeros(self.n_in, dtype=np.float32)
         ts = ctypes.c_float()
         self._check(self.lib.nls_guess_get_normalisation(self.h, _ptr(mean), _ptr(scale), ctypes.byref(ts)),
                     "nls_guess_get_normalisation")
@@ -486,12 +496,16 @@ class GuessNet:
     def set_normalisation(self, mean, scale, tscale: float):
         mean = np.ascontiguousarray(mean, dtype=np.float32)
         scale = np.ascontiguousarray(scale, dtype=np.float32)
+        if mean.shape != (self.n_in,) or scale.shape != (self.n_in,):
+            raise ValueError(f"mean and scale need {self.n_in} entries")
         self._check(self.lib.nls_guess_set_normalisation(self.h, _ptr(mean), _ptr(scale), tscale),
                     "nls_guess_set_normalisation")
 
     def gradient(self, X: np.ndarray, T: np.ndarray, bf16: bool = False):
         X = np.ascontiguousarray(X, dtype=np.float32)
         T = np.ascontiguousarray(T, dtype=np.float32)
+        if X.ndim != 2 or X.shape[1] != self.n_in or T.shape != (X.shape[0], self.n_out):
+            raise ValueError(f"X must be [B, {self.n_in}] and T [B, {self.n_out}]")
         g = np.zeros(self.params().shape[0], dtype=np.float32)
         L = ctypes.c_float()
         self._check(self.lib.nls_guess_gradient(self.h, X.shape[0], _ptr(X), _ptr(T), 1 if bf16 else 0, _ptr(g),
@@ -500,7 +514,9 @@ class GuessNet:
 
     def forward(self, X: np.ndarray) -> np.ndarray:
         X = np.ascontiguousarray(X, dtype=np.float32)
-        Y = np.zeros((X.shape[0], GUESS_OUTPUTS), dtype=np.float32)
+        if X.ndim != 2 or X.shape[1] != self.n_in:
+            raise ValueError(f"X must be [B, {self.n_in}]")
+        Y = np.zeros((X.shape[0], self.n_out), dtype=np.float32)
         self._check(self.lib.nls_guess_forward(self.h, X.shape[0], _ptr(X), _ptr(Y)), "nls_guess_forward")
         return Y
 
@@ -511,7 +527,7 @@ class GuessNet:
 
     def split(self, flat: np.ndarray):
         """[(W, b)] of the three layers from a flat parameter array."""
-        sizes = [GUESS_FEATURES, self.h1, self.h2, GUESS_OUTPUTS]
+        sizes = [self.n_in, self.h1, self.h2, self.n_out]
         out, o = [], 0
         for fi, fo in zip(sizes[:-1], sizes[1:]):
             W = flat[o:o + fo * fi].reshape(fo, fi)
@@ -524,6 +540,14 @@ class GuessNet:
 
 def attach_guess(solver: "Solver", net: "GuessNet", mode: int):
     solver._check(solver.lib.nls_guess_attach(solver.h, net.h if net else None, mode), "nls_guess_attach")
+    solver._guess_dims = (net.n_in, net.n_out) if (net and mode) else None
+
+
+def _attached_dims(solver: "Solver"):
+    dims = getattr(solver, "_guess_dims", None)
+    if dims is None:
+        raise ValueError("the learned-guess hooks need an attached network")
+    return dims
 
 
 def set_guess_smoothing(solver: "Solver", sweeps: int, omega: float = 0.8):
@@ -531,17 +555,25 @@ def set_guess_smoothing(solver: "Solver", sweeps: int, omega: float = 0.8):
 
 
 def guess_features(solver: "Solver", x: np.ndarray, load: float = 1.0) -> np.ndarray:
-    """Raw inputs [n_sub, 391] of every subdomain at x (test hook; needs an attached network)."""
+    """Raw inputs [n_sub, n_in] of every subdomain at x (test hook; needs an attached network)."""
+    n_in, _ = _attached_dims(solver)
     x = np.ascontiguousarray(x, dtype=np.float64)
-    out = np.zeros((solver.n_sub, GUESS_FEATURES), dtype=np.float32)
+    n = solver.n_nodes * solver.ndof
+    if x.shape != (n,):
+        raise ValueError(f"x must have {n} entries")
+    out = np.zeros((solver.n_sub, n_in), dtype=np.float32)
     solver._check(solver.lib.nls_guess_features(solver.h, _ptr(x), load, _ptr(out)), "nls_guess_features")
     return out
 
 
 def guess_decode(solver: "Solver", x: np.ndarray, Y: np.ndarray, load: float = 1.0) -> np.ndarray:
-    """Proposal (concatenated local unknowns) decoded from network outputs Y [n_sub, 1024] at x."""
+    """Proposal (concatenated local unknowns) decoded from network outputs Y [n_sub, n_out] at x."""
+    _, n_out = _attached_dims(solver)
     x = np.ascontiguousarray(x, dtype=np.float64)
     Y = np.ascontiguousarray(Y, dtype=np.float32)
+    n = solver.n_nodes * solver.ndof
+    if x.shape != (n,) or Y.shape != (solver.n_sub, n_out):
+        raise ValueError(f"x must have {n} entries and Y be [{solver.n_sub}, {n_out}]")
     out = np.zeros(solver.sizes().total_local_dofs)
     solver._check(solver.lib.nls_guess_decode(solver.h, _ptr(x), load, _ptr(Y), _ptr(out)), "nls_guess_decode")
     return out
@@ -551,6 +583,9 @@ def guess_smooth(solver: "Solver", x: np.ndarray, w: np.ndarray, load: float = 1
     """The smoothing of given starts w (concatenated local unknowns) at x."""
     x = np.ascontiguousarray(x, dtype=np.float64)
     w = np.ascontiguousarray(w, dtype=np.float64)
+    n, nt = solver.n_nodes * solver.ndof, solver.sizes().total_local_dofs
+    if x.shape != (n,) or w.shape != (nt,):
+        raise ValueError(f"x must have {n} entries and w {nt}")
     out = np.zeros_like(w)
     solver._check(solver.lib.nls_guess_smooth(solver.h, _ptr(x), load, _ptr(w), _ptr(out)), "nls_guess_smooth")
     return out

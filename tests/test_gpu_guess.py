@@ -29,13 +29,16 @@ def _blocks(net, flat):
     return [(W.astype(np.float64), b.astype(np.float64)) for W, b in net.split(flat)]
 
 
+@pytest.mark.parametrize("kind", [0, 1], ids=["scalar", "displacement"])
 @pytest.mark.parametrize("bf16,tol", [(False, 1e-4), (True, 2e-2)])
-def test_gradient_matches_reference(nls, bf16, tol):
-    net = nls.GuessNet(h1=32, h2=48, seed=3)
+def test_gradient_matches_reference(nls, bf16, tol, kind):
+    net = nls.GuessNet(h1=32, h2=48, seed=3, kind=kind)
+    assert (net.n_in, net.n_out) == ((nls.GUESS_FEATURES, nls.GUESS_OUTPUTS) if kind == 0 else
+                                     (nls.GUESS_FEATURES_DISP, nls.GUESS_OUTPUTS_DISP))
     rng = np.random.default_rng(0)
     B = 24
-    X = rng.standard_normal((B, nls.GUESS_FEATURES)).astype(np.float32)
-    T = rng.standard_normal((B, nls.GUESS_OUTPUTS)).astype(np.float32)
+    X = rng.standard_normal((B, net.n_in)).astype(np.float32)
+    T = rng.standard_normal((B, net.n_out)).astype(np.float32)
     g, L = net.gradient(X, T, bf16=bf16)
     params = _blocks(net, net.params())
     Y, cache = mlp.forward(params, X.astype(np.float64))
@@ -47,10 +50,11 @@ def test_gradient_matches_reference(nls, bf16, tol):
         assert np.linalg.norm(gb - rb) <= tol * max(np.linalg.norm(rb), 1e-30)
 
 
-def test_inference_matches_reference(nls):
-    net = nls.GuessNet(h1=64, h2=32, seed=5)
+@pytest.mark.parametrize("kind", [0, 1], ids=["scalar", "displacement"])
+def test_inference_matches_reference(nls, kind):
+    net = nls.GuessNet(h1=64, h2=32, seed=5, kind=kind)
     rng = np.random.default_rng(1)
-    X = rng.standard_normal((10, nls.GUESS_FEATURES)).astype(np.float32)
+    X = rng.standard_normal((10, net.n_in)).astype(np.float32)
     Y = net.forward(X)
     params = _blocks(net, net.params())
     Yr, _ = mlp.forward(params, X.astype(np.float64))
@@ -198,3 +202,95 @@ def test_smoothing_matches_oracle(nls, guess_case):
                           for lp, w0 in zip(sw.locals, starts)])
     np.testing.assert_allclose(got, ref, rtol=0, atol=1e-12 * np.abs(ref).max())
     assert np.abs(got - np.concatenate(starts)).max() > 1e-3  # the sweeps did change the starts
+
+
+# ---- Eq. 2: the displacement kind -------------------------------------------------------------
+
+def _nh_case(n=32, per=3, seed=7, traction=4.0):
+    """Q1 Neo-Hooke on n x n cells, per x per bricks, overlap 2 (the right column of bricks reaches
+    the traction edge, the top and bottom rows the free edges: their boxes are clamped)."""
+    return I.neohooke_problem(n, I.brick_partition(n, per, per, seed), per * per, 2, traction, load_steps=3)
+
+
+@pytest.fixture(scope="module")
+def nh_guess_case(nls):
+    p = _nh_case()
+    s = nls.make_solver(p, coupling="one", precision="fp32")
+    net = nls.GuessNet(h1=32, h2=32, seed=2, kind=nls.GUESS_KIND_DISPLACEMENT)
+    nls.attach_guess(s, net, nls.GUESS_USE)
+    nls.set_guess_smoothing(s, 6, 0.8)
+    # a smooth bending state (det F > 0 everywhere) plus small noise on the free dofs
+    X, Y = p.xy[:, 0], p.xy[:, 1]
+    x = np.zeros(2 * p.n_nodes)
+    x[0::2] = 0.01 * np.sin(np.pi * X) * Y
+    x[1::2] = -0.02 * X ** 2
+    x += 1e-4 * np.random.default_rng(12).standard_normal(2 * p.n_nodes)
+    x = np.where(fem.free_mask(p), x, 0.0)
+    return p, s, net, x
+
+
+def test_displacement_kind_is_checked_against_the_problem(nls):
+    from paper_2410_24138_gb300.nls import NLSError
+    s = nls.make_solver(_c4_family(1001, n=32, per=2), coupling="one")
+    with pytest.raises(NLSError):
+        nls.attach_guess(s, nls.GuessNet(h1=16, h2=16, kind=nls.GUESS_KIND_DISPLACEMENT), nls.GUESS_USE)
+    t = nls.make_solver(_nh_case(n=16, per=2), coupling="one")
+    with pytest.raises(NLSError):
+        nls.attach_guess(t, nls.GuessNet(h1=16, h2=16), nls.GUESS_USE)
+
+
+def test_displacement_feature_map_matches_oracle(nls, nh_guess_case):
+    """All 267 raw inputs of every subdomain (both components' side samples, load, box) against
+    the oracle: FP32 storage of FP64 values (1e-6 relative, +1e-7 of the field)."""
+    from oracle import decomposition as dec, guess as G
+    p, s, net, x = nh_guess_case
+    F = nls.guess_features(s, x, 0.7)
+    assert F.shape == (p.n_sub, nls.GUESS_FEATURES_DISP)
+    subs, _ = dec.decompose(p)
+    for i, sub in enumerate(subs):
+        ref = G.features(p, sub.vnodes, x, 0.7)
+        np.testing.assert_allclose(F[i], ref, rtol=1e-6, atol=1e-7 * np.abs(x).max())
+
+
+def test_displacement_decode_matches_oracle(nls, nh_guess_case):
+    """Both components' Coons patches plus their corrections at every local unknown, FP64 on
+    both sides from the same FP32 outputs: 1e-12 of the largest value."""
+    from oracle import decomposition as dec, guess as G
+    p, s, net, x = nh_guess_case
+    Y = np.random.default_rng(3).standard_normal((p.n_sub, nls.GUESS_OUTPUTS_DISP)).astype(np.float32)
+    tscale = net.normalisation()[2]
+    got = nls.guess_decode(s, x, Y, 0.7)
+    subs, _ = dec.decompose(p)
+    ref = np.concatenate([G.decode(p, sub.vnodes, x, Y[i].astype(np.float64), tscale) for i, sub in enumerate(subs)])
+    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+
+
+def test_displacement_smoothing_matches_oracle(nls, nh_guess_case):
+    """Six damped Jacobi sweeps with the elastic-stiffness diagonal on both sides, FP64: only the
+    summation order of the local residuals differs (1e-12 of the largest value)."""
+    from oracle import guess as G, schwarz as S
+    p, s, net, x = nh_guess_case
+    sw = S.Schwarz(p, S.Options(coupling=S.ONE_LEVEL), with_coarse=False)
+    rng = np.random.default_rng(5)
+    starts = [x[lp.sub.dofs] + 1e-4 * rng.standard_normal(lp.sub.n) for lp in sw.locals]
+    got = nls.guess_smooth(s, x, np.concatenate(starts), 0.7)
+    ref = np.concatenate([G.smooth(lp, x, w0, 0.7, 6, 0.8, G.jacobi_diagonal(p, lp.sub.vnodes))
+                          for lp, w0 in zip(sw.locals, starts)])
+    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+    assert np.abs(got - np.concatenate(starts)).max() > 1e-5  # the sweeps did change the starts
+
+
+def test_displacement_garbage_network_does_not_change_the_solution(nls):
+    p = _nh_case(n=24, per=3)
+    ref = nls.make_solver(p, coupling="hybrid")
+    u_ref, _ = ref.solve()
+    s = nls.make_solver(p, coupling="hybrid")
+    net = nls.GuessNet(h1=32, h2=32, seed=9, kind=nls.GUESS_KIND_DISPLACEMENT)
+    mean, scale, _ = net.normalisation()
+    net.set_normalisation(mean, scale, 1e3)
+    nls.attach_guess(s, net, nls.GUESS_USE)
+    u, rep = s.solve()
+    proposed, accepted = nls.guess_counts(s)
+    assert rep.status == 0 and rep.final_residual < 1e-8
+    assert proposed > 0 and accepted == 0
+    assert np.linalg.norm(u - u_ref) <= 1e-6 * np.linalg.norm(u_ref)
