@@ -93,7 +93,7 @@ struct GuessCtx {
   int32_t* accepted = nullptr;
   double* fcell_dev = nullptr;
   double* diag = nullptr;  // per local unknown: the Jacobi smoothing's diagonal
-  int sweeps = 6;
+  int sweeps = 6;  // smoothing defaults: 6 sweeps for the scalar kind, 2 for the displacement kind
   double omega = 0.8;
   int64_t proposed_total = 0, accepted_total = 0;
   std::vector<void*> allocs;
@@ -1142,6 +1142,7 @@ int guess_attach(Context& c, nls_guess_net* w, int32_t mode) {
     GuessCtx* G = new GuessCtx();
     G->net = &w->n;
     G->mode = mode;
+    if (w->n.kind == NLS_GUESS_KIND_DISPLACEMENT) G->sweeps = 2;
     build_geometry(c, *G);
     c.dev->guess = G;
   } catch (const std::exception& ex) {

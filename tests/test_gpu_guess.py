@@ -294,3 +294,42 @@ def test_displacement_garbage_network_does_not_change_the_solution(nls):
     assert rep.status == 0 and rep.final_residual < 1e-8
     assert proposed > 0 and accepted == 0
     assert np.linalg.norm(u - u_ref) <= 1e-6 * np.linalg.norm(u_ref)
+
+
+def test_displacement_guess_gains_full_local_newton_steps(nls):
+    """Harvest along the load ramp of 24 solves on training partitions (Neo-Hooke, 256^2 Q1, 64
+    bricks of ~32^2 cells, as in the 2048^2 workload), train, then propose at the first outer
+    iteration of every load step on two held-out partitions in the chosen form (chord steps on
+    kept factors from the second outer iteration on): most proposals are taken, the full local
+    Newton steps (assembly + factorization) drop, and the converged solutions are the method's own."""
+    n, per = 256, 8
+
+    def case(seed):
+        return I.neohooke_problem(n, I.brick_partition(n, per, per, seed), per * per, 2, I.NEOHOOKE_TRACTION_MAX, 5)
+
+    net = nls.GuessNet(h1=512, h2=512, seed=11, capacity=24 * per * per * 20, kind=nls.GUESS_KIND_DISPLACEMENT)
+    for seed in range(1, 25):
+        s = nls.make_solver(case(seed), coupling="hybrid")
+        nls.attach_guess(s, net, nls.GUESS_HARVEST)
+        _, rep = s.solve()
+        assert rep.status == 0
+        s.close()
+    losses = net.train(steps=6000, batch=256, lr=1e-3, seed=5)
+    assert losses[-100:].mean() < 0.2 * losses[:20].mean()
+    full_plain = full_guess = taken = offered = 0
+    for seed in (101, 102):
+        p = case(seed)
+        a = nls.make_solver(p, coupling="hybrid")
+        ua, ra = a.solve()
+        b = nls.make_solver(p, coupling="hybrid")
+        nls.attach_guess(b, net, nls.GUESS_USE | nls.GUESS_FIRST_OUTER)
+        ub, rb = b.solve()
+        pr, ac = nls.guess_counts(b)
+        assert rb.status == 0 and rb.final_residual < 1e-8
+        assert np.linalg.norm(ub - ua) <= 1e-6 * np.linalg.norm(ua)
+        full_plain += ra.subdomain_newton_steps - ra.local_chord_steps
+        full_guess += rb.subdomain_newton_steps - rb.local_chord_steps
+        taken += ac
+        offered += pr
+    assert taken > 0.5 * offered
+    assert full_guess < full_plain
