@@ -143,6 +143,8 @@ __global__ void __launch_bounds__(512) k_tlu_panel(int k, int NT, int TB, FT* __
 #pragma unroll
     for (int b = 0; b < CB; ++b) R[a][b] = Akk[(ty + 16 * a) * TS + tx + 32 * b];
   if (tid == 0) s_bad = 0;
+  // Row r = ty + 16 a is the same in a whole warp, so the tests on r (and on whole 32-column
+  // groups b) are warp-uniform: finished row groups and column groups skip their updates.
   for (int t = 0; t < TS; ++t) {
     FT* rb = rowbuf + (t & 1) * TS;
     FT* cb = colbuf + (t & 1) * TS;
@@ -163,12 +165,16 @@ __global__ void __launch_bounds__(512) k_tlu_panel(int k, int NT, int TB, FT* __
 #pragma unroll
     for (int a = 0; a < RA; ++a) {
       const int r = ty + 16 * a;
-      const FT l = cb[r] * rp;
+      if (r > t) {  // warp-uniform
+        const FT l = cb[r] * rp;
 #pragma unroll
-      for (int b = 0; b < CB; ++b) {
-        const int c = tx + 32 * b;
-        if (r > t && c > t) R[a][b] -= l * rb[c];
-        else if (r > t && c == t) R[a][b] = l;  // the multiplier of L
+        for (int b = 0; b < CB; ++b) {
+          if (32 * b + 31 >= t) {  // the column group is not finished
+            const int c = tx + 32 * b;
+            if (c > t) R[a][b] -= l * rb[c];
+            else if (c == t) R[a][b] = l;  // the multiplier of L
+          }
+        }
       }
     }
   }
@@ -205,7 +211,7 @@ __global__ void __launch_bounds__(512) k_tlu_panel(int k, int NT, int TB, FT* __
 #pragma unroll
     for (int b = 0; b < CB; ++b) {
       const int c = tx + 32 * b;
-      m[b] = lower ? Dg[t * LD + c] : Dg[c * LD + t];
+      m[b] = (32 * b + 31 < t) ? (FT)0 : (lower ? Dg[t * LD + c] : Dg[c * LD + t]);
     }
     __syncthreads();
 #pragma unroll
@@ -213,9 +219,11 @@ __global__ void __launch_bounds__(512) k_tlu_panel(int k, int NT, int TB, FT* __
       const FT x = cb[ty + 16 * a];
 #pragma unroll
       for (int b = 0; b < CB; ++b) {
-        const int c = tx + 32 * b;
-        if (c > t) X[a][b] -= x * m[b];
-        else if (c == t) X[a][b] = x;  // final value of column t
+        if (32 * b + 31 >= t) {  // the column group is not final
+          const int c = tx + 32 * b;
+          if (c > t) X[a][b] -= x * m[b];
+          else if (c == t) X[a][b] = x;  // final value of column t
+        }
       }
     }
   }
@@ -472,9 +480,17 @@ __global__ void __launch_bounds__(1024) k_tile_inverses(int NT, const float* __r
 // ---- the cluster solve -------------------------------------------------------------------------
 // z = (accumulate ? z : 0) + A_0^-1 rhs with the tile products above, by one cluster of kSolveCL
 // CTAs (see the head of this file).  Shared memory per CTA: the whole forward result y (every CTA
-// keeps all of it: NT x 128 FP32), a ring of TB + 1 tiles of x, and the current tile of rhs.
-// With *skip set the kernel returns at once in every CTA (the flag is written by an earlier
-// kernel, so all CTAs read the same value); `reset`, if given, is cleared.
+// keeps all of it: NT x 128 FP32), a ring of TB + 1 tiles of x, the current tile of rhs
+// (double-buffered) and one mbarrier per step of each sweep.  CTA r solves rows 16 r .. 16 r + 15
+// of every tile (two per warp) and sends them to every CTA of the cluster with st.async, which
+// completes 8 bytes per warp on the receiver's mbarrier of that step (8 CTAs x 8 warps x 8 bytes =
+// 512 bytes per step); a step waits only for the mbarrier of the tile it needs, not for a
+// cluster-wide barrier.  Each mbarrier is used once (phase 0).  Ring slots of x are safe to
+// overwrite: a CTA sends x_t only after x_{t+1} has arrived from every CTA, i.e. after every warp
+// of the cluster has read what it needed from slot t mod (TB + 1).  Waits are bounded: a CTA that
+// gives up sets *status = ST_TIMEOUT and stops waiting (its results are then garbage; the host
+// raises).  With *skip set the kernel returns at once in every CTA (the flag is written by an
+// earlier kernel, so all CTAs read the same value); `reset`, if given, is cleared.
 constexpr int kSolveCL = 8;
 constexpr int kSolveRows = kTcTS / kSolveCL;  // rows of every tile per CTA (two per warp)
 constexpr int kSolveMaxTB = 4;                // TB of half bandwidths up to 480 (the solves' limit)
@@ -483,7 +499,7 @@ __device__ inline float dot4(const float4 a, const float4 b) { return a.x * b.x 
 
 __global__ void __cluster_dims__(kSolveCL, 1, 1) __launch_bounds__(256, 1)
     k_tile_solve(int N0, int NT, int TB, const float* __restrict__ pool, const double* __restrict__ rhs,
-                 double* __restrict__ z, int accumulate, const int* skip, int* reset) {
+                 double* __restrict__ z, int accumulate, const int* skip, int* reset, int32_t* status) {
   if (skip && *skip) return;
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank();
@@ -491,11 +507,26 @@ __global__ void __cluster_dims__(kSolveCL, 1, 1) __launch_bounds__(256, 1)
   float* y = sms;                                 // NT x 128
   float* xr = y + (int64_t)NT * kTcTS;            // (TB + 1) x 128 ring
   float* gt = xr + (kSolveMaxTB + 1) * kTcTS;     // 2 x 128 (double-buffered right-hand side)
+  uint64_t* fb = (uint64_t*)(gt + 2 * kTcTS);     // NT forward-step barriers
+  uint64_t* bb = fb + NT;                         // NT backward-step barriers
   const PoolIdx P = pool_index(NT, TB);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int row0 = rank * kSolveRows + 2 * warp;  // this warp's rows within every tile
   if (reset && rank == 0 && threadIdx.x == 0) *reset = 0;
   constexpr int64_t TT = (int64_t)kTcTS * kTcTS;
+  constexpr uint32_t kStepBytes = kSolveCL * kSolveRows * sizeof(float);
+  if (threadIdx.x == 0) {
+    for (int t = 0; t < 2 * NT; ++t) tc::mbar_init(fb + t, 1);
+    tc::mbar_init_fence();
+    for (int t = 0; t < 2 * NT; ++t) tc::mbar_arrive_expect_tx(fb + t, kStepBytes);
+  }
+  bool live = true;  // false once a wait gave up: no further waits
+  auto wait = [&](uint64_t* bar) {
+    if (live && !tc::mbar_wait_cluster(bar, 0)) {
+      live = false;
+      if (lane == 0) atomicExch(status, (int32_t)ST_TIMEOUT);
+    }
+  };
   // operand rows of one step into registers: [0] the diagonal inverse, [k] the k-th product
   float4 cur[kSolveMaxTB + 1][2], nxt[kSolveMaxTB + 1][2];
   auto load = [&](int t, bool fwd, float4 (&R)[kSolveMaxTB + 1][2]) {
@@ -526,8 +557,12 @@ __global__ void __cluster_dims__(kSolveCL, 1, 1) __launch_bounds__(256, 1)
       asm volatile("prefetch.global.L2 [%0];" ::"l"(__cvta_generic_to_global(a)));
     }
   };
+  // this warp's two solved rows of step t into CTA `lane`'s copy of `buf`, completing on its `bar`
+  auto send = [&](float* buf, uint64_t* bar, float a0, float a1) {
+    if (lane < kSolveCL) tc::st_async_f2(tc::cluster_addr(buf + row0, lane), a0, a1, tc::cluster_addr(bar, lane));
+  };
   constexpr int kSolveL2 = 4;
-  cl.sync();  // every CTA of the cluster runs before the first remote store
+  cl.sync();  // every CTA's barriers are initialised and armed before the first remote store
   // forward: y_t = L_tt^-1 g_t - sum_k M_tk y_{t-k}; the right-hand side of the next step is read
   // into a register during the current one (double-buffered tile gt)
   load(0, true, cur);
@@ -544,6 +579,7 @@ __global__ void __cluster_dims__(kSolveCL, 1, 1) __launch_bounds__(256, 1)
     }
     const float4 g4 = ((const float4*)(gt + (t & 1) * kTcTS))[lane];
     float a0 = dot4(cur[0][0], g4), a1 = dot4(cur[0][1], g4);
+    if (t >= 1) wait(fb + t - 1);  // y_{t-1} complete (older tiles were waited for before)
 #pragma unroll
     for (int k = 1; k <= kSolveMaxTB; ++k)
       if (k <= TB && t - k >= 0) {
@@ -556,16 +592,13 @@ __global__ void __cluster_dims__(kSolveCL, 1, 1) __launch_bounds__(256, 1)
       a0 += __shfl_xor_sync(0xffffffffu, a0, o);
       a1 += __shfl_xor_sync(0xffffffffu, a1, o);
     }
-    if (lane < kSolveCL) {
-      float* dst = cl.map_shared_rank(y + (int64_t)t * kTcTS, lane);
-      dst[row0] = a0;
-      dst[row0 + 1] = a1;
-    }
+    send(y + (int64_t)t * kTcTS, fb + t, a0, a1);
     if (threadIdx.x < kTcTS && t + 1 < NT) gt[((t + 1) & 1) * kTcTS + threadIdx.x] = gnext;
-    cl.sync();
+    __syncthreads();  // the next step's right-hand side tile
 #pragma unroll
     for (int k = 0; k <= kSolveMaxTB; ++k) cur[k][0] = nxt[k][0], cur[k][1] = nxt[k][1];
   }
+  wait(fb + NT - 1);
   // backward: x_t = U_tt^-1 y_t - sum_k N_tk x_{t+k}
   const int RB = TB + 1;
   load(NT - 1, false, cur);
@@ -575,6 +608,7 @@ __global__ void __cluster_dims__(kSolveCL, 1, 1) __launch_bounds__(256, 1)
     if (t - kSolveL2 >= 0) l2_ahead(t - kSolveL2, false);
     const float4 yv = ((const float4*)(y + (int64_t)t * kTcTS))[lane];
     float a0 = dot4(cur[0][0], yv), a1 = dot4(cur[0][1], yv);
+    if (t + 1 < NT) wait(bb + t + 1);  // x_{t+1} complete
 #pragma unroll
     for (int k = 1; k <= kSolveMaxTB; ++k)
       if (k <= TB && t + k < NT) {
@@ -587,23 +621,22 @@ __global__ void __cluster_dims__(kSolveCL, 1, 1) __launch_bounds__(256, 1)
       a0 += __shfl_xor_sync(0xffffffffu, a0, o);
       a1 += __shfl_xor_sync(0xffffffffu, a1, o);
     }
-    if (lane < kSolveCL) {
-      float* dst = cl.map_shared_rank(xr + (t % RB) * kTcTS, lane);
-      dst[row0] = a0;
-      dst[row0 + 1] = a1;
-    }
+    send(xr + (t % RB) * kTcTS, bb + t, a0, a1);
     if (lane == 0) {
       const int64_t R0 = (int64_t)t * kTcTS + row0;
       if (R0 < N0) z[R0] = (accumulate ? z[R0] : 0.0) + (double)a0;
       if (R0 + 1 < N0) z[R0 + 1] = (accumulate ? z[R0 + 1] : 0.0) + (double)a1;
     }
-    cl.sync();
 #pragma unroll
     for (int k = 0; k <= kSolveMaxTB; ++k) cur[k][0] = nxt[k][0], cur[k][1] = nxt[k][1];
   }
+  wait(bb);  // every remote store into this CTA has landed before it leaves
+  cl.sync();
 }
 
-size_t tile_solve_smem(int NT) { return sizeof(float) * ((size_t)NT * kTcTS + (kSolveMaxTB + 3) * kTcTS); }
+size_t tile_solve_smem(int NT) {
+  return sizeof(float) * ((size_t)NT * kTcTS + (kSolveMaxTB + 3) * kTcTS) + 2 * sizeof(uint64_t) * (size_t)NT;
+}
 
 // ---- tiles -> band layout of the one-CTA factorization: d < b0 L (scaled), d = b0 the reciprocal
 // pivot, d > b0 U -------------------------------------------------------------------------------
@@ -737,6 +770,8 @@ void tlu_prepare(Context& c, bool f32) {
     const int64_t tiles = L->solve_tiles ? P.total : (int64_t)L->NT * L->SW;
     L->T = D.alloc<float>((size_t)tiles * per);
     L->DG = D.alloc<float>((size_t)L->NT * per);
+    L->solve_status = D.alloc<int32_t>(1);
+    CK(cudaMemsetAsync(L->solve_status, 0, sizeof(int32_t), D.s));
     auto enc = tensor_map_encoder();
     if (!enc) throw std::runtime_error("cuTensorMapEncodeTiled is not available from the driver");
     const uint64_t rows = (uint64_t)tiles * L->TS;
@@ -788,8 +823,19 @@ bool tlu_solve(Context& c, const double* rhs, double* z, int accumulate, const i
   if (!D.tlu || !D.tlu->solve_tiles) return false;
   TileLU& L = *D.tlu;
   LAUNCH_NAMED(D, "k_tile_solve", k_tile_solve, kSolveCL, 256, tile_solve_smem(L.NT), c.cs.N0, L.NT, L.TB,
-               (const float*)L.T, rhs, z, accumulate, skip, reset);
+               (const float*)L.T, rhs, z, accumulate, skip, reset, L.solve_status);
   return true;
+}
+
+// Raises DeviceTimeout if a cluster solve since the context's setup gave up waiting for its
+// partners' rows (synchronises the stream when the tiled solve is in use).
+void tlu_check_solves(Context& c) {
+  Dev& D = *c.dev;
+  if (!D.tlu || !D.tlu->solve_status) return;
+  int32_t st = 0;
+  CK(cudaMemcpyAsync(&st, D.tlu->solve_status, sizeof(int32_t), cudaMemcpyDeviceToHost, D.s));
+  CK(cudaStreamSynchronize(D.s));
+  if (st == ST_TIMEOUT) throw DeviceTimeout("a CTA of the coarse cluster solve gave up waiting for its partners' rows");
 }
 
 }  // namespace nls

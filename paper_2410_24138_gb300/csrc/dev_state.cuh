@@ -63,6 +63,7 @@ struct TileLU {
   void* DG = nullptr;  // factored diagonal tiles (unit L below the diagonal, U on and above it)
   CUtensorMap map;     // FP32 tiles as a 2D tensor of rows of TS values (TMA, 32 x TS boxes)
   bool solve_tiles = false;  // FP32: inverted diagonal tiles and solve products for the cluster solve
+  int32_t* solve_status = nullptr;  // ST_TIMEOUT once a cluster solve gave up waiting (else 0)
   int64_t launches_per_factor = 0;
 };
 

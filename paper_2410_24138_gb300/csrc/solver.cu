@@ -41,6 +41,7 @@ void tlu_prepare(Context& c, bool f32);
 void tlu_factor(Context& c);
 void tlu_free(Context& c);
 bool tlu_solve(Context& c, const double* rhs, double* z, int accumulate, const int* skip, int* reset);
+void tlu_check_solves(Context& c);
 
 namespace {
 
@@ -1466,10 +1467,15 @@ bool coarse_status_ok(Dev& D) {
   if (st == ST_TIMEOUT) throw DeviceTimeout("a tile of the coarse factorization gave up waiting for its operands");
   return st == ST_OK;
 }
+// The same, after checking that no coarse cluster solve gave up waiting.
+bool coarse_status_ok(Context& c) {
+  tlu_check_solves(c);
+  return coarse_status_ok(*c.dev);
+}
 
 bool coarse_matrix(Context& c, const double* x) {
   coarse_matrix_launch(c, x);
-  return coarse_status_ok(*c.dev);
+  return coarse_status_ok(c);
 }
 
 // A_0(x) = P_0^T DF(x) P_0 in band storage (D.A0): Galerkin blocks per non-overlapping subdomain
@@ -2118,7 +2124,7 @@ FxInfo evaluate_Fx(Context& c, const double* u, double load, double* t_inner, do
     // second stream
     LAUNCH(D, k_p0_apply, grid_for(c.N), 256, 0, c.N, D.p0_rowptr, D.p0_col, D.p0_val, D.c, 1.0, D.Fx, 1.0, D.Fx);
     if (!serial_coarse) CK(cudaStreamWaitEvent(D.s, D.ev_coarse, 0));
-    D.coarse_fact_valid = coarse_status_ok(D);
+    D.coarse_fact_valid = coarse_status_ok(c);
     if (!D.coarse_fact_valid) info.pivot_failure = true;
     D.ainv_valid = D.coarse_fact_valid && D.ainv != nullptr;
   }
@@ -2449,6 +2455,7 @@ int solve(Context& c, double* u_user, int u_dev, nls_report* rep) {
     CK(cudaMemcpyAsync(u_user, D.u, sizeof(double) * N, u_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, D.s));
     CK(cudaEventRecord(e1, D.s));
     CK(cudaEventSynchronize(e1));
+    tlu_check_solves(c);
     float ms = 0.f;
     CK(cudaEventElapsedTime(&ms, e0, e1));
     cudaEventDestroy(e0);
@@ -2730,6 +2737,7 @@ int band_solve(int device, int32_t n, int32_t b, const double* band, const doubl
         for (size_t k = 0; k < nw; ++k) factors_out[k] = (double)f[k];
     }
     sync(D);
+    tlu_check_solves(c);
   } catch (const DeviceTimeout&) {
     status = NLS_E_DEVICE_TIMEOUT;
   } catch (const CudaFailure&) {

@@ -63,6 +63,42 @@ __device__ inline bool mbar_wait(uint64_t* bar, uint32_t parity) {
   }
 }
 
+// ---- cluster exchange through distributed shared memory ------------------------------------
+// Address of the same shared-memory location in CTA `rank` of the cluster.
+__device__ inline uint32_t cluster_addr(const void* local, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(local)), "r"(rank));
+  return r;
+}
+// Two floats into another CTA's shared memory (8-byte aligned address); the store completes 8
+// transaction bytes on that CTA's mbarrier `rbar` (both cluster addresses from cluster_addr).
+__device__ inline void st_async_f2(uint32_t raddr, float a, float b, uint32_t rbar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f32 [%0], {%1, %2}, [%3];" ::"r"(raddr),
+               "f"(a), "f"(b), "r"(rbar)
+               : "memory");
+}
+// Wait on a local mbarrier whose transactions come from other CTAs of the cluster (acquire at
+// cluster scope, so their stores are visible afterwards); false after kWaitLimitNs.
+__device__ inline bool mbar_try_wait_cluster(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ inline bool mbar_wait_cluster(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait_cluster(bar, parity)) return true;
+  const uint64_t t0 = globaltimer_ns();
+  for (;;) {
+    if (mbar_try_wait_cluster(bar, parity)) return true;
+    if (globaltimer_ns() - t0 > kWaitLimitNs) return false;
+  }
+}
+
 // ---- TMA ---------------------------------------------------------------------------------
 // 2D tiled load of the box at (x, y) (x = innermost coordinate, in elements; x times the
 // element size must be a multiple of 16 bytes) into shared memory; completion is signalled on
