@@ -108,8 +108,9 @@ __global__ void k_tlu_init(int N0, int b0, int NT, int TB, const double* __restr
 // stores it in DG[k] and flags a zero or non-finite pivot.  Panel p < TB is the L tile
 // (k+1+p, k): X := X U_kk^-1 on rows of the tile; panel p >= TB is the U tile (k, k+1+p-TB),
 // stored transposed: X := X L_kk^-T on rows of the stored transpose.  Both are X := X M^-1 with
-// M upper triangular, solved column by column (one barrier per column).  With LT given, an L
-// tile is also written transposed there (the B operand of M_tk for the solves).
+// M upper triangular.  The diagonal tile's LU and the slab's solve are both blocked by 32-column
+// groups: one barrier per column inside a group, a rank-32 update of the rest after it.  With LT
+// given, an L tile is also written transposed there (the B operand of M_tk for the solves).
 template <typename FT>
 __device__ inline FT rcp(FT x) {
   if constexpr (sizeof(FT) == 4) return __frcp_rn(x);
@@ -143,39 +144,70 @@ __global__ void __launch_bounds__(512) k_tlu_panel(int k, int NT, int TB, FT* __
 #pragma unroll
     for (int b = 0; b < CB; ++b) R[a][b] = Akk[(ty + 16 * a) * TS + tx + 32 * b];
   if (tid == 0) s_bad = 0;
-  // Row r = ty + 16 a is the same in a whole warp, so the tests on r (and on whole 32-column
-  // groups b) are warp-uniform: finished row groups and column groups skip their updates.
-  for (int t = 0; t < TS; ++t) {
-    FT* rb = rowbuf + (t & 1) * TS;
-    FT* cb = colbuf + (t & 1) * TS;
+  // Blocked right-looking LU over the 32-column panels j of the tile.  Row r = ty + 16 a is the
+  // same in a whole warp and column c = tx + 32 b is lane tx of column group b, so panel j is the
+  // register column R[.][j] and its 32 pivot rows are a = 2j, 2j + 1.  For each pivot t of the
+  // panel: rows below t update their panel column and, inside the panel's own 32 rows, also the
+  // columns right of the panel (which makes those rows U12 = L11^-1 A12); then the rows below the
+  // panel take the rank-32 product A22 -= L21 U12 at once, L21 from warp shuffles (row r's
+  // multipliers sit in the lanes of its warp) and U12 through shared memory.
 #pragma unroll
-    for (int a = 0; a < RA; ++a)
+  for (int j = 0; j < CB; ++j) {
+    for (int t = 32 * j; t < 32 * j + 32; ++t) {
+      FT* rb = rowbuf + (t & 1) * TS;
+      FT* cb = colbuf + (t & 1) * TS;
 #pragma unroll
-      for (int b = 0; b < CB; ++b) {
-        if (ty + 16 * a == t) rb[tx + 32 * b] = R[a][b];
-        if (tx + 32 * b == t) cb[ty + 16 * a] = R[a][b];
+      for (int a = 0; a < RA; ++a)
+        if (ty + 16 * a == t) {
+#pragma unroll
+          for (int b = j; b < CB; ++b) rb[tx + 32 * b] = R[a][b];
+        }
+      if (tx == t - 32 * j) {
+#pragma unroll
+        for (int a = 0; a < RA; ++a) cb[ty + 16 * a] = R[a][j];
       }
-    __syncthreads();
-    const FT piv = rb[t];
-    const FT rp = rcp<FT>(piv);
-    if (tid == 0) {
-      rpiv[t] = rp;
-      if (!(piv != (FT)0) || !isfinite((double)piv)) s_bad = 1;
-    }
+      __syncthreads();
+      const FT piv = rb[t];
+      const FT rp = rcp<FT>(piv);
+      if (tid == 0) {
+        rpiv[t] = rp;
+        if (!(piv != (FT)0) || !isfinite((double)piv)) s_bad = 1;
+      }
 #pragma unroll
-    for (int a = 0; a < RA; ++a) {
-      const int r = ty + 16 * a;
-      if (r > t) {  // warp-uniform
-        const FT l = cb[r] * rp;
+      for (int a = 0; a < RA; ++a) {
+        const int r = ty + 16 * a;
+        if (r > t) {  // warp-uniform
+          const FT l = cb[r] * rp;
+          const int c = tx + 32 * j;
+          if (c > t) R[a][j] -= l * rb[c];
+          else if (c == t) R[a][j] = l;  // the multiplier of L
+          if (a == 2 * j || a == 2 * j + 1) {  // the panel's own rows: U12
 #pragma unroll
-        for (int b = 0; b < CB; ++b) {
-          if (32 * b + 31 >= t) {  // the column group is not finished
-            const int c = tx + 32 * b;
-            if (c > t) R[a][b] -= l * rb[c];
-            else if (c == t) R[a][b] = l;  // the multiplier of L
+            for (int b = j + 1; b < CB; ++b) R[a][b] -= l * rb[tx + 32 * b];
           }
         }
       }
+    }
+    if (j + 1 < CB) {
+      // U12 (rows 32 j .. 32 j + 31, columns right of the panel) into shared memory (Dg serves as
+      // scratch until the end), then A22 -= L21 U12 on the rows below the panel
+#pragma unroll
+      for (int a = 2 * j; a < 2 * j + 2; ++a)
+#pragma unroll
+        for (int b = j + 1; b < CB; ++b) Dg[(ty + 16 * (a - 2 * j)) * LD + tx + 32 * b] = R[a][b];
+      __syncthreads();
+      for (int kk = 0; kk < 32; ++kk) {
+        FT l[RA];
+#pragma unroll
+        for (int a = 2 * j + 2; a < RA; ++a) l[a] = __shfl_sync(0xffffffffu, R[a][j], kk);
+#pragma unroll
+        for (int b = j + 1; b < CB; ++b) {
+          const FT u = Dg[kk * LD + tx + 32 * b];
+#pragma unroll
+          for (int a = 2 * j + 2; a < RA; ++a) R[a][b] -= l[a] * u;
+        }
+      }
+      __syncthreads();  // U12 read by every warp before the next panel's rows overwrite the scratch
     }
   }
 #pragma unroll
@@ -195,34 +227,47 @@ __global__ void __launch_bounds__(512) k_tlu_panel(int k, int NT, int TB, FT* __
   // X := X M^-1 on the slab's rows, M = U_kk (lower panel) or L_kk^T (upper panel, unit diagonal)
   FT* P = T + (lower ? tile_slot(other, k, TB) : tile_slot(k, other, TB)) * TS * TS + (int64_t)q * SLAB * TS;
   FT X[SA][CB];
-#pragma unroll
-  for (int a = 0; a < SA; ++a)
-#pragma unroll
-    for (int b = 0; b < CB; ++b) X[a][b] = P[(ty + 16 * a) * TS + tx + 32 * b];
-  for (int t = 0; t < TS; ++t) {
-    FT* cb = colbuf + (t & 1) * TS;
-    const FT rt = lower ? rpiv[t] : (FT)1;
+  {
 #pragma unroll
     for (int a = 0; a < SA; ++a)
 #pragma unroll
-      for (int b = 0; b < CB; ++b)
-        if (tx + 32 * b == t) cb[ty + 16 * a] = X[a][b] * rt;
-    FT m[CB];
+      for (int b = 0; b < CB; ++b) X[a][b] = P[(ty + 16 * a) * TS + tx + 32 * b];
+    // blocked over the 32-column groups j: column by column inside the group (one barrier per
+    // column, only the group's register column X[.][j] changes), then the columns right of the
+    // group take X[:, right] -= X[:, group] M[group, right] at once (the row's group values from
+    // warp shuffles, M from the factored tile)
 #pragma unroll
-    for (int b = 0; b < CB; ++b) {
-      const int c = tx + 32 * b;
-      m[b] = (32 * b + 31 < t) ? (FT)0 : (lower ? Dg[t * LD + c] : Dg[c * LD + t]);
-    }
-    __syncthreads();
+    for (int j = 0; j < CB; ++j) {
+      for (int t = 32 * j; t < 32 * j + 32; ++t) {
+        FT* cb = colbuf + (t & 1) * TS;
+        const FT rt = lower ? rpiv[t] : (FT)1;
+        if (tx == t - 32 * j) {
 #pragma unroll
-    for (int a = 0; a < SA; ++a) {
-      const FT x = cb[ty + 16 * a];
+          for (int a = 0; a < SA; ++a) cb[ty + 16 * a] = X[a][j] * rt;
+        }
+        const int c = tx + 32 * j;
+        const FT m = (c > t) ? (lower ? Dg[t * LD + c] : Dg[c * LD + t]) : (FT)0;
+        __syncthreads();
 #pragma unroll
-      for (int b = 0; b < CB; ++b) {
-        if (32 * b + 31 >= t) {  // the column group is not final
-          const int c = tx + 32 * b;
-          if (c > t) X[a][b] -= x * m[b];
-          else if (c == t) X[a][b] = x;  // final value of column t
+        for (int a = 0; a < SA; ++a) {
+          const FT x = cb[ty + 16 * a];
+          if (c > t) X[a][j] -= x * m;
+          else if (c == t) X[a][j] = x;  // final value of column t
+        }
+      }
+      if (j + 1 < CB) {
+        for (int kk = 0; kk < 32; ++kk) {
+          FT xv[SA];
+#pragma unroll
+          for (int a = 0; a < SA; ++a) xv[a] = __shfl_sync(0xffffffffu, X[a][j], kk);
+          const int k = 32 * j + kk;
+#pragma unroll
+          for (int b = j + 1; b < CB; ++b) {
+            const int c = tx + 32 * b;
+            const FT m = lower ? Dg[k * LD + c] : Dg[c * LD + k];
+#pragma unroll
+            for (int a = 0; a < SA; ++a) X[a][b] -= xv[a] * m;
+          }
         }
       }
     }
@@ -579,14 +624,20 @@ __global__ void __cluster_dims__(kSolveCL, 1, 1) __launch_bounds__(256, 1)
     }
     const float4 g4 = ((const float4*)(gt + (t & 1) * kTcTS))[lane];
     float a0 = dot4(cur[0][0], g4), a1 = dot4(cur[0][1], g4);
-    if (t >= 1) wait(fb + t - 1);  // y_{t-1} complete (older tiles were waited for before)
+    // the terms of tiles that arrived in earlier steps first, then wait for y_{t-1}
 #pragma unroll
-    for (int k = 1; k <= kSolveMaxTB; ++k)
+    for (int k = 2; k <= kSolveMaxTB; ++k)
       if (k <= TB && t - k >= 0) {
         const float4 yv = ((const float4*)(y + (int64_t)(t - k) * kTcTS))[lane];
         a0 -= dot4(cur[k][0], yv);
         a1 -= dot4(cur[k][1], yv);
       }
+    if (t >= 1) {
+      wait(fb + t - 1);
+      const float4 yv = ((const float4*)(y + (int64_t)(t - 1) * kTcTS))[lane];
+      a0 -= dot4(cur[1][0], yv);
+      a1 -= dot4(cur[1][1], yv);
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       a0 += __shfl_xor_sync(0xffffffffu, a0, o);
@@ -608,14 +659,19 @@ __global__ void __cluster_dims__(kSolveCL, 1, 1) __launch_bounds__(256, 1)
     if (t - kSolveL2 >= 0) l2_ahead(t - kSolveL2, false);
     const float4 yv = ((const float4*)(y + (int64_t)t * kTcTS))[lane];
     float a0 = dot4(cur[0][0], yv), a1 = dot4(cur[0][1], yv);
-    if (t + 1 < NT) wait(bb + t + 1);  // x_{t+1} complete
 #pragma unroll
-    for (int k = 1; k <= kSolveMaxTB; ++k)
+    for (int k = 2; k <= kSolveMaxTB; ++k)
       if (k <= TB && t + k < NT) {
         const float4 xv = ((const float4*)(xr + ((t + k) % RB) * kTcTS))[lane];
         a0 -= dot4(cur[k][0], xv);
         a1 -= dot4(cur[k][1], xv);
       }
+    if (t + 1 < NT) {
+      wait(bb + t + 1);  // x_{t+1} complete
+      const float4 xv = ((const float4*)(xr + ((t + 1) % RB) * kTcTS))[lane];
+      a0 -= dot4(cur[1][0], xv);
+      a1 -= dot4(cur[1][1], xv);
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       a0 += __shfl_xor_sync(0xffffffffu, a0, o);
