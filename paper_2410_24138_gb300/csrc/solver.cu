@@ -84,6 +84,7 @@ struct LocalArgs {
   int guess_sweeps;
   double guess_omega;
   int want_tangent;
+  int split_factor;           // 1: the tangent's band LU and packing run in k_local_factor
   int32_t* accepted;          // per subdomain: 1 where the proposed start was taken
   unsigned long long* phase;  // optional per-phase clock counters (profiling), see kPhaseNames
   // tangent application
@@ -547,8 +548,10 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 128 ? 4 : 1)) k_local_newton(Lo
     if (A.want_tangent && status != ST_NONFINITE && status != ST_PIVOT) {
       local_jacobian<LAW, FT>(A, m, xt, csr, F);
       mark(5);
-      if (dev::band_lu_inplace<FT>(n, m.b, F, win, rp, flag)) status = ST_PIVOT;
-      else dev::band_pack_solve<FT>(n, m.b, F, Dv, win, inv_warps);
+      if (!A.split_factor) {
+        if (dev::band_lu_inplace<FT>(n, m.b, F, win, rp, flag)) status = ST_PIVOT;
+        else dev::band_pack_solve<FT>(n, m.b, F, Dv, win, inv_warps);
+      }
       mark(6);
     }
     for (int a = tid; a < n; a += blockDim.x) {
@@ -565,6 +568,49 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 128 ? 4 : 1)) k_local_newton(Lo
     }
     __syncthreads();
     mark(7);
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// k_local_factor: the tangent's refactorisation at the converged states -- band LU of the band
+// that k_local_newton assembled and the packed solve operands -- as its own launch.  The Newton
+// kernel's FP64 element tangents of Eq. 2 hold all of an SM's registers for one CTA; this kernel
+// needs few registers and (FP32) about 65 KB of shared memory, so three CTAs share an SM and hide
+// each other's per-step barrier latency.  One CTA per subdomain, longest first; subdomains whose
+// local solve failed are skipped, a zero pivot marks the subdomain ST_PIVOT.
+// ------------------------------------------------------------------------------------------
+template <typename FT>
+__host__ __device__ inline LocalPlan factor_plan(int max_b) {
+  LocalPlan p{};
+  size_t o = 0;
+  const size_t lu = (size_t)dev::band_lu_window_rows(max_b) * dev::band_lu_window_stride(max_b);
+  const size_t inv = 4 * (size_t)dev::SolveBlock<FT>::BS * (dev::SolveBlock<FT>::BS + 1);
+  p.win = o; o += align_up(sizeof(FT) * (lu > inv ? lu : inv), 16);
+  p.rp = o; o += align_up(sizeof(FT) * dev::band_lu_window_rows(max_b), 16);
+  p.flag = o; o += 16;
+  p.total = o;
+  return p;
+}
+
+template <typename FT>
+__global__ void __launch_bounds__(256, 3) k_local_factor(LocalArgs A) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const LocalPlan P = factor_plan<FT>(A.max_b);
+  FT* win = (FT*)(smem + P.win);
+  FT* rp = (FT*)(smem + P.rp);
+  int* flag = (int*)(smem + P.flag);
+  constexpr int BSI = dev::SolveBlock<FT>::BS;
+  const int inv_warps = min((int)(blockDim.x >> 5), (int)((P.rp - P.win) / (sizeof(FT) * BSI * (BSI + 1))));
+  const int sub = A.order[blockIdx.x];
+  const int st = A.status[sub];
+  if (st == ST_NONFINITE || st == ST_PIVOT) return;
+  const SubMeta m = A.meta[sub];
+  FT* F = (FT*)A.factor + m.factor_off;
+  FT* Dv = (FT*)A.dinv + m.dinv_off;
+  if (dev::band_lu_inplace<FT>(m.n, m.b, F, win, rp, flag)) {
+    if (threadIdx.x == 0) A.status[sub] = ST_PIVOT;
+  } else {
+    dev::band_pack_solve<FT>(m.n, m.b, F, Dv, win, inv_warps);
   }
 }
 
@@ -1317,6 +1363,17 @@ int newton_ctas_per_sm(Context& c) {
   return std::max(1, occ);
 }
 
+// The tangent's refactorisation goes to k_local_factor when the Newton kernel, at its current
+// CTA size, holds one CTA per SM and the factor kernel fits at least two.
+bool split_local_factor(Context& c) {
+  int occ = 0;
+  if (fp32_local(c))
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_local_factor<float>, 256, factor_plan<float>(c.ov.max_b).total));
+  else
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_local_factor<double>, 256, factor_plan<double>(c.ov.max_b).total));
+  return newton_ctas_per_sm(c) == 1 && occ >= 2;
+}
+
 void dispatch_local_newton(Context& c, const LocalSet& s, const LocalArgs& A, int T) {
   Dev& D = *c.dev;
   const bool f32 = fp32_local(c);
@@ -1343,10 +1400,15 @@ void launch_local_newton(Context& c, const double* x, double* out, double load, 
   A.guess_sweeps = g.x ? g.sweeps : 0;
   A.guess_omega = g.omega;
   A.want_tangent = want_tangent ? 1 : 0;
+  A.split_factor = (want_tangent && split_local_factor(c)) ? 1 : 0;
   A.phase = D.prof ? D.phase : nullptr;
   A.reuse = (D.local_reuse_active && D.local_factors_valid) ? 1 : 0;
   CK(cudaMemsetAsync(D.ov.queue, 0, sizeof(int32_t), D.s));
   dispatch_local_newton(c, c.ov, A, local_threads(c));
+  if (A.split_factor) {
+    if (fp32_local(c)) LAUNCH(D, k_local_factor<float>, c.ov.count, 256, factor_plan<float>(c.ov.max_b).total, A);
+    else LAUNCH(D, k_local_factor<double>, c.ov.count, 256, factor_plan<double>(c.ov.max_b).total, A);
+  }
 }
 
 void launch_local_apply(Context& c, const double* v, const double* add, double* out) {
@@ -1848,6 +1910,8 @@ int device_setup(Context& c) {
     set_smem(k_local_newton<NLS_LAW_NEOHOOKE, float, 256>, lim);
     set_smem(k_local_newton<NLS_LAW_NEOHOOKE, double, 256>, lim);
     set_smem(k_local_apply<float>, lim);
+    set_smem(k_local_factor<float>, lim);
+    set_smem(k_local_factor<double>, lim);
     set_smem(k_guess_smooth<NLS_LAW_DIFFUSION>, lim);
     set_smem(k_guess_smooth<NLS_LAW_NEOHOOKE>, lim);
     set_smem(k_local_apply<double>, lim);
