@@ -7,7 +7,8 @@
 // is cut into square tiles and factored without pivoting, right-looking, one tile column per
 // step, across many CTAs:
 //
-//   step k:  A_kk = L_kk U_kk                      (every panel CTA, in shared memory)
+//   step k:  A_kk = L_kk U_kk                      (every panel CTA, in registers, blocked by
+//                                                   32-column groups)
 //            L_ik = A_ik U_kk^-1,  U_kj = L_kk^-1 A_kj   (i, j = k+1 .. k+TB; row slabs per CTA)
 //            A_ij -= L_ik U_kj                     (i, j = k+1 .. k+TB; one CTA per tile)
 //
@@ -28,9 +29,9 @@
 //   y_t = L_tt^-1 g_t - sum_k M_tk y_{t-k},      x_t = U_tt^-1 y_t - sum_k N_tk x_{t+k}:
 // one independent GEMV per row of the tile.  One cluster of 8 CTAs runs a solve: each CTA owns
 // 16 rows of every tile, loads the next step's operand rows into registers while it finishes the
-// current step, and broadcasts its rows of y_t (x_t) into every CTA's shared memory (distributed
-// shared memory), one cluster barrier per tile step.  Every coarse solve is refined in FP64
-// against the band A_0 by the caller.
+// current step, and sends its rows of y_t (x_t) into every CTA's shared memory (distributed shared
+// memory, st.async completing on that step's mbarrier in the receiver), so that a step waits only
+// for the tile it needs.  Every coarse solve is refined in FP64 against the band A_0 by the caller.
 //
 // The factors are also written in the band layout of the one-CTA factorization and packed into
 // its triangular-solve operands (the explicit coarse inverse is built from those).
