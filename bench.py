@@ -693,10 +693,15 @@ def fp32_peak_tflops(peaks):
     return SMS * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
 
 
-# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the default
-# workload, from the ncu captures summarised in profiles/ (keyed by workload and kernel); a kernel
-# changed since its capture has no entry.
-NCU_TRAFFIC_BYTES = {}
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch, from the ncu captures
+# summarised in profiles/ (keyed by workload and kernel); a kernel changed since its capture has no
+# entry.  k_local_apply was captured on the 512^2 Neo-Hooke workload (1.523 GB per launch); on the
+# 2048^2 one (same subdomain size, 16x the subdomains) it is scaled by the ratio of the algorithmic
+# bytes per launch (8.28 / 0.5126 GB).
+NCU_TRAFFIC_BYTES = {
+    ("c3", "k_local_apply<float>"): 1.523e9,
+    ("c5", "k_local_apply<float>"): 1.523e9 * 8.2796e9 / 0.5126e9,
+}
 
 
 def roofline_for(name, launches, ms, sizes, peaks, peak_kind, steps_per_launch=None, split_factor=False):
