@@ -21,6 +21,12 @@ takes both far below that.  Both forms run: F_x within 1e-9 in both; the tangent
 FP64 form and 1e-7 in the FP32 form, whose FP32 factors are refined to 1e-10 against the local
 Jacobian assembled from FP64 element tangents -- the same bounds as for Eq. 1.  Every comparison
 is also made entry by entry in the max norm, at ten times the l2 bound.
+
+The whole pipeline at full size (hybrid coupling: coarse Newton, local solves, exact tangent in
+GMRES, outer Newton) is checked on the 1024 x 1024 diffusion workload against the oracle's plain
+global Newton on the same mesh (F(u) = 0 of Eq. 1 written out, sparse direct FP64 solves): both
+sides are driven to ||F|| < 1e-12, and the converged solutions must agree within 1e-8 (FP64 form)
+and 1e-6 (FP32 factors + refinement) relative l2, the bounds of the small-size tests.
 """
 import numpy as np
 import pytest
@@ -95,3 +101,19 @@ def test_full_size_neohooke_sampled_local_corrections_and_tangent(nls, workload,
         tol = 1e-9 if precision == "fp64" else 1e-7
         assert np.linalg.norm(y[owned] - yo[owned]) <= tol * np.linalg.norm(yo[owned])
         assert np.abs(y[owned] - yo[owned]).max() <= 10 * tol * np.abs(yo[owned]).max()
+
+
+def test_full_size_converged_solution_matches_oracle_plain_newton(nls):
+    p = I.diffusion_c2()
+    ustar, _ = S.plain_newton(p, tol=1e-12, load_steps=p.load_steps)
+    F = fem.global_residual(fem.Model(p), ustar)
+    assert np.linalg.norm(F) < 1e-12
+    for precision, tol in (("fp64", 1e-8), ("fp32", 1e-6)):
+        # local solves tight enough that their corrections still resolve ||F|| ~ 1e-12 (with the
+        # default local tolerance every correction vanishes once ||F|| ~ 1e-11: F_x = 0, done)
+        s = nls.make_solver(p, coupling="hybrid", precision=precision, outer_atol=1e-12, inner_atol=1e-15)
+        u, rep = s.solve()
+        s.close()
+        assert rep.status == 0 and rep.final_residual < 1e-12, (precision, rep.final_residual)
+        err = np.linalg.norm(u - ustar) / np.linalg.norm(ustar)
+        assert err < tol, (precision, err)
